@@ -1,0 +1,326 @@
+"""Benchmark of the per-ray VR-NeRF field renderer on one GB300.
+
+Workload (the step): one render of a single 2048x2048 eye buffer in the
+20 m x 20 m x 3 m synthetic room (L=16 hash levels, T=2^21, fp16 features,
+256^3 occupancy, <= 1024 exponential samples per ray), camera at 1.7 m,
+every step of the path (ray generation, occupancy march, LOD hash-grid
+gather, density/colour MLP, compositing, PQ decode) in one launch.
+
+Reports, as one JSON line:
+  value            Mrays/s of the tuned path, inputs resident in HBM
+  e2e              Mrays/s through vrnerf_render_host (host buffers, copies
+                   inside the timed region)
+  plain_fp32       the same for the fp32 MLP path
+  stereo           2 x 2048^2 frame latency p50 / p99 (tuned path)
+  roofline         dominant kernel (the fused render kernel) vs measured HBM peak
+  cpu_baseline     the CPU oracle on a bounded crop of the same frame
+  clocks           SM clocks sampled with nvidia-smi during the timed region
+
+`--impl reference` times the CPU oracle instead (the only reference that
+exists: the paper ships no code), on a 256x256 crop per step.
+With --gpus N > 1 (torchrun) every rank renders its own frame: the path
+shards by views with no collective (replicas only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "room_2048x2048_single_eye"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="auto")
+    ap.add_argument("--variant", default="room", choices=["room", "room_surface"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.f.read().splitlines():
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(mx)) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def pick_precision(V, arg):
+    if arg != "auto":
+        return V.PRECISIONS[arg]
+    return V.FP16
+
+
+def run_oracle_sample(sc, c2w, K, seconds, threads):
+    """Renders 128x128 crops of the frame with the CPU oracle until about
+    `seconds` have passed; returns (rays, elapsed)."""
+    import oracle as O
+    from paper_2311_02542_gb300 import synth as S
+    F = O.Field(sc.cfg, sc.grid, sc.mlp, sc.occ_bits)
+    rng = np.random.default_rng(0)
+    rays, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        x0, y0 = rng.integers(0, 2048 - 128, 2)
+        F.render(c2w, S.crop_camera(K, int(x0), int(y0)), np.array([[128, 128]], np.int32),
+                 threads=threads)
+        rays += 128 * 128
+    return rays, time.perf_counter() - t0
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2311_02542_gb300 import synth as S
+    import oracle as O
+    sc = S.make_scene(args.variant)
+    c2w, K, res = S.camera_room(sc.occ, sc.cfg, 2, 2048, 2048)
+    F = O.Field(sc.cfg, sc.grid, sc.mlp, sc.occ_bits)
+    threads = os.cpu_count() or 1
+    crop = np.array([[256, 256]], np.int32)
+    rng = np.random.default_rng(1)
+
+    def step():
+        x0, y0 = rng.integers(0, 2048 - 256, 2)
+        F.render(c2w, S.crop_camera(K, int(x0), int(y0)), crop, threads=threads)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    rays = 256 * 256 * args.steps
+    v = rays / dt / 1e6
+    line = {"impl": "reference", "metric": "Mrays/s", "value": round(v, 4), "unit": "Mrays/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * dt / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "variant": args.variant,
+                       "sample": "one 256x256 crop of the 2048x2048 frame per step"},
+            "cpu_baseline": {"value": round(v, 4), "unit": "Mrays/s", "cores": threads,
+                             "kind": "oracle",
+                             "sample": "one 256x256 crop of the 2048x2048 frame per step"},
+            "e2e": {"value": round(v, 4), "unit": "Mrays/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2311_02542_gb300 import synth as S
+    from paper_2311_02542_gb300 import vrnerf as V
+    V.load()
+    dev = torch.device("cuda", local)
+
+    sc = S.make_scene(args.variant)
+    cfg = sc.cfg
+    field = V.Field(cfg, sc.grid, sc.mlp, sc.occ_bits)
+    c2w, K, res = S.camera_room(sc.occ, cfg, 2 + rank, 2048, 2048)
+    cams, intr = torch.from_numpy(c2w).to(dev), torch.from_numpy(K).to(dev)
+    rays = int(res[0, 0]) * int(res[0, 1])
+    out = torch.empty((rays, 3), device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    stream = torch.cuda.current_stream()
+    tuned = pick_precision(V, args.precision)
+    try:
+        V.vrnerf_render(field, cams, intr, res, out=out, precision=tuned)
+        torch.cuda.synchronize()
+    except V.VrnerfError:
+        tuned = V.FP32
+    precision_name = {v: k for k, v in V.PRECISIONS.items()}[tuned]
+
+    def timed(precision, steps, warmup, resolution=res, cam=cams, K_=intr, o=out):
+        for _ in range(warmup):
+            V.vrnerf_render(field, cam, K_, resolution, out=o, precision=precision)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            V.vrnerf_render(field, cam, K_, resolution, out=o, precision=precision)
+            b.record(stream)
+            ts.append((a, b))
+        torch.cuda.synchronize()
+        return np.array([a.elapsed_time(b) for a, b in ts])
+
+    # work statistics of one frame (untimed): samples, levels fetched, steps
+    stats = torch.zeros(4, dtype=torch.int64, device=dev)
+    V.vrnerf_render(field, cams, intr, res, out=out, precision=tuned, stats=stats)
+    torch.cuda.synchronize()
+    n_samples, n_levels, n_steps, n_rays_done = [int(x) for x in stats.cpu()]
+
+    # timed region: tuned path, bracketed by barrier + synchronize
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    t_wall0 = time.perf_counter()
+    ms = timed(tuned, args.steps, args.warmup)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall0
+    clocks = clk.stop()
+    ms_step = float(ms.mean())
+    if world > 1:
+        t = torch.tensor([ms_step], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * rays / (ms_step * 1e-3) / 1e6
+
+    # plain fp32 path on the same frame
+    ms32 = timed(V.FP32, max(3, args.steps // 2), 2) if tuned != V.FP32 else ms
+
+    # stereo 2 x 2048^2 frame latency (tuned)
+    st_c2w = S.stereo_pair(c2w[0])
+    st_K = np.concatenate([K, K])
+    st_res = np.array([[2048, 2048], [2048, 2048]], np.int32)
+    st_out = torch.empty((2 * rays, 3), device=dev)
+    st_ms = timed(tuned, max(args.steps, 20), 3, st_res, torch.from_numpy(st_c2w).to(dev),
+                  torch.from_numpy(st_K).to(dev), st_out)
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    h_out = torch.empty((rays, 3), dtype=torch.float32, pin_memory=True).numpy()
+    h_cam = torch.from_numpy(c2w.copy()).pin_memory().numpy()
+    h_K = torch.from_numpy(K.copy()).pin_memory().numpy()
+    for _ in range(2):
+        V.vrnerf_render_host(field, h_cam, h_K, res, out=h_out, precision=tuned)
+    e2e_t = []
+    for _ in range(max(3, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        V.vrnerf_render_host(field, h_cam, h_K, res, out=h_out, precision=tuned)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_v = world * rays / float(np.mean(e2e_t)) / 1e6
+
+    hbm_peak, peak_kind = load_peaks()
+    feat_bytes = 2 if cfg.feat_fp16 else 4
+    # algorithmic bytes of one launch: 8 corners x F features per fetched
+    # level, 12 B of output per ray, 1 bit of occupancy per tested step
+    alg_bytes = n_levels * 8 * cfg.feats * feat_bytes + rays * 12 + n_steps / 8.0
+    achieved = alg_bytes / (ms_step * 1e-3) / 1e9
+
+    line = {
+        "metric": "Mrays/s", "value": round(value, 3), "unit": "Mrays/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "fp16": "f16+f32acc", "bf16": "bf16+f32acc",
+                  "fp8": "e4m3+f16+f32acc"}[precision_name],
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "variant": args.variant, "resolution": [2048, 2048],
+                   "views_per_step": 1, "rays_per_step": rays, "mlp_precision": precision_name,
+                   "levels": cfg.levels, "log2_T": cfg.log2_T, "occ_res": list(cfg.occ_res),
+                   "max_steps": cfg.max_steps, "parallelism": f"replicas{world}",
+                   "l2": "256 MB buffer written between timed steps"},
+        "work": {"samples_per_ray": round(n_samples / rays, 3),
+                 "levels_per_sample": round(n_levels / max(n_samples, 1), 3),
+                 "steps_per_ray": round(n_steps / rays, 2), "rays_finished": n_rays_done},
+        "plain_fp32": {"value": round(world * rays / (float(ms32.mean()) * 1e-3) / 1e6, 3),
+                       "unit": "Mrays/s", "ms_per_step": round(float(ms32.mean()), 4)},
+        "stereo_2x2048": {"p50_ms": round(float(np.percentile(st_ms, 50)), 4),
+                          "p99_ms": round(float(np.percentile(st_ms, 99)), 4),
+                          "fps_p99": round(1e3 / float(np.percentile(st_ms, 99)), 2),
+                          "frames": int(st_ms.size)},
+        "e2e": {"value": round(e2e_v, 3), "unit": "Mrays/s", "h2d_bytes_per_step": 64,
+                "d2h_bytes_per_step": rays * 12},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": hbm_peak,
+                     "unit": "GB/s", "frac": round(achieved / hbm_peak, 5), "traffic": None,
+                     "peak_kind": peak_kind, "kernel": "render (fused march+gather+MLP+composite)"},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+        "wall_s_timed": round(wall, 3),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        crays, cdt = run_oracle_sample(sc, c2w, K, args.cpu_seconds, threads)
+        line["cpu_baseline"] = {"value": round(crays / cdt / 1e6, 5), "unit": "Mrays/s",
+                                "cores": threads, "kind": "oracle",
+                                "sample": f"{crays // (128 * 128)} random 128x128 crops of the "
+                                          f"2048x2048 frame ({cdt:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,220 @@
+/*
+ * vrnerf.h -- C ABI of the GB300 (sm_103a) renderer of VR-NeRF's field
+ * ("VR-NeRF: High-Fidelity Virtualized Walkable Spaces", SIGGRAPH Asia 2023).
+ *
+ * The library renders an instant-NGP-style radiance field per ray: pinhole
+ * ray generation, a march through a binary occupancy grid (Sec. 4.3),
+ * multiresolution hash-grid features weighted by the level-of-detail scheme
+ * of Sec. 4.2.1 (Eq. 3) with an optional LOD bias (Sec. 4.2.2), a density MLP
+ * and a colour MLP (Sec. 6; the in-register tensor-core MLP of Sec. 5),
+ * sigmoid colour in the PQ perceptual space (Sec. 4.1), front-to-back
+ * compositing with early termination, and PQ decoding (Eq. 1-2) to linear
+ * colour (1.0 = 100 cd/m^2). It also trains the field: the L1 loss in PQ
+ * space (Sec. 4.1; supplement "Loss Design") back-propagated through the
+ * compositor, the MLPs and the hash grid, and the Adam step of Sec. 6.
+ *
+ * Conventions for every entry point:
+ *  - Return value: VRNERF_OK (0) or a negative VRNERF_E* code. The message
+ *    of the last failure on the calling thread is vrnerf_last_error().
+ *    No C++ exception crosses this interface.
+ *  - Pointers named *_host are host memory; every other array pointer is
+ *    device memory of the current CUDA device. The caller owns all buffers
+ *    it passes; the library never frees or keeps them past the call (except
+ *    where an entry point says so).
+ *  - A field owns its device parameters, occupancy bits and scratch memory,
+ *    allocated on the device that is current at vrnerf_field_create.
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream) and is asynchronous unless stated otherwise: outputs are valid
+ *    once the stream has been synchronised. Sizes and shapes are validated
+ *    on the host before anything is launched; a rejected call enqueues
+ *    nothing.
+ *  - A field is not thread-safe: calls on one field must not overlap in
+ *    time on different host threads, and work of different calls on one
+ *    field must not run concurrently on different streams.
+ *
+ * Layouts:
+ *  - hash grid [L][T][F], F contiguous, fp32 or IEEE fp16 (feat_fp16); every
+ *    level holds T = 2^log2_T slots, dense levels use the first (N_l+1)^3.
+ *  - MLP weights fp32, [out][in] row-major, concatenated W1 (64 x L*F),
+ *    W2 (16 x 64), W3 (64 x 32), W4 (64 x 64), W5 (3 x 64); no biases.
+ *  - occupancy bits: voxel (x, y, z) -> i = x + rx*(y + ry*z), word i >> 5,
+ *    bit i & 31 (uint32 words).
+ *  - cameras [n][3][4] fp32 camera-to-world (columns right, down, forward,
+ *    centre; the camera looks down its +z axis); intrinsics [n][4] fp32
+ *    (fx, fy, cx, cy) in pixels; resolution [n][2] int32 (W, H).
+ *  - image outputs are packed per view, row-major, RGB interleaved: view v
+ *    starts at pixel sum_{u<v} W_u*H_u.
+ */
+#ifndef VRNERF_H
+#define VRNERF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VRNERF_OK 0
+#define VRNERF_EINVAL (-1)    /* bad argument, shape or size */
+#define VRNERF_ENOMEM (-2)    /* device or host allocation failed */
+#define VRNERF_ECUDA (-3)     /* a CUDA call or kernel launch failed */
+#define VRNERF_ETIMEDOUT (-4) /* a bounded wait ran out */
+#define VRNERF_EBUSY (-5)     /* admission refused: over budget or queue full */
+#define VRNERF_ENOTFOUND (-6) /* unknown ticket */
+#define VRNERF_ECANCELED (-7) /* request was cancelled */
+
+/* Arithmetic of the MLP. Hash features, transmittance and PQ are always fp32. */
+#define VRNERF_FP32 0 /* plain fp32 on the CUDA cores */
+#define VRNERF_FP16 1 /* fp16 operands, fp32 accumulate, tcgen05 tensor cores */
+#define VRNERF_BF16 2 /* bf16 operands, fp32 accumulate, tcgen05 tensor cores */
+#define VRNERF_FP8 3  /* e4m3 hidden layers, fp16 first/last layers, fp32 accumulate */
+
+#define VRNERF_MAX_LEVELS 16
+#define VRNERF_MAX_VIEWS 256
+
+typedef struct vrnerf_field vrnerf_field;
+
+/* Field description. The MLP widths are fixed to the paper's (Sec. 6):
+ * d_hidden = 64, d_out = 16, c_hidden = 64, c_layers = 2; levels * feats
+ * must be 16 or 32 with feats = 2. Level l has resolution
+ * N_l = floor(base_res * growth^l + 1e-6) and is dense when
+ * (N_l + 1)^3 <= 2^log2_T, else hashed (instant-NGP spatial hash).
+ * Samples sit at t_i = t_near (t_far / t_near)^(i / max_steps), i <
+ * max_steps (Sec. 6: exponential distances); the march ends at the first
+ * sample outside the occupancy grid's box [aabb_min, aabb_max]. Hash-grid
+ * coordinates are (p - aabb_min) / max extent. The ray's base radius is
+ * radius_scale / fx; L* = -log_growth(2 base_res r t / max extent) +
+ * lod_bias (Eq. 3, Sec. 4.2.2). sigma = exp(o_0 + density_bias).
+ * Compositing stops after the sample where transmittance < T_eps. */
+typedef struct {
+    int32_t levels, feats, log2_T, feat_fp16;
+    double base_res, growth;
+    int32_t d_hidden, d_out, c_hidden, c_layers;
+    float aabb_min[3], aabb_max[3];
+    int32_t occ_res[3];
+    int32_t max_steps;
+    float t_near, t_far;
+    float lod_bias, T_eps, radius_scale, density_bias;
+} vrnerf_field_desc;
+
+/* Optional per-call render settings (NULL = fp32 MLP, linear output only). */
+typedef struct {
+    int32_t precision; /* VRNERF_FP32 / FP16 / BF16 / FP8 */
+    int32_t reserved;
+    float *out_pq;     /* optional [rays][3] PQ-space colour before decoding */
+    float *out_T;      /* optional [rays] final transmittance */
+    int32_t *out_n;    /* optional [rays] number of composited samples */
+    uint64_t *stats;   /* optional [4] counters, added to (not reset): evaluated
+                          samples, hash-grid levels fetched, march steps tested,
+                          rays finished */
+} vrnerf_render_opts;
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *vrnerf_last_error(void);
+
+/* Bytes of the hash grid, floats of the MLP and uint32 words of the
+ * occupancy bits that a description needs. Any output may be NULL.
+ * EINVAL for an unsupported description. */
+int vrnerf_field_sizes(const vrnerf_field_desc *desc, uint64_t *grid_bytes, uint64_t *mlp_floats,
+                       uint64_t *occ_words);
+
+/* Creates a field on the current device (Sec. 4, the model of Sec. 6).
+ * grid_host / mlp_host: initial parameters in the layouts above, or NULL to
+ * draw them from `seed` with the library's SplitMix64 stream (grid
+ * U(-1e-2, 1e-2), Xavier-uniform weights). occ_bits_host: required.
+ * *out receives the field; destroy it with vrnerf_field_destroy.
+ * Synchronous. EINVAL, ENOMEM, ECUDA. */
+int vrnerf_field_create(const vrnerf_field_desc *desc, const void *grid_host, const float *mlp_host,
+                        const uint32_t *occ_bits_host, uint64_t seed, vrnerf_field **out);
+
+/* Frees the field and all its device memory (synchronises its device). */
+void vrnerf_field_destroy(vrnerf_field *field);
+
+/* Copies the current parameters (after training) to host buffers of the
+ * sizes vrnerf_field_sizes gives; either may be NULL. Synchronous. */
+int vrnerf_field_get_params(vrnerf_field *field, void *grid_host, float *mlp_host);
+
+/* Replaces the occupancy bits (Sec. 4.3). Synchronous. */
+int vrnerf_field_set_occupancy(vrnerf_field *field, const uint32_t *occ_bits_host);
+
+/* Renders n views (Sec. 5): cameras / intrinsics in device memory,
+ * resolution_host in host memory, out = device [sum W*H][3] linear colour
+ * (1.0 = 100 cd/m^2), decoded from PQ per channel (Eq. 1-2). n <=
+ * VRNERF_MAX_VIEWS, W, H in [1, 16384], fx, fy > 0. EINVAL, ECUDA. */
+int vrnerf_render(vrnerf_field *field, const float *cameras, const float *intrinsics,
+                  const int32_t *resolution_host, int32_t n, float *out,
+                  const vrnerf_render_opts *opts, void *stream);
+
+/* vrnerf_render with every array in host memory: copies the cameras in and
+ * the image out on `stream` through the field's device staging buffers and
+ * returns after the stream has finished (synchronous). The optional outputs
+ * of opts are ignored. EINVAL, ENOMEM, ECUDA. */
+int vrnerf_render_host(vrnerf_field *field, const float *cameras_host, const float *intrinsics_host,
+                       const int32_t *resolution_host, int32_t n, float *out_host,
+                       const vrnerf_render_opts *opts, void *stream);
+
+/* Renders B explicit rays: origins / unit directions [B][3], base radii [B]
+ * (footprint radius at unit distance, Sec. 4.2.1), device memory;
+ * out [B][3] linear colour. EINVAL, ECUDA. */
+int vrnerf_render_rays(vrnerf_field *field, const float *rays_o, const float *rays_d,
+                       const float *radii, int32_t B, float *out, const vrnerf_render_opts *opts,
+                       void *stream);
+
+/* Evaluates the field at n points (Sec. 4.2.1 and Sec. 6): world positions
+ * [n][3], unit directions [n][3], footprint radii [n] in world units (t r).
+ * Outputs: sigma [n], PQ colour rgb [n][3], optional LOD-weighted features
+ * feat [n][L*F] (may be NULL). Points outside the box are clamped to the
+ * grid's edge cells. precision as in vrnerf_render_opts. EINVAL, ECUDA. */
+int vrnerf_query(vrnerf_field *field, const float *pos, const float *dir, const float *radius,
+                 int32_t n, float *sigma, float *rgb, float *feat, int32_t precision, void *stream);
+
+/* Occupancy visits (Sec. 4.3) of B explicit rays, without early
+ * termination: for ray b, the step index i and voxel index of each
+ * evaluated sample in order, into rec_i / rec_vox [B][cap] (records past
+ * cap are dropped), and count [B] = the full number. Device memory.
+ * EINVAL, ECUDA. */
+int vrnerf_debug_march(vrnerf_field *field, const float *rays_o, const float *rays_d, int32_t B,
+                       int32_t cap, int32_t *rec_i, int32_t *rec_vox, int32_t *count, void *stream);
+
+/* Hash-grid corner indices (Sec. 4, instant-NGP encoding; dense coarse
+ * levels per the supplement) of n world positions: idx [n][L][8], corner b
+ * at offset (b & 1, b >> 1 & 1, b >> 2 & 1). Device memory. EINVAL, ECUDA. */
+int vrnerf_debug_corners(vrnerf_field *field, const float *pos, int32_t n, uint32_t *idx,
+                         void *stream);
+
+/* Training (Sec. 6; Sec. 4.1 and supplement "Loss Design"): renders B
+ * explicit rays, and computes loss = mean over rays and channels of
+ * |C_pq - PQ(target / 100)| and its gradient with respect to every hash-grid
+ * entry and MLP weight into the field's gradient buffers (overwritten).
+ * target_linear [B][3] device memory. loss_host (may be NULL) receives the
+ * loss; when it is non-NULL the call synchronises `stream`. EINVAL, ECUDA. */
+int vrnerf_backward(vrnerf_field *field, const float *rays_o, const float *rays_d,
+                    const float *radii, const float *target_linear, int32_t B, float *loss_host,
+                    void *stream);
+
+/* Copies the gradient buffers of the last vrnerf_backward to the host:
+ * grid_grad_host [L][T][F] fp32, mlp_grad_host fp32 (either may be NULL).
+ * Synchronous. */
+int vrnerf_field_get_grads(vrnerf_field *field, float *grid_grad_host, float *mlp_grad_host);
+
+/* One Adam step (Sec. 6: beta1 = 0.9, beta2 = 0.99, eps = 1e-15) on all
+ * parameters from the gradient buffers; learning rate lr_grid for the hash
+ * grid and lr_mlp for the MLP weights (paper: 0.01 and 0.005). The field
+ * keeps fp32 master weights and the first and second moments. */
+int vrnerf_adam_step(vrnerf_field *field, float lr_grid, float lr_mlp, void *stream);
+
+/* vrnerf_backward followed by vrnerf_adam_step. */
+int vrnerf_train_step(vrnerf_field *field, const float *rays_o, const float *rays_d,
+                      const float *radii, const float *target_linear, int32_t B, float lr_grid,
+                      float lr_mlp, float *loss_host, void *stream);
+
+/* Loads a gradient buffer from the host into the field (for testing the
+ * optimiser on given gradients). Synchronous. */
+int vrnerf_field_set_grads(vrnerf_field *field, const float *grid_grad_host,
+                           const float *mlp_grad_host);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VRNERF_H */

@@ -1,0 +1,276 @@
+// common.cuh -- device-side building blocks of the per-ray field renderer.
+//
+// Geometry that decides integers (ray directions, sample positions, occupancy
+// voxels, hash-grid corners) is computed in fp32 with each operation rounded
+// on its own (__fadd_rn / __fmul_rn / __fdiv_rn / __fsqrt_rn): nvcc would
+// otherwise contract a*b+c into one FMA and change which voxel or corner a
+// sample lands in. Everything continuous (LOD weights, interpolation, MLP,
+// compositing, PQ) uses ordinary fp32 arithmetic and CUDA's math functions.
+#pragma once
+#include <cstdint>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+
+namespace vrn {
+
+constexpr int kMaxLevels = 16;
+constexpr int kMaxViews = 256;
+constexpr int kTileW = 8;   // rays of one warp cover an 8 x 4 pixel tile
+constexpr int kTileH = 4;
+
+// Everything a kernel needs to read the field; passed by value.
+struct FieldView {
+    const void *grid;       // [L][T][F] fp32 or fp16
+    const float *mlp;       // fp32 W1..W5, [out][in]
+    const uint32_t *occ;    // occupancy bits
+    const float *t_tab;     // sample distances t_0..t_S
+    int L, F, d_in, log2_T, feat_fp16, S;
+    uint32_t T_mask;
+    int N[kMaxLevels];
+    uint32_t dense_mask;
+    float mn[3], inv_cell[3], res_f[3];
+    int res[3];
+    float inv_ext;
+    float two_s, inv_ln_f, lod_bias, T_eps, density_bias, radius_scale;
+    int n_mlp;
+};
+
+// One launch's rays: either camera views (pixels in 8x4 tiles) or explicit arrays.
+struct ViewInfo {
+    int W, H, tiles_x;
+    int slot_begin;       // first ray slot of this view
+    long long pix_begin;  // first output pixel of this view
+};
+
+struct RaySource {
+    // camera mode
+    const float *c2w;     // [n][12]
+    const float *K;       // [n][4]
+    int n_views;
+    ViewInfo views[kMaxViews];
+    // explicit mode (n_views == 0)
+    const float *o, *d, *r;
+    long long n_slots;    // ray slots to process (camera mode: padded to whole tiles)
+};
+
+struct RenderOut {
+    float *lin;   // [rays][3]
+    float *pq;    // optional
+    float *T;     // optional
+    int *n;       // optional
+    unsigned long long *stats;  // optional [4]: samples, levels fetched, steps tested, rays
+};
+
+// Warp-aggregated add of per-thread counters into stats (all lanes call).
+__device__ __forceinline__ void add_stats(unsigned long long *stats, unsigned a, unsigned b,
+                                          unsigned c, unsigned d) {
+    if (!stats) return;
+    unsigned long long v[4] = {a, b, c, d};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        unsigned long long x = v[k];
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) x += __shfl_xor_sync(0xffffffffu, x, s);
+        if ((threadIdx.x & 31) == 0 && x) atomicAdd(stats + k, x);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// fp32 geometry with separate rounding
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void camera_ray(const float *__restrict__ c2w, const float *__restrict__ K,
+                                           int u, int v, float o[3], float d[3]) {
+    float x = __fdiv_rn(__fsub_rn(__fadd_rn((float)u, 0.5f), K[2]), K[0]);
+    float y = __fdiv_rn(__fsub_rn(__fadd_rn((float)v, 0.5f), K[3]), K[1]);
+    float n = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)), 1.0f));
+    float cx = __fdiv_rn(x, n), cy = __fdiv_rn(y, n), cz = __fdiv_rn(1.0f, n);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        d[k] = __fadd_rn(__fadd_rn(__fmul_rn(c2w[4 * k + 0], cx), __fmul_rn(c2w[4 * k + 1], cy)),
+                         __fmul_rn(c2w[4 * k + 2], cz));
+        o[k] = c2w[4 * k + 3];
+    }
+}
+
+// p = o + t d and its occupancy voxel; false once the sample leaves the grid.
+__device__ __forceinline__ bool sample_voxel(const FieldView &f, const float o[3], const float d[3],
+                                             float t, float p[3], int &vox) {
+    int v[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        p[k] = __fadd_rn(o[k], __fmul_rn(t, d[k]));
+        float g = __fmul_rn(__fsub_rn(p[k], f.mn[k]), f.inv_cell[k]);
+        if (!(g >= 0.0f) || !(g < f.res_f[k])) return false;
+        v[k] = (int)g;
+    }
+    vox = v[0] + f.res[0] * (v[1] + f.res[1] * v[2]);
+    return true;
+}
+
+__device__ __forceinline__ bool occupied(const uint32_t *__restrict__ occ, int vox) {
+    return (__ldg(occ + (vox >> 5)) >> (vox & 31)) & 1u;
+}
+
+// Corner indices of level l (corner b at offset (b&1, b>>1&1, b>>2&1)) and
+// the position inside the cell.
+__device__ __forceinline__ void level_corners(const FieldView &f, int l, const float p[3],
+                                              uint32_t idx[8], float fr[3]) {
+    const int N = f.N[l];
+    int c0[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float ph = __fmul_rn(__fsub_rn(p[k], f.mn[k]), f.inv_ext);
+        float x = __fmul_rn(ph, (float)N);
+        int c = (int)floorf(x);
+        c = c < 0 ? 0 : (c > N - 1 ? N - 1 : c);
+        c0[k] = c;
+        fr[k] = __fsub_rn(x, (float)c);
+    }
+    if ((f.dense_mask >> l) & 1u) {
+        const uint32_t n1 = (uint32_t)N + 1u;
+#pragma unroll
+        for (int b = 0; b < 8; ++b)
+            idx[b] = (uint32_t)(c0[0] + (b & 1)) +
+                     n1 * ((uint32_t)(c0[1] + ((b >> 1) & 1)) + n1 * (uint32_t)(c0[2] + ((b >> 2) & 1)));
+    } else {
+        // instant-NGP spatial hash, primes (1, 2654435761, 805459861)
+        const uint32_t hx0 = (uint32_t)c0[0], hx1 = hx0 + 1u;
+        const uint32_t hy0 = (uint32_t)c0[1] * 2654435761u, hy1 = ((uint32_t)c0[1] + 1u) * 2654435761u;
+        const uint32_t hz0 = (uint32_t)c0[2] * 805459861u, hz1 = ((uint32_t)c0[2] + 1u) * 805459861u;
+#pragma unroll
+        for (int b = 0; b < 8; ++b)
+            idx[b] = ((b & 1 ? hx1 : hx0) ^ (b & 2 ? hy1 : hy0) ^ (b & 4 ? hz1 : hz0)) & f.T_mask;
+    }
+}
+
+// Eq. 3 as a clamp: w_l = clamp(L* - l + 1, 0, 1).
+__device__ __forceinline__ float lod_star(const FieldView &f, float r_norm) {
+    return -logf(f.two_s * r_norm) * f.inv_ln_f + f.lod_bias;
+}
+__device__ __forceinline__ float lod_weight(float Lstar, int l) {
+    return fminf(fmaxf(Lstar - (float)l + 1.0f, 0.0f), 1.0f);
+}
+
+// ---------------------------------------------------------------------------
+// PQ (Eq. 1-2), fp32
+// ---------------------------------------------------------------------------
+constexpr float kPqM1 = 1305.0f / 8192.0f;
+constexpr float kPqM2 = 2523.0f / 32.0f;
+constexpr float kPqInvM1 = 8192.0f / 1305.0f;
+constexpr float kPqInvM2 = 32.0f / 2523.0f;
+constexpr float kPqC1 = 107.0f / 128.0f;
+constexpr float kPqC2 = 2413.0f / 128.0f;
+constexpr float kPqC3 = 2392.0f / 128.0f;
+
+__device__ __forceinline__ float pq_to_linear(float E) {
+    E = fminf(fmaxf(E, 0.0f), 1.0f);
+    float e = powf(E, kPqInvM2);
+    float num = fmaxf(e - kPqC1, 0.0f);
+    return 100.0f * powf(num / (kPqC2 - kPqC3 * e), kPqInvM1);
+}
+
+__device__ __forceinline__ float linear_to_pq(float c) {
+    float Y = fminf(fmaxf(c * 0.01f, 0.0f), 1.0f);
+    float ym = powf(Y, kPqM1);
+    return powf((kPqC1 + kPqC2 * ym) / (1.0f + kPqC3 * ym), kPqM2);
+}
+
+// ---------------------------------------------------------------------------
+// Real spherical harmonics, bands 0..3, Condon-Shortley phase, index l^2+l+m.
+// Coefficients: sqrt(2) N_lm (-1)^m d^m P_l / dz^m, N_lm^2 = (2l+1)/(4 pi)
+// (l-m)!/(l+m)!, times Re / Im of (x + i y)^m.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void sh16(float x, float y, float z, float s[16]) {
+    const float xx = x * x, yy = y * y, zz = z * z;
+    s[0] = 0.28209479177387814f;                 // 1 / (2 sqrt(pi))
+    s[1] = -0.48860251190291987f * y;            // sqrt(3 / 4pi)
+    s[2] = 0.48860251190291987f * z;
+    s[3] = -0.48860251190291987f * x;
+    s[4] = 1.0925484305920792f * x * y;          // sqrt(15 / 4pi)
+    s[5] = -1.0925484305920792f * y * z;
+    s[6] = 0.31539156525252005f * (3.0f * zz - 1.0f);  // sqrt(5 / 16pi)
+    s[7] = -1.0925484305920792f * x * z;
+    s[8] = 0.54627421529603959f * (xx - yy);     // sqrt(15 / 16pi)
+    s[9] = -0.59004358992664352f * y * (3.0f * xx - yy);   // sqrt(35 / 32pi)
+    s[10] = 2.8906114426405538f * x * y * z;     // sqrt(105 / 4pi)
+    s[11] = -0.45704579946446572f * y * (5.0f * zz - 1.0f);  // sqrt(21 / 32pi)
+    s[12] = 0.37317633259011540f * z * (5.0f * zz - 3.0f);  // sqrt(7 / 16pi)
+    s[13] = -0.45704579946446572f * x * (5.0f * zz - 1.0f);
+    s[14] = 1.4453057213202769f * z * (xx - yy); // sqrt(105 / 16pi)
+    s[15] = -0.59004358992664352f * x * (xx - 3.0f * yy);
+}
+
+// ---------------------------------------------------------------------------
+// Ray slots: camera mode maps slot -> (view, pixel) in 8x4 tiles.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool slot_ray(const RaySource &src, const FieldView &f, long long slot,
+                                         float o[3], float d[3], float &r, long long &pix) {
+    if (src.n_views == 0) {
+        pix = slot;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            o[k] = __ldg(src.o + 3 * slot + k);
+            d[k] = __ldg(src.d + 3 * slot + k);
+        }
+        r = __ldg(src.r + slot);
+        return true;
+    }
+    int v = 0;
+    while (v + 1 < src.n_views && slot >= src.views[v + 1].slot_begin) ++v;
+    const ViewInfo &vi = src.views[v];
+    int q = (int)(slot - vi.slot_begin);
+    int tile = q >> 5, lane = q & 31;
+    int px = (tile % vi.tiles_x) * kTileW + (lane & (kTileW - 1));
+    int py = (tile / vi.tiles_x) * kTileH + (lane >> 3);
+    if (px >= vi.W || py >= vi.H) return false;
+    const float *K = src.K + 4 * v;
+    camera_ray(src.c2w + 12 * v, K, px, py, o, d);
+    r = __fdiv_rn(f.radius_scale, __ldg(K));
+    pix = vi.pix_begin + (long long)py * vi.W + px;
+    return true;
+}
+
+__device__ __forceinline__ float2 load_feat(const FieldView &f, int l, uint32_t idx) {
+    size_t e = (size_t)l * (f.T_mask + 1u) + idx;
+    if (f.feat_fp16) {
+        uint32_t bits = __ldg(reinterpret_cast<const unsigned int *>(f.grid) + e);
+        __half2 h = *reinterpret_cast<__half2 *>(&bits);
+        return __half22float2(h);
+    }
+    return __ldg(reinterpret_cast<const float2 *>(f.grid) + e);
+}
+
+// LOD-weighted hash-grid features of one sample (Eq. 3): levels with zero
+// weight are not fetched and give zeros.
+template <int L>
+__device__ __forceinline__ int gather_features(const FieldView &f, const float p[3], float r_norm,
+                                               float feat[2 * L]) {
+    const float Ls = lod_star(f, r_norm);
+    int fetched = 0;
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+        const float w = lod_weight(Ls, l);
+        float a0 = 0.0f, a1 = 0.0f;
+        if (w > 0.0f) {
+            ++fetched;
+            uint32_t idx[8];
+            float fr[3];
+            level_corners(f, l, p, idx, fr);
+            float2 e[8];
+#pragma unroll
+            for (int b = 0; b < 8; ++b) e[b] = load_feat(f, l, idx[b]);
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                float cw = (b & 1 ? fr[0] : 1.0f - fr[0]) * (b & 2 ? fr[1] : 1.0f - fr[1]) *
+                           (b & 4 ? fr[2] : 1.0f - fr[2]);
+                a0 += cw * e[b].x;
+                a1 += cw * e[b].y;
+            }
+        }
+        feat[2 * l] = w * a0;
+        feat[2 * l + 1] = w * a1;
+    }
+    return fetched;
+}
+
+}  // namespace vrn

@@ -1,0 +1,365 @@
+// render_simt.cu -- plain fp32 renderer: the whole per-ray path in one
+// persistent kernel with the MLP on the CUDA cores (the fp32 baseline).
+//
+// Each thread owns one ray slot. A round has two phases:
+//  1. march: every thread advances its ray through the exponential samples
+//     (Sec. 6) until it reaches a sample in an occupied voxel (Sec. 4.3) or
+//     the ray ends; finished slots take new rays from a global counter, one
+//     atomic per warp;
+//  2. evaluate: threads holding a sample gather the LOD-weighted hash-grid
+//     features (Sec. 4.2.1, Eq. 3), run the density and colour MLPs (Sec. 6)
+//     with weights in shared memory, and composite front to back, stopping
+//     when transmittance drops below T_eps; the output is PQ-decoded
+//     (Eq. 1-2).
+// Phase 2 runs with the warp converged, so the MLP's FMAs are not serialised
+// against the march.
+#include "internal.h"
+
+namespace vrn {
+
+constexpr int kSimtThreads = 128;
+constexpr int kChunk = 32;  // march steps between refill points
+
+// Shared-memory weight layout (SIMT-friendly, float4 rows):
+// W1 [64][D], W2^T [64][16], W3 [64][32], W4 [64][64], W5^T [64][4]
+template <int D>
+struct SimtW {
+    static constexpr int oW1 = 0;
+    static constexpr int oW2T = oW1 + 64 * D;
+    static constexpr int oW3 = oW2T + 64 * 16;
+    static constexpr int oW4 = oW3 + 64 * 32;
+    static constexpr int oW5T = oW4 + 64 * 64;
+    static constexpr int size = oW5T + 64 * 4;
+};
+
+template <int D>
+__device__ void load_weights_simt(const float *__restrict__ mlp, float *s) {
+    using W = SimtW<D>;
+    for (int i = threadIdx.x; i < 64 * D; i += blockDim.x) s[W::oW1 + i] = mlp[i];
+    const float *W2 = mlp + 64 * D;
+    for (int i = threadIdx.x; i < 64 * 16; i += blockDim.x) s[W::oW2T + i] = W2[(i & 15) * 64 + (i >> 4)];
+    const float *W3 = W2 + 16 * 64;
+    for (int i = threadIdx.x; i < 64 * 32; i += blockDim.x) s[W::oW3 + i] = W3[i];
+    const float *W4 = W3 + 64 * 32;
+    for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) s[W::oW4 + i] = W4[i];
+    const float *W5 = W4 + 64 * 64;
+    for (int i = threadIdx.x; i < 64 * 4; i += blockDim.x) {
+        int j = i >> 2, c = i & 3;
+        s[W::oW5T + i] = c < 3 ? W5[c * 64 + j] : 0.0f;
+    }
+}
+
+// Density MLP (D -> 64 -> 16, ReLU), sigma = exp(o_0 + bias); colour MLP
+// ([o, SH(d)] 32 -> 64 -> 64 -> 3, ReLU) and sigmoid to PQ colour.
+template <int D>
+__device__ __forceinline__ void mlp_simt(const float *__restrict__ s, const float feat[D],
+                                         const float dir[3], float density_bias, float &sigma,
+                                         float rgb[3], float o_out[16] = nullptr) {
+    using W = SimtW<D>;
+    float o[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) o[i] = 0.0f;
+#pragma unroll 4
+    for (int j = 0; j < 64; ++j) {
+        const float4 *w = reinterpret_cast<const float4 *>(s + W::oW1 + j * D);
+        float a = 0.0f;
+#pragma unroll
+        for (int k = 0; k < D / 4; ++k) {
+            float4 q = w[k];
+            a = fmaf(q.x, feat[4 * k], a);
+            a = fmaf(q.y, feat[4 * k + 1], a);
+            a = fmaf(q.z, feat[4 * k + 2], a);
+            a = fmaf(q.w, feat[4 * k + 3], a);
+        }
+        a = fmaxf(a, 0.0f);
+        const float4 *w2 = reinterpret_cast<const float4 *>(s + W::oW2T + j * 16);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float4 q = w2[k];
+            o[4 * k] = fmaf(q.x, a, o[4 * k]);
+            o[4 * k + 1] = fmaf(q.y, a, o[4 * k + 1]);
+            o[4 * k + 2] = fmaf(q.z, a, o[4 * k + 2]);
+            o[4 * k + 3] = fmaf(q.w, a, o[4 * k + 3]);
+        }
+    }
+    sigma = expf(o[0] + density_bias);
+    if (o_out) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) o_out[i] = o[i];
+    }
+    float x[32];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) x[i] = o[i];
+    sh16(dir[0], dir[1], dir[2], x + 16);
+    float h1[64];
+#pragma unroll
+    for (int j = 0; j < 64; ++j) {
+        const float4 *w = reinterpret_cast<const float4 *>(s + W::oW3 + j * 32);
+        float a = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            float4 q = w[k];
+            a = fmaf(q.x, x[4 * k], a);
+            a = fmaf(q.y, x[4 * k + 1], a);
+            a = fmaf(q.z, x[4 * k + 2], a);
+            a = fmaf(q.w, x[4 * k + 3], a);
+        }
+        h1[j] = fmaxf(a, 0.0f);
+    }
+    float z0 = 0.0f, z1 = 0.0f, z2 = 0.0f;
+#pragma unroll 2
+    for (int j = 0; j < 64; ++j) {
+        const float4 *w = reinterpret_cast<const float4 *>(s + W::oW4 + j * 64);
+        float a = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            float4 q = w[k];
+            a = fmaf(q.x, h1[4 * k], a);
+            a = fmaf(q.y, h1[4 * k + 1], a);
+            a = fmaf(q.z, h1[4 * k + 2], a);
+            a = fmaf(q.w, h1[4 * k + 3], a);
+        }
+        a = fmaxf(a, 0.0f);
+        float4 w5 = reinterpret_cast<const float4 *>(s + W::oW5T)[j];
+        z0 = fmaf(w5.x, a, z0);
+        z1 = fmaf(w5.y, a, z1);
+        z2 = fmaf(w5.z, a, z2);
+    }
+    rgb[0] = 1.0f / (1.0f + expf(-z0));
+    rgb[1] = 1.0f / (1.0f + expf(-z1));
+    rgb[2] = 1.0f / (1.0f + expf(-z2));
+}
+
+__device__ __forceinline__ void finish_ray(const RenderOut &out, long long pix, const float C[3],
+                                           float T, int n) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        out.lin[3 * pix + c] = pq_to_linear(C[c]);
+        if (out.pq) out.pq[3 * pix + c] = C[c];
+    }
+    if (out.T) out.T[pix] = T;
+    if (out.n) out.n[pix] = n;
+}
+
+template <int L>
+__global__ void __launch_bounds__(kSimtThreads)
+render_simt_kernel(const FieldView f, const RaySource src, const RenderOut out,
+                   unsigned long long *__restrict__ counter) {
+    constexpr int D = 2 * L;
+    extern __shared__ float4 smem4[];
+    float *sW = reinterpret_cast<float *>(smem4);
+    float *sT = sW + SimtW<D>::size;
+    load_weights_simt<D>(f.mlp, sW);
+    for (int i = threadIdx.x; i <= f.S; i += blockDim.x) sT[i] = f.t_tab[i];
+    __syncthreads();
+
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    long long ray = -1, pix = 0;
+    bool exhausted = false;
+    float o[3] = {0, 0, 0}, d[3] = {0, 0, 1}, r = 0.0f, T = 1.0f, C[3] = {0, 0, 0};
+    int step = 0, n_eval = 0;
+    unsigned st_samples = 0, st_levels = 0, st_steps = 0, st_rays = 0;
+
+    while (true) {
+        bool have = false;
+        float p[3];
+        // ---- phase 1: march to the next occupied sample, refilling slots ----
+        while (true) {
+            const bool need = ray < 0 && !exhausted;
+            const unsigned m = __ballot_sync(FULL, need);
+            if (m) {
+                const int leader = __ffs(m) - 1;
+                unsigned long long base = 0;
+                if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(m));
+                base = __shfl_sync(FULL, base, leader);
+                if (need) {
+                    long long slot = (long long)base + __popc(m & ((1u << lane) - 1u));
+                    if (slot >= src.n_slots) {
+                        exhausted = true;
+                    } else if (slot_ray(src, f, slot, o, d, r, pix)) {
+                        ray = slot;
+                        step = 0;
+                        n_eval = 0;
+                        T = 1.0f;
+                        C[0] = C[1] = C[2] = 0.0f;
+                    }
+                }
+            }
+            if (ray >= 0 && !have) {
+                for (int k = 0; k < kChunk; ++k) {
+                    int vox;
+                    if (step >= f.S || !sample_voxel(f, o, d, sT[step], p, vox)) {
+                        finish_ray(out, pix, C, T, n_eval);
+                        ray = -1;
+                        ++st_rays;
+                        break;
+                    }
+                    ++st_steps;
+                    if (occupied(f.occ, vox)) {
+                        have = true;
+                        break;
+                    }
+                    ++step;
+                }
+            }
+            if (__all_sync(FULL, have || exhausted)) break;
+        }
+        if (!__any_sync(FULL, have)) break;
+        // ---- phase 2: features, MLPs, compositing ----
+        if (have) {
+            const float t = sT[step], delta = sT[step + 1] - t;
+            const float r_norm = t * r * f.inv_ext;
+            float feat[D];
+            st_levels += gather_features<L>(f, p, r_norm, feat);
+            ++st_samples;
+            float sigma, rgb[3];
+            mlp_simt<D>(sW, feat, d, f.density_bias, sigma, rgb);
+            const float sd = sigma * delta;
+            const float w = T * (-expm1f(-sd));
+            C[0] += w * rgb[0];
+            C[1] += w * rgb[1];
+            C[2] += w * rgb[2];
+            T *= expf(-sd);
+            ++n_eval;
+            ++step;
+            if (T < f.T_eps) {
+                finish_ray(out, pix, C, T, n_eval);
+                ray = -1;
+                ++st_rays;
+            }
+        }
+    }
+    add_stats(out.stats, st_samples, st_levels, st_steps, st_rays);
+}
+
+template <int L>
+__global__ void __launch_bounds__(kSimtThreads)
+query_simt_kernel(const FieldView f, const float *__restrict__ pos, const float *__restrict__ dir,
+                  const float *__restrict__ radius, int n, float *__restrict__ sigma_out,
+                  float *__restrict__ rgb_out, float *__restrict__ feat_out) {
+    constexpr int D = 2 * L;
+    extern __shared__ float4 smem4[];
+    float *sW = reinterpret_cast<float *>(smem4);
+    load_weights_simt<D>(f.mlp, sW);
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float p[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
+    float dd[3] = {dir[3 * i], dir[3 * i + 1], dir[3 * i + 2]};
+    float feat[D];
+    gather_features<L>(f, p, radius[i] * f.inv_ext, feat);
+    float sigma, rgb[3];
+    mlp_simt<D>(sW, feat, dd, f.density_bias, sigma, rgb);
+    sigma_out[i] = sigma;
+    for (int c = 0; c < 3; ++c) rgb_out[3 * i + c] = rgb[c];
+    if (feat_out)
+        for (int k = 0; k < D; ++k) feat_out[(long long)i * D + k] = feat[k];
+}
+
+__global__ void debug_march_kernel(const FieldView f, const float *__restrict__ o_in,
+                                   const float *__restrict__ d_in, int B, int cap,
+                                   int *__restrict__ rec_i, int *__restrict__ rec_vox,
+                                   int *__restrict__ count) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    float o[3] = {o_in[3 * b], o_in[3 * b + 1], o_in[3 * b + 2]};
+    float d[3] = {d_in[3 * b], d_in[3 * b + 1], d_in[3 * b + 2]};
+    int n = 0;
+    for (int i = 0; i < f.S; ++i) {
+        float p[3];
+        int vox;
+        if (!sample_voxel(f, o, d, __ldg(f.t_tab + i), p, vox)) break;
+        if (!occupied(f.occ, vox)) continue;
+        if (n < cap) {
+            rec_i[(long long)b * cap + n] = i;
+            rec_vox[(long long)b * cap + n] = vox;
+        }
+        ++n;
+    }
+    count[b] = n;
+}
+
+__global__ void debug_corners_kernel(const FieldView f, const float *__restrict__ pos, int n,
+                                     uint32_t *__restrict__ idx) {
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (long long)n * f.L) return;
+    const int i = (int)(q / f.L), l = (int)(q % f.L);
+    float p[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
+    uint32_t id[8];
+    float fr[3];
+    level_corners(f, l, p, id, fr);
+    for (int b = 0; b < 8; ++b) idx[q * 8 + b] = id[b];
+}
+
+// ---------------------------------------------------------------------------
+// launches
+// ---------------------------------------------------------------------------
+size_t simt_smem_bytes(const FieldView &f) {
+    const int wsize = f.L == 8 ? SimtW<16>::size : SimtW<32>::size;
+    return sizeof(float) * (size_t)(wsize + f.S + 1);
+}
+
+template <int L>
+static cudaError_t render_simt_t(const FieldView &f, const RaySource &src, const RenderOut &out,
+                                 unsigned long long *counter, cudaStream_t st) {
+    static int blocks_per_sm = 0;
+    static size_t configured_smem = 0;
+    const size_t smem = simt_smem_bytes(f);
+    auto kern = render_simt_kernel<L>;
+    if (smem != configured_smem) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, kSimtThreads, smem);
+        if (e != cudaSuccess) return e;
+        if (blocks_per_sm < 1) blocks_per_sm = 1;
+        configured_smem = smem;
+    }
+    long long want = (src.n_slots + kSimtThreads - 1) / kSimtThreads;
+    long long grid = (long long)num_sms() * blocks_per_sm;
+    if (want < grid) grid = want;
+    if (grid < 1) grid = 1;
+    kern<<<(unsigned)grid, kSimtThreads, smem, st>>>(f, src, out, counter);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_render_simt(const FieldView &f, const RaySource &src, const RenderOut &out,
+                               unsigned long long *counter, cudaStream_t st) {
+    return f.L == 8 ? render_simt_t<8>(f, src, out, counter, st)
+                    : render_simt_t<16>(f, src, out, counter, st);
+}
+
+template <int L>
+static cudaError_t query_simt_t(const FieldView &f, const float *pos, const float *dir,
+                                const float *radius, int n, float *sigma, float *rgb, float *feat,
+                                cudaStream_t st) {
+    const size_t smem = sizeof(float) * SimtW<2 * L>::size;
+    auto kern = query_simt_kernel<L>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(n + kSimtThreads - 1) / kSimtThreads, kSimtThreads, smem, st>>>(f, pos, dir, radius, n,
+                                                                             sigma, rgb, feat);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_query_simt(const FieldView &f, const float *pos, const float *dir,
+                              const float *radius, int n, float *sigma, float *rgb, float *feat,
+                              cudaStream_t st) {
+    return f.L == 8 ? query_simt_t<8>(f, pos, dir, radius, n, sigma, rgb, feat, st)
+                    : query_simt_t<16>(f, pos, dir, radius, n, sigma, rgb, feat, st);
+}
+
+cudaError_t launch_debug_march(const FieldView &f, const float *o, const float *d, int B, int cap,
+                               int *rec_i, int *rec_vox, int *count, cudaStream_t st) {
+    debug_march_kernel<<<(B + 127) / 128, 128, 0, st>>>(f, o, d, B, cap, rec_i, rec_vox, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_debug_corners(const FieldView &f, const float *pos, int n, uint32_t *idx,
+                                 cudaStream_t st) {
+    long long q = (long long)n * f.L;
+    debug_corners_kernel<<<(unsigned)((q + 127) / 128), 128, 0, st>>>(f, pos, n, idx);
+    return cudaGetLastError();
+}
+
+}  // namespace vrn

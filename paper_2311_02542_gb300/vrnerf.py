@@ -1,0 +1,319 @@
+"""Thin Python binding of the C ABI in include/vrnerf.h.
+
+Argument marshalling only: every step of rendering and training runs in the
+CUDA library. PyTorch supplies device memory and streams. Importing this
+module loads ``_build/libvrnerf.so`` and raises if it has not been built
+(``python -m paper_2311_02542_gb300.build``); there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+FP32, FP16, BF16, FP8 = 0, 1, 2, 3
+PRECISIONS = {"fp32": FP32, "fp16": FP16, "bf16": BF16, "fp8": FP8}
+OK, EINVAL, ENOMEM, ECUDA, ETIMEDOUT, EBUSY, ENOTFOUND, ECANCELED = 0, -1, -2, -3, -4, -5, -6, -7
+
+
+class VrnerfError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"vrnerf error {code}: {msg}")
+        self.code = code
+
+
+class FieldDesc(ctypes.Structure):
+    _fields_ = [
+        ("levels", ctypes.c_int32), ("feats", ctypes.c_int32), ("log2_T", ctypes.c_int32),
+        ("feat_fp16", ctypes.c_int32),
+        ("base_res", ctypes.c_double), ("growth", ctypes.c_double),
+        ("d_hidden", ctypes.c_int32), ("d_out", ctypes.c_int32), ("c_hidden", ctypes.c_int32),
+        ("c_layers", ctypes.c_int32),
+        ("aabb_min", ctypes.c_float * 3), ("aabb_max", ctypes.c_float * 3),
+        ("occ_res", ctypes.c_int32 * 3),
+        ("max_steps", ctypes.c_int32),
+        ("t_near", ctypes.c_float), ("t_far", ctypes.c_float),
+        ("lod_bias", ctypes.c_float), ("T_eps", ctypes.c_float),
+        ("radius_scale", ctypes.c_float), ("density_bias", ctypes.c_float),
+    ]
+
+
+class RenderOpts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("out_pq", ctypes.c_void_p), ("out_T", ctypes.c_void_p), ("out_n", ctypes.c_void_p),
+                ("stats", ctypes.c_void_p)]
+
+
+_VP = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_F = ctypes.c_float
+_SIGS = {
+    "vrnerf_last_error": (ctypes.c_char_p, []),
+    "vrnerf_field_sizes": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "vrnerf_field_create": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_uint64, _VP]),
+    "vrnerf_field_destroy": (None, [_VP]),
+    "vrnerf_field_get_params": (ctypes.c_int, [_VP, _VP, _VP]),
+    "vrnerf_field_set_occupancy": (ctypes.c_int, [_VP, _VP]),
+    "vrnerf_render": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP]),
+    "vrnerf_render_host": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP]),
+    "vrnerf_render_rays": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP]),
+    "vrnerf_query": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP, _I32, _VP]),
+    "vrnerf_debug_march": (ctypes.c_int, [_VP, _VP, _VP, _I32, _I32, _VP, _VP, _VP, _VP]),
+    "vrnerf_debug_corners": (ctypes.c_int, [_VP, _VP, _I32, _VP, _VP]),
+    "vrnerf_backward": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _I32, _VP, _VP]),
+    "vrnerf_field_get_grads": (ctypes.c_int, [_VP, _VP, _VP]),
+    "vrnerf_field_set_grads": (ctypes.c_int, [_VP, _VP, _VP]),
+    "vrnerf_adam_step": (ctypes.c_int, [_VP, _F, _F, _VP]),
+    "vrnerf_train_step": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _I32, _F, _F, _VP, _VP]),
+}
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Loads the CUDA library (torch is imported first so both share one CUDA runtime)."""
+    global _lib
+    if _lib is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library {path} is not built; run "
+                               "`python -m paper_2311_02542_gb300.build` (no CPU fallback exists)")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name, None)
+            if fn is None:
+                continue
+            fn.restype, fn.argtypes = res, args
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return load().vrnerf_last_error().decode()
+
+
+def _check(rc):
+    if rc != OK:
+        raise VrnerfError(rc, last_error())
+
+
+def desc(cfg) -> FieldDesc:
+    d = FieldDesc()
+    d.levels, d.feats, d.log2_T = cfg.levels, cfg.feats, cfg.log2_T
+    d.feat_fp16 = int(cfg.feat_fp16)
+    d.base_res, d.growth = cfg.base_res, cfg.growth
+    d.d_hidden, d.d_out, d.c_hidden, d.c_layers = cfg.d_hidden, cfg.d_out, cfg.c_hidden, cfg.c_layers
+    d.aabb_min[:] = list(cfg.aabb_min)
+    d.aabb_max[:] = list(cfg.aabb_max)
+    d.occ_res[:] = list(cfg.occ_res)
+    d.max_steps = cfg.max_steps
+    d.t_near, d.t_far = cfg.t_near, cfg.t_far
+    d.lod_bias, d.T_eps = cfg.lod_bias, cfg.T_eps
+    d.radius_scale, d.density_bias = cfg.radius_scale, cfg.density_bias
+    return d
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        assert t.is_contiguous(), "tensors passed to the library must be contiguous"
+        return ctypes.c_void_p(t.data_ptr())
+    if isinstance(t, np.ndarray):
+        assert t.flags.c_contiguous
+        return ctypes.c_void_p(t.ctypes.data)
+    raise TypeError(type(t))
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev(t, dtype=torch.float32):
+    assert isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()
+    return t
+
+
+class Field:
+    """Owns a vrnerf_field* (device parameters, occupancy and scratch)."""
+
+    def __init__(self, cfg, grid=None, mlp=None, occ_bits=None, seed=0):
+        L = load()
+        self.cfg = cfg
+        self._desc = desc(cfg)
+        h = ctypes.c_void_p()
+        g = None if grid is None else np.ascontiguousarray(grid)
+        m = None if mlp is None else np.ascontiguousarray(mlp, dtype=np.float32)
+        o = np.ascontiguousarray(occ_bits, dtype=np.uint32)
+        if g is not None:
+            want = np.float16 if cfg.feat_fp16 else np.float32
+            assert g.dtype == want and g.size == cfg.levels * cfg.T * cfg.feats
+        _check(L.vrnerf_field_create(ctypes.byref(self._desc), _ptr(g), _ptr(m), _ptr(o),
+                                     ctypes.c_uint64(seed), ctypes.byref(h)))
+        self.h = h
+        self.n_rays_last = 0
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h and _lib is not None:
+            _lib.vrnerf_field_destroy(h)
+            self.h = None
+
+    def close(self):
+        self.__del__()
+
+
+def vrnerf_field_sizes(cfg):
+    gb, mf, ow = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    d = desc(cfg)
+    _check(load().vrnerf_field_sizes(ctypes.byref(d), ctypes.byref(gb), ctypes.byref(mf), ctypes.byref(ow)))
+    return gb.value, mf.value, ow.value
+
+
+def vrnerf_field_create(cfg, grid=None, mlp=None, occ_bits=None, seed=0) -> Field:
+    return Field(cfg, grid, mlp, occ_bits, seed)
+
+
+def vrnerf_field_destroy(field: Field):
+    field.close()
+
+
+def vrnerf_field_get_params(field: Field):
+    cfg = field.cfg
+    g = np.empty((cfg.levels, cfg.T, cfg.feats), np.float16 if cfg.feat_fp16 else np.float32)
+    m = np.empty(cfg.n_mlp(), np.float32)
+    _check(load().vrnerf_field_get_params(field.h, _ptr(g), _ptr(m)))
+    return g, m
+
+
+def vrnerf_field_set_occupancy(field: Field, occ_bits):
+    o = np.ascontiguousarray(occ_bits, dtype=np.uint32)
+    _check(load().vrnerf_field_set_occupancy(field.h, _ptr(o)))
+
+
+def _opts(precision, out_pq=None, out_T=None, out_n=None, stats=None):
+    o = RenderOpts()
+    o.stats = None if stats is None else _dev(stats, torch.int64).data_ptr()
+    o.precision = PRECISIONS.get(precision, precision) if isinstance(precision, str) else int(precision)
+    o.out_pq = None if out_pq is None else _dev(out_pq).data_ptr()
+    o.out_T = None if out_T is None else _dev(out_T).data_ptr()
+    o.out_n = None if out_n is None else _dev(out_n, torch.int32).data_ptr()
+    return o
+
+
+def vrnerf_render(field: Field, cameras, intrinsics, resolution, out=None, precision=FP32,
+                  out_pq=None, out_T=None, out_n=None, stats=None, stream=None):
+    """cameras [n][3][4], intrinsics [n][4]: float32 CUDA tensors; resolution
+    [n][2] (W, H) on the host. Returns out [sum W*H][3] linear colour."""
+    res = np.ascontiguousarray(resolution, dtype=np.int32).reshape(-1, 2)
+    rays = int((res[:, 0].astype(np.int64) * res[:, 1]).sum())
+    if out is None:
+        out = torch.empty((rays, 3), device=cameras.device, dtype=torch.float32)
+    o = _opts(precision, out_pq, out_T, out_n, stats)
+    _check(load().vrnerf_render(field.h, _ptr(_dev(cameras)), _ptr(_dev(intrinsics)), _ptr(res),
+                                res.shape[0], _ptr(_dev(out)), ctypes.byref(o), _stream(stream)))
+    return out
+
+
+def vrnerf_render_host(field: Field, cameras, intrinsics, resolution, out=None, precision=FP32,
+                       stream=None):
+    """All arrays on the host (numpy); copies in and out inside the call."""
+    res = np.ascontiguousarray(resolution, dtype=np.int32).reshape(-1, 2)
+    rays = int((res[:, 0].astype(np.int64) * res[:, 1]).sum())
+    cams = np.ascontiguousarray(cameras, dtype=np.float32)
+    K = np.ascontiguousarray(intrinsics, dtype=np.float32)
+    if out is None:
+        out = np.empty((rays, 3), np.float32)
+    o = _opts(precision)
+    _check(load().vrnerf_render_host(field.h, _ptr(cams), _ptr(K), _ptr(res), res.shape[0],
+                                     _ptr(out), ctypes.byref(o), _stream(stream)))
+    return out
+
+
+def vrnerf_render_rays(field: Field, rays_o, rays_d, radii, out=None, precision=FP32, out_pq=None,
+                       out_T=None, out_n=None, stats=None, stream=None):
+    B = rays_o.shape[0]
+    if out is None:
+        out = torch.empty((B, 3), device=rays_o.device, dtype=torch.float32)
+    o = _opts(precision, out_pq, out_T, out_n, stats)
+    _check(load().vrnerf_render_rays(field.h, _ptr(_dev(rays_o)), _ptr(_dev(rays_d)),
+                                     _ptr(_dev(radii)), B, _ptr(_dev(out)), ctypes.byref(o),
+                                     _stream(stream)))
+    return out
+
+
+def vrnerf_query(field: Field, pos, direction, radius, precision=FP32, with_feat=False, stream=None):
+    n = pos.shape[0]
+    dev = pos.device
+    sigma = torch.empty(n, device=dev)
+    rgb = torch.empty((n, 3), device=dev)
+    feat = torch.empty((n, field.cfg.d_in), device=dev) if with_feat else None
+    p = PRECISIONS.get(precision, precision) if isinstance(precision, str) else int(precision)
+    _check(load().vrnerf_query(field.h, _ptr(_dev(pos)), _ptr(_dev(direction)), _ptr(_dev(radius)),
+                               n, _ptr(sigma), _ptr(rgb), _ptr(feat), p, _stream(stream)))
+    return sigma, rgb, feat
+
+
+def vrnerf_debug_march(field: Field, rays_o, rays_d, cap, stream=None):
+    B = rays_o.shape[0]
+    dev = rays_o.device
+    rec_i = torch.full((B, cap), -1, device=dev, dtype=torch.int32)
+    rec_v = torch.full((B, cap), -1, device=dev, dtype=torch.int32)
+    cnt = torch.empty(B, device=dev, dtype=torch.int32)
+    _check(load().vrnerf_debug_march(field.h, _ptr(_dev(rays_o)), _ptr(_dev(rays_d)), B, cap,
+                                     _ptr(rec_i), _ptr(rec_v), _ptr(cnt), _stream(stream)))
+    return rec_i, rec_v, cnt
+
+
+def vrnerf_debug_corners(field: Field, pos, stream=None):
+    n = pos.shape[0]
+    idx = torch.empty((n, field.cfg.levels, 8), device=pos.device, dtype=torch.int32)
+    _check(load().vrnerf_debug_corners(field.h, _ptr(_dev(pos)), n, _ptr(idx), _stream(stream)))
+    return idx
+
+
+def vrnerf_backward(field: Field, rays_o, rays_d, radii, target_linear, stream=None):
+    B = rays_o.shape[0]
+    loss = ctypes.c_float()
+    _check(load().vrnerf_backward(field.h, _ptr(_dev(rays_o)), _ptr(_dev(rays_d)), _ptr(_dev(radii)),
+                                  _ptr(_dev(target_linear)), B, ctypes.byref(loss), _stream(stream)))
+    return loss.value
+
+
+def vrnerf_field_get_grads(field: Field):
+    cfg = field.cfg
+    g = np.empty((cfg.levels, cfg.T, cfg.feats), np.float32)
+    m = np.empty(cfg.n_mlp(), np.float32)
+    _check(load().vrnerf_field_get_grads(field.h, _ptr(g), _ptr(m)))
+    return g, m
+
+
+def vrnerf_field_set_grads(field: Field, grid_grad, mlp_grad):
+    g = np.ascontiguousarray(grid_grad, dtype=np.float32)
+    m = np.ascontiguousarray(mlp_grad, dtype=np.float32)
+    _check(load().vrnerf_field_set_grads(field.h, _ptr(g), _ptr(m)))
+
+
+def vrnerf_adam_step(field: Field, lr_grid=0.01, lr_mlp=0.005, stream=None):
+    _check(load().vrnerf_adam_step(field.h, lr_grid, lr_mlp, _stream(stream)))
+
+
+def vrnerf_train_step(field: Field, rays_o, rays_d, radii, target_linear, lr_grid=0.01,
+                      lr_mlp=0.005, want_loss=True, stream=None):
+    B = rays_o.shape[0]
+    loss = ctypes.c_float()
+    _check(load().vrnerf_train_step(field.h, _ptr(_dev(rays_o)), _ptr(_dev(rays_d)),
+                                    _ptr(_dev(radii)), _ptr(_dev(target_linear)), B, lr_grid,
+                                    lr_mlp, ctypes.byref(loss) if want_loss else None,
+                                    _stream(stream)))
+    return loss.value if want_loss else None

@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--variant", default="room", choices=["room", "room_surface"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--profile-case", action="store_true",
+                    help="small case for ncu: two renders of a 1024x1024 window of the room frame")
     return ap.parse_args()
 
 
@@ -175,10 +177,35 @@ def reference_arm(args):
     return 0
 
 
+def profile_case(args):
+    """Two renders of a 1024x1024 window of the benchmark frame (same field,
+    about 140 MB on the device): the small case for ncu captures."""
+    import torch
+    from paper_2311_02542_gb300 import synth as S
+    from paper_2311_02542_gb300 import vrnerf as V
+    V.load()
+    sc = S.make_scene(args.variant)
+    field = V.Field(sc.cfg, sc.grid, sc.mlp, sc.occ_bits)
+    c2w, K, _ = S.camera_room(sc.occ, sc.cfg, 2, 2048, 2048)
+    K = S.crop_camera(K, 512, 512)
+    res = np.array([[1024, 1024]], np.int32)
+    prec = V.PRECISIONS["fp32" if args.precision == "auto" else args.precision]
+    cams, intr = torch.from_numpy(c2w).cuda(), torch.from_numpy(K).cuda()
+    out = torch.empty((1024 * 1024, 3), device="cuda")
+    for _ in range(2):
+        V.vrnerf_render(field, cams, intr, res, out=out, precision=prec)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": "room 1024x1024 window", "precision": prec,
+                      "mean_linear": float(out.mean())}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.profile_case:
+        return profile_case(args)
     import torch
     rank, world, local = dist_env()
     torch.cuda.set_device(local)

@@ -213,6 +213,24 @@ int vrnerf_train_step(vrnerf_field *field, const float *rays_o, const float *ray
 int vrnerf_field_set_grads(vrnerf_field *field, const float *grid_grad_host,
                            const float *mlp_grad_host);
 
+/* The fp32 render of vrnerf_render for callers that cannot allocate GPU
+ * memory: it calls no cudaMalloc, cudaFree or other allocating routine.
+ * The paper has no counterpart; this exists for callers such as a VR
+ * compositor's frame callback, where an allocation could stall the frame,
+ * or a plug-in whose host application owns every device allocation.
+ * The caller passes the field's parameters in device buffers it owns, in the
+ * layouts above: grid [L][T][F], mlp W1..W5, occ_bits; cameras, intrinsics
+ * and out as in vrnerf_render (device), resolution_host on the host. The
+ * kernel's scratch (ray-slot counter and sample-distance table) lives in one
+ * 32 KiB static device array that every GPU loading the library keeps until
+ * the process exits; its address is looked up on the first call made on
+ * each device (make that call outside stream capture). max_steps above 8127
+ * is rejected with EINVAL. Calls share the scratch: calls whose work
+ * overlaps on the GPU race, so order them on one stream. EINVAL, ECUDA. */
+int vrnerf_render_noalloc(const vrnerf_field_desc *desc, const void *grid, const float *mlp,
+                          const uint32_t *occ_bits, const float *cameras, const float *intrinsics,
+                          const int32_t *resolution_host, int32_t n, float *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

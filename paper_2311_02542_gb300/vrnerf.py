@@ -69,6 +69,7 @@ _SIGS = {
     "vrnerf_field_set_grads": (ctypes.c_int, [_VP, _VP, _VP]),
     "vrnerf_adam_step": (ctypes.c_int, [_VP, _F, _F, _VP]),
     "vrnerf_train_step": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _I32, _F, _F, _VP, _VP]),
+    "vrnerf_render_noalloc": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _I32, _VP, _VP]),
 }
 
 _lib = None
@@ -317,3 +318,21 @@ def vrnerf_train_step(field: Field, rays_o, rays_d, radii, target_linear, lr_gri
                                     lr_mlp, ctypes.byref(loss) if want_loss else None,
                                     _stream(stream)))
     return loss.value if want_loss else None
+
+
+def vrnerf_render_noalloc(cfg, grid, mlp, occ_bits, cameras, intrinsics, resolution, out=None,
+                          stream=None):
+    """fp32 render that allocates nothing in the library: grid / mlp / occ_bits
+    are caller-owned CUDA tensors (fp16 or fp32 grid, fp32 weights, occupancy
+    words as int32 or uint32). `out` is allocated here only when not given."""
+    res = np.ascontiguousarray(resolution, dtype=np.int32).reshape(-1, 2)
+    rays = int((res[:, 0].astype(np.int64) * res[:, 1]).sum())
+    if out is None:
+        out = torch.empty((rays, 3), device=cameras.device, dtype=torch.float32)
+    for t in (grid, mlp, occ_bits):
+        assert isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()
+    d = desc(cfg)
+    _check(load().vrnerf_render_noalloc(ctypes.byref(d), _ptr(grid), _ptr(_dev(mlp)), _ptr(occ_bits),
+                                        _ptr(_dev(cameras)), _ptr(_dev(intrinsics)), _ptr(res),
+                                        res.shape[0], _ptr(_dev(out)), _stream(stream)))
+    return out

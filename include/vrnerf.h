@@ -127,6 +127,12 @@ int vrnerf_field_sizes(const vrnerf_field_desc *desc, uint64_t *grid_bytes, uint
 int vrnerf_field_create(const vrnerf_field_desc *desc, const void *grid_host, const float *mlp_host,
                         const uint32_t *occ_bits_host, uint64_t seed, vrnerf_field **out);
 
+/* VRNERF_OK, or the error a kernel of this field recorded since the last
+ * call (VRNERF_ETIMEDOUT when a bounded device-side wait of the tensor-core
+ * kernels ran out; the kernel then stopped early and its output is
+ * incomplete), and clears it. Synchronises the field's device. */
+int vrnerf_field_status(vrnerf_field *field);
+
 /* Frees the field and all its device memory (synchronises its device). */
 void vrnerf_field_destroy(vrnerf_field *field);
 

@@ -107,6 +107,34 @@ void derive_view(const vrnerf_field_desc &d, FieldView &f, std::vector<float> &t
     f.density_bias = d.density_bias;
     f.radius_scale = d.radius_scale;
     f.n_mlp = 64 * f.d_in + 16 * 64 + 64 * 32 + 64 * 64 + 3 * 64;
+    // occupancy pyramid: level m has ceil(res / 2^m) blocks a side, up to one block
+    int res_max = max(d.occ_res[0], max(d.occ_res[1], d.occ_res[2]));
+    f.n_mip = 0;
+    while ((1 << f.n_mip) < res_max && f.n_mip < kMaxMip - 1) ++f.n_mip;
+    long long words = 0;
+    for (int m = 1; m <= f.n_mip; ++m) {
+        const long long rx = (d.occ_res[0] + (1 << m) - 1) >> m, ry = (d.occ_res[1] + (1 << m) - 1) >> m,
+                        rz = (d.occ_res[2] + (1 << m) - 1) >> m;
+        f.mip_off[m] = (int)words;
+        f.mip_rx[m] = (int)rx;
+        f.mip_ry[m] = (int)ry;
+        words += (rx * ry * rz + 31) / 32;
+    }
+    f.mip_words = (int)words;
+    // Skipping is exact when skip_eps exceeds the rounding error of the fp32
+    // grid coordinate of a sample and of a block-exit distance, both below
+    // 2^-24 (c (t_far + 2 A + ext) + res) up to a small factor (A: largest
+    // |coordinate| of the box, c: largest voxels per unit); keep a 16x margin.
+    f.skip_eps = 1.0f / 16.0f;
+    double A = 0.0, c_max = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        A = fmax(A, fmax(fabs((double)d.aabb_min[k]), fabs((double)d.aabb_max[k])));
+        c_max = fmax(c_max, (double)f.inv_cell[k]);
+    }
+    const double err = ldexp(1.0, -24) * (c_max * ((double)d.t_far + 2.0 * A + ext_max) + res_max);
+    f.skip = (16.0 * err < (double)f.skip_eps) ? 1 : 0;
+    f.ln_tn = logf(d.t_near);
+    f.inv_ln_q = (float)((double)d.max_steps / log((double)d.t_far / (double)d.t_near));
     // exponential sample distances t_i = t_near (t_far / t_near)^(i / S), fp64 -> fp32
     t_tab.resize(d.max_steps + 1);
     const double tn = d.t_near, tf = d.t_far;
@@ -163,7 +191,7 @@ using namespace vrn;
 
 void vrnerf_field::release() {
     void *ptrs[] = {grid,     mlp,      occ,         t_tab,  counter, tc_w,   grid_grad, mlp_grad,
-                    grid_master, m_grid, v_grid, m_mlp, v_mlp, loss_acc, stage_cam, stage_out};
+                    grid_master, m_grid, v_grid, m_mlp, v_mlp, loss_acc, stage_cam, stage_out, mip};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     grid = nullptr;
@@ -171,6 +199,7 @@ void vrnerf_field::release() {
     occ = nullptr;
     t_tab = nullptr;
     counter = nullptr;
+    mip = nullptr;
     tc_w = nullptr;
     grid_grad = mlp_grad = grid_master = m_grid = v_grid = m_mlp = v_mlp = loss_acc = nullptr;
     stage_cam = stage_out = nullptr;
@@ -245,7 +274,8 @@ int vrnerf_field_create(const vrnerf_field_desc *desc, const void *grid_host, co
         (e = cudaMalloc(&F->mlp, nmlp * sizeof(float))) != cudaSuccess ||
         (e = cudaMalloc(&F->occ, nocc * sizeof(uint32_t))) != cudaSuccess ||
         (e = cudaMalloc(&F->t_tab, t_tab.size() * sizeof(float))) != cudaSuccess ||
-        (e = cudaMalloc(&F->counter, 64)) != cudaSuccess) {
+        (e = cudaMalloc(&F->counter, 64)) != cudaSuccess ||
+        (e = cudaMalloc(&F->mip, sizeof(uint32_t) * (size_t)(F->view.mip_words > 0 ? F->view.mip_words : 1))) != cudaSuccess) {
         vrnerf_field_destroy(F);
         cudaGetLastError();
         return fail(VRNERF_ENOMEM, "device allocation failed: %s", cudaGetErrorString(e));
@@ -265,17 +295,20 @@ int vrnerf_field_create(const vrnerf_field_desc *desc, const void *grid_host, co
         }
     }
     if (e == cudaSuccess) e = cudaMemcpy(F->occ, occ_bits_host, nocc * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(F->counter, 0, 64);
     if (e == cudaSuccess)
         e = cudaMemcpy(F->t_tab, t_tab.data(), t_tab.size() * 4, cudaMemcpyHostToDevice);
+    F->view.grid = F->grid;
+    F->view.mlp = F->mlp;
+    F->view.occ = F->occ;
+    F->view.t_tab = F->t_tab;
+    F->view.mip = F->mip;
+    if (e == cudaSuccess) e = launch_build_mip(F->view, F->mip, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         vrnerf_field_destroy(F);
         return cuda_fail(e, "field_create");
     }
-    F->view.grid = F->grid;
-    F->view.mlp = F->mlp;
-    F->view.occ = F->occ;
-    F->view.t_tab = F->t_tab;
     *out = F;
     return VRNERF_OK;
     ABI_GUARD_END
@@ -295,6 +328,20 @@ void vrnerf_field_destroy(vrnerf_field *F) {
     }
 }
 
+int vrnerf_field_status(vrnerf_field *F) {
+    ABI_GUARD_BEGIN
+    if (!F) return fail(VRNERF_EINVAL, "field is NULL");
+    unsigned long long st = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess)
+        e = cudaMemcpy(&st, reinterpret_cast<unsigned long long *>(F->counter) + 1, sizeof st, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && st) e = cudaMemset(reinterpret_cast<unsigned long long *>(F->counter) + 1, 0, sizeof st);
+    if (e != cudaSuccess) return cuda_fail(e, "field_status");
+    if (st) return fail(-(int)st, "a device-side wait timed out; the last kernel stopped early");
+    return VRNERF_OK;
+    ABI_GUARD_END
+}
+
 int vrnerf_field_get_params(vrnerf_field *F, void *grid_host, float *mlp_host) {
     ABI_GUARD_BEGIN
     if (!F) return fail(VRNERF_EINVAL, "field is NULL");
@@ -311,6 +358,8 @@ int vrnerf_field_set_occupancy(vrnerf_field *F, const uint32_t *occ) {
     ABI_GUARD_BEGIN
     if (!F || !occ) return fail(VRNERF_EINVAL, "NULL argument");
     cudaError_t e = cudaMemcpy(F->occ, occ, occ_words(F->desc) * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_build_mip(F->view, F->mip, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "set_occupancy");
     return VRNERF_OK;
     ABI_GUARD_END

@@ -17,6 +17,7 @@ constexpr int kMaxLevels = 16;
 constexpr int kMaxViews = 256;
 constexpr int kTileW = 8;   // rays of one warp cover an 8 x 4 pixel tile
 constexpr int kTileH = 4;
+constexpr int kMaxMip = 12;  // occupancy pyramid levels 1..11 (res <= 2048)
 
 // Everything a kernel needs to read the field; passed by value.
 struct FieldView {
@@ -33,6 +34,16 @@ struct FieldView {
     float inv_ext;
     float two_s, inv_ln_f, lod_bias, T_eps, density_bias, radius_scale;
     int n_mlp;
+    // empty-space skipping: occupancy pyramid, level m >= 1 holds one bit per
+    // block of 2^m voxels a side (set when any voxel of the block is occupied)
+    const uint32_t *mip;      // all levels, concatenated
+    int skip;                 // 0: test every sample
+    int n_mip;                // levels 1 .. n_mip present
+    int mip_off[kMaxMip];     // word offset of level m
+    int mip_rx[kMaxMip], mip_ry[kMaxMip];
+    float skip_eps;           // margin (voxels) kept from block faces
+    float ln_tn, inv_ln_q;    // ln t_near and S / ln(t_far / t_near)
+    int mip_words;            // total words of levels 1..n_mip
 };
 
 // One launch's rays: either camera views (pixels in 8x4 tiles) or explicit arrays.
@@ -94,8 +105,7 @@ __device__ __forceinline__ void camera_ray(const float *__restrict__ c2w, const 
 
 // p = o + t d and its occupancy voxel; false once the sample leaves the grid.
 __device__ __forceinline__ bool sample_voxel(const FieldView &f, const float o[3], const float d[3],
-                                             float t, float p[3], int &vox) {
-    int v[3];
+                                             float t, float p[3], int &vox, int v[3]) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         p[k] = __fadd_rn(o[k], __fmul_rn(t, d[k]));
@@ -106,9 +116,104 @@ __device__ __forceinline__ bool sample_voxel(const FieldView &f, const float o[3
     vox = v[0] + f.res[0] * (v[1] + f.res[1] * v[2]);
     return true;
 }
+__device__ __forceinline__ bool sample_voxel(const FieldView &f, const float o[3], const float d[3],
+                                             float t, float p[3], int &vox) {
+    int v[3];
+    return sample_voxel(f, o, d, t, p, vox, v);
+}
 
 __device__ __forceinline__ bool occupied(const uint32_t *__restrict__ occ, int vox) {
     return (__ldg(occ + (vox >> 5)) >> (vox & 31)) & 1u;
+}
+
+// ---------------------------------------------------------------------------
+// Occupancy march (Sec. 4.3) with exact empty-space skipping.
+//
+// The evaluated samples are defined per sample: sample i is evaluated iff its
+// fp32 position falls in an occupied voxel, and the march ends at the first
+// sample outside the grid. The skip never changes that set. From a sample in
+// an empty voxel it takes the largest empty pyramid block around the voxel
+// (clipped to the grid), shrinks it by skip_eps voxels on every face, and
+// jumps to the first sample at or past the ray's exit from the shrunken
+// block. Every sample jumped over lies, exactly, at least skip_eps inside the
+// block; skip_eps is far above the rounding error of the fp32 position and of
+// the exit distance (checked when the field is created), so each of those
+// samples would have been found, one by one, in an empty voxel of the block.
+// ---------------------------------------------------------------------------
+struct MarchRay {
+    float o[3], d[3];
+    float g0[3], inv_s[3];  // grid coordinate at t = 0 and 1 / (grid units per unit t)
+    int step;
+};
+
+__device__ __forceinline__ void march_init(const FieldView &f, MarchRay &m) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        m.g0[k] = (m.o[k] - f.mn[k]) * f.inv_cell[k];
+        const float s = m.d[k] * f.inv_cell[k];
+        m.inv_s[k] = s != 0.0f ? 1.0f / s : 0.0f;
+    }
+    m.step = 0;
+}
+
+__device__ __forceinline__ bool mip_occupied(const FieldView &f, int m, const int v[3]) {
+    const int bx = v[0] >> m, by = v[1] >> m, bz = v[2] >> m;
+    const int i = bx + f.mip_rx[m] * (by + f.mip_ry[m] * bz);
+    return (__ldg(f.mip + f.mip_off[m] + (i >> 5)) >> (i & 31)) & 1u;
+}
+
+// First sample index j >= lo whose distance is >= t (S if none).
+__device__ __forceinline__ int first_sample_at(const FieldView &f, const float *__restrict__ sT,
+                                               float t, int lo) {
+    int j = (int)ceilf((logf(t) - f.ln_tn) * f.inv_ln_q);
+    j = j < lo ? lo : (j > f.S ? f.S : j);
+    while (j > lo && sT[j - 1] >= t) --j;
+    while (j < f.S && sT[j] < t) ++j;
+    return j;
+}
+
+enum { MARCH_END = 0, MARCH_SAMPLE = 1, MARCH_MORE = 2 };
+
+// Advances m.step to the next evaluated sample (MARCH_SAMPLE, p set,
+// m.step = its index), to the end of the ray (MARCH_END), or stops after
+// max_iter iterations (MARCH_MORE). tested counts canonical sample tests.
+__device__ __forceinline__ int march_next(const FieldView &f, const float *__restrict__ sT,
+                                          MarchRay &m, float p[3], int max_iter,
+                                          unsigned &tested) {
+    for (int it = 0; it < max_iter; ++it) {
+        if (m.step >= f.S) return MARCH_END;
+        const float t = sT[m.step];
+        int vox, v[3];
+        if (!sample_voxel(f, m.o, m.d, t, p, vox, v)) return MARCH_END;
+        ++tested;
+        if (occupied(f.occ, vox)) return MARCH_SAMPLE;
+        if (!f.skip) {
+            ++m.step;
+            continue;
+        }
+        int lev = 0;
+        while (lev < f.n_mip && !mip_occupied(f, lev + 1, v)) ++lev;
+        float t_in = -INFINITY, t_out = INFINITY;
+        bool ok = true;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int lo_i = (v[k] >> lev) << lev;
+            const int hi_i = min(lo_i + (1 << lev), f.res[k]);
+            const float lo = (float)lo_i + f.skip_eps, hi = (float)hi_i - f.skip_eps;
+            if (m.inv_s[k] != 0.0f) {
+                const float ta = (lo - m.g0[k]) * m.inv_s[k], tb = (hi - m.g0[k]) * m.inv_s[k];
+                t_in = fmaxf(t_in, fminf(ta, tb));
+                t_out = fminf(t_out, fmaxf(ta, tb));
+            } else if (!(m.g0[k] >= lo && m.g0[k] <= hi)) {
+                ok = false;
+            }
+        }
+        if (ok && t_in <= t && t_out > t)
+            m.step = first_sample_at(f, sT, t_out, m.step + 1);
+        else
+            ++m.step;
+    }
+    return MARCH_MORE;
 }
 
 // Corner indices of level l (corner b at offset (b&1, b>>1&1, b>>2&1)) and

@@ -75,4 +75,49 @@ cudaError_t launch_seeded_mlp(float *mlp, const int (*shapes)[2], int n_mats, ui
     return cudaSuccess;
 }
 
+// Level m of the occupancy pyramid from level m - 1: bit = OR of the (up to)
+// 2x2x2 child bits. One thread per output word.
+__global__ void mip_level_kernel(const uint32_t *__restrict__ prev, int prx, int pry, int prz,
+                                 uint32_t *__restrict__ out, int rx, int ry, int rz) {
+    const long long n = (long long)rx * ry * rz;
+    const long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w * 32 >= n) return;
+    uint32_t bits = 0;
+    for (int b = 0; b < 32; ++b) {
+        const long long i = w * 32 + b;
+        if (i >= n) break;
+        const int bx = (int)(i % rx), by = (int)((i / rx) % ry), bz = (int)(i / ((long long)rx * ry));
+        uint32_t any = 0;
+        for (int c = 0; c < 8; ++c) {
+            const int cx = 2 * bx + (c & 1), cy = 2 * by + ((c >> 1) & 1), cz = 2 * bz + (c >> 2);
+            if (cx < prx && cy < pry && cz < prz) {
+                const long long j = cx + (long long)prx * (cy + (long long)pry * cz);
+                any |= (prev[j >> 5] >> (j & 31)) & 1u;
+            }
+        }
+        bits |= any << b;
+    }
+    out[w] = bits;
+}
+
+cudaError_t launch_build_mip(const FieldView &f, uint32_t *mip, cudaStream_t st) {
+    const uint32_t *prev = f.occ;
+    int prx = f.res[0], pry = f.res[1], prz = f.res[2];
+    for (int m = 1; m <= f.n_mip; ++m) {
+        const int rx = (f.res[0] + (1 << m) - 1) >> m, ry = (f.res[1] + (1 << m) - 1) >> m,
+                  rz = (f.res[2] + (1 << m) - 1) >> m;
+        const long long words = ((long long)rx * ry * rz + 31) / 32;
+        uint32_t *out = mip + f.mip_off[m];
+        mip_level_kernel<<<(unsigned)((words + 127) / 128), 128, 0, st>>>(prev, prx, pry, prz, out, rx,
+                                                                         ry, rz);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        prev = out;
+        prx = rx;
+        pry = ry;
+        prz = rz;
+    }
+    return cudaSuccess;
+}
+
 }  // namespace vrn

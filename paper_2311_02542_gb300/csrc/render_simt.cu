@@ -157,8 +157,9 @@ render_simt_kernel(const FieldView f, const RaySource src, const RenderOut out,
     const int lane = threadIdx.x & 31;
     long long ray = -1, pix = 0;
     bool exhausted = false;
-    float o[3] = {0, 0, 0}, d[3] = {0, 0, 1}, r = 0.0f, T = 1.0f, C[3] = {0, 0, 0};
-    int step = 0, n_eval = 0;
+    MarchRay mr;
+    float r = 0.0f, T = 1.0f, C[3] = {0, 0, 0};
+    int n_eval = 0;
     unsigned st_samples = 0, st_levels = 0, st_steps = 0, st_rays = 0;
 
     while (true) {
@@ -177,9 +178,9 @@ render_simt_kernel(const FieldView f, const RaySource src, const RenderOut out,
                     long long slot = (long long)base + __popc(m & ((1u << lane) - 1u));
                     if (slot >= src.n_slots) {
                         exhausted = true;
-                    } else if (slot_ray(src, f, slot, o, d, r, pix)) {
+                    } else if (slot_ray(src, f, slot, mr.o, mr.d, r, pix)) {
+                        march_init(f, mr);
                         ray = slot;
-                        step = 0;
                         n_eval = 0;
                         T = 1.0f;
                         C[0] = C[1] = C[2] = 0.0f;
@@ -187,20 +188,13 @@ render_simt_kernel(const FieldView f, const RaySource src, const RenderOut out,
                 }
             }
             if (ray >= 0 && !have) {
-                for (int k = 0; k < kChunk; ++k) {
-                    int vox;
-                    if (step >= f.S || !sample_voxel(f, o, d, sT[step], p, vox)) {
-                        finish_ray(out, pix, C, T, n_eval);
-                        ray = -1;
-                        ++st_rays;
-                        break;
-                    }
-                    ++st_steps;
-                    if (occupied(f.occ, vox)) {
-                        have = true;
-                        break;
-                    }
-                    ++step;
+                const int mres = march_next(f, sT, mr, p, kChunk, st_steps);
+                if (mres == MARCH_SAMPLE) {
+                    have = true;
+                } else if (mres == MARCH_END) {
+                    finish_ray(out, pix, C, T, n_eval);
+                    ray = -1;
+                    ++st_rays;
                 }
             }
             if (__all_sync(FULL, have || exhausted)) break;
@@ -208,13 +202,13 @@ render_simt_kernel(const FieldView f, const RaySource src, const RenderOut out,
         if (!__any_sync(FULL, have)) break;
         // ---- phase 2: features, MLPs, compositing ----
         if (have) {
-            const float t = sT[step], delta = sT[step + 1] - t;
+            const float t = sT[mr.step], delta = sT[mr.step + 1] - t;
             const float r_norm = t * r * f.inv_ext;
             float feat[D];
             st_levels += gather_features<L>(f, p, r_norm, feat);
             ++st_samples;
             float sigma, rgb[3];
-            mlp_simt<D>(sW, feat, d, f.density_bias, sigma, rgb);
+            mlp_simt<D>(sW, feat, mr.d, f.density_bias, sigma, rgb);
             const float sd = sigma * delta;
             const float w = T * (-expm1f(-sd));
             C[0] += w * rgb[0];
@@ -222,7 +216,7 @@ render_simt_kernel(const FieldView f, const RaySource src, const RenderOut out,
             C[2] += w * rgb[2];
             T *= expf(-sd);
             ++n_eval;
-            ++step;
+            ++mr.step;
             if (T < f.T_eps) {
                 finish_ray(out, pix, C, T, n_eval);
                 ray = -1;
@@ -263,19 +257,26 @@ __global__ void debug_march_kernel(const FieldView f, const float *__restrict__ 
                                    int *__restrict__ count) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= B) return;
-    float o[3] = {o_in[3 * b], o_in[3 * b + 1], o_in[3 * b + 2]};
-    float d[3] = {d_in[3 * b], d_in[3 * b + 1], d_in[3 * b + 2]};
+    // the render kernels' march (with empty-space skipping when enabled)
+    MarchRay m;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        m.o[k] = o_in[3 * b + k];
+        m.d[k] = d_in[3 * b + k];
+    }
+    march_init(f, m);
+    unsigned tested = 0;
     int n = 0;
-    for (int i = 0; i < f.S; ++i) {
-        float p[3];
+    float p[3];
+    while (march_next(f, f.t_tab, m, p, 1 << 30, tested) == MARCH_SAMPLE) {
         int vox;
-        if (!sample_voxel(f, o, d, __ldg(f.t_tab + i), p, vox)) break;
-        if (!occupied(f.occ, vox)) continue;
+        sample_voxel(f, m.o, m.d, f.t_tab[m.step], p, vox);
         if (n < cap) {
-            rec_i[(long long)b * cap + n] = i;
+            rec_i[(long long)b * cap + n] = m.step;
             rec_vox[(long long)b * cap + n] = vox;
         }
         ++n;
+        ++m.step;
     }
     count[b] = n;
 }

@@ -1,16 +1,472 @@
-// render_tc.cu -- tensor-core (tcgen05) MLP path. Placeholder until the
-// kernel lands: reports "not supported" so callers fail loudly.
+// render_tc.cu -- the renderer with its MLPs on the tcgen05 tensor cores
+// (the paper's in-register tensor-core MLP, Sec. 5, rebuilt for sm_103a).
+//
+// A CTA of 128 threads owns 128 ray slots; each round every slot marches to
+// its next evaluated sample (Sec. 4.3), gathers its LOD-weighted hash-grid
+// features (Sec. 4.2.1, Eq. 3) and writes them as one row of a 128-row
+// operand tile in shared memory. The five layers of the density and colour
+// MLPs (Sec. 6) then run as M=128 tcgen05 MMAs (fp16 or bf16 operands, fp32
+// accumulation in TMEM): one thread issues each layer and commits it to an
+// mbarrier; all four warps read their 32 TMEM lanes back (tcgen05.ld),
+// apply ReLU / exp / sigmoid and write the next layer's operand rows. Each
+// thread then composites its own sample front to back and stops its ray when
+// transmittance drops below T_eps; the PQ decode (Eq. 1-2) runs when the ray
+// finishes. Slots whose rays end take new rays from a global counter, so the
+// tile stays full until the frame runs out of rays.
+//
+// Shared memory per CTA: MLP weights in the MMA operand layout (18-20 KB),
+// one 128 x 64 activation tile (16 KB, reused by every layer), the sample
+// distance table, an mbarrier. TMEM: 64 columns (every layer writes columns
+// 0 .. N-1 after the previous layer's values have been read).
 #include "field.h"
+#include "tc.cuh"
 
 namespace vrn {
 
-cudaError_t launch_render_tc(vrnerf_field *, const RaySource &, const RenderOut &, int, cudaStream_t) {
-    return cudaErrorNotSupported;
+constexpr int kTcThreads = 128;
+constexpr uint32_t kTmemCols = 64;
+
+template <int D>
+struct TcW {  // byte offsets of the weight image (K-major operands)
+    static constexpr int w1 = 0;                 // [64][D]
+    static constexpr int w2 = w1 + 64 * D * 2;   // [16][64]
+    static constexpr int w3 = w2 + 16 * 64 * 2;  // [64][32]
+    static constexpr int w4 = w3 + 64 * 32 * 2;  // [64][64]
+    static constexpr int w5 = w4 + 64 * 64 * 2;  // [16][64], rows 3..15 zero
+    static constexpr int bytes = w5 + 16 * 64 * 2;
+};
+
+struct TcShared {
+    unsigned char *w;     // weight image
+    unsigned char *act;   // 128 x 64 operand tile
+    uint64_t *mbar;
+    volatile int *abort;
+    uint32_t tbase;       // TMEM base address (lane 0, column 0)
+};
+
+template <int FMT>
+__device__ __forceinline__ uint32_t pack2(float a, float b) {
+    if (FMT == 0) {
+        __half2 h = __floats2half2_rn(a, b);
+        return *reinterpret_cast<uint32_t *>(&h);
+    } else {
+        __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<uint32_t *>(&h);
+    }
 }
 
-cudaError_t launch_query_tc(vrnerf_field *, const float *, const float *, const float *, int, float *,
-                            float *, float *, int, cudaStream_t) {
-    return cudaErrorNotSupported;
+// Row r of a 128 x K operand tile (K-major core matrices).
+template <int K>
+__device__ __forceinline__ void store_row(unsigned char *base, int r, const uint32_t (&pk)[K / 2]) {
+#pragma unroll
+    for (int j = 0; j < K / 8; ++j) {
+        uint4 v = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+        *reinterpret_cast<uint4 *>(base + (r >> 3) * (K / 8) * 128 + j * 128 + (r & 7) * 16) = v;
+    }
+}
+
+template <int K, int N, int FMT>
+__device__ __forceinline__ void issue_layer(uint32_t a_addr, uint32_t b_addr, uint32_t tmem) {
+    constexpr uint32_t sbo = (K / 8) * 128;
+    constexpr uint32_t idesc = tc::idesc_f16(N, FMT);
+#pragma unroll
+    for (int ks = 0; ks < K / 16; ++ks)
+        tc::mma_f16(tmem, tc::smem_desc(a_addr + ks * 256, 128, sbo), tc::smem_desc(b_addr + ks * 256, 128, sbo),
+                    idesc, ks > 0 ? 1u : 0u);
+}
+
+// Runs one layer: the tile's rows are written; all threads sync, thread 0
+// issues and commits, everyone waits for the accumulators.
+template <int K, int N, int FMT>
+__device__ __forceinline__ void run_layer(const TcShared &S, int w_off, uint32_t &phase, bool &ok) {
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        tc::fence_after_sync();
+        issue_layer<K, N, FMT>(tc::smem_u32(S.act), tc::smem_u32(S.w) + w_off, S.tbase);
+        tc::mma_commit(S.mbar);
+    }
+    ok = tc::mbar_wait_bounded(S.mbar, phase, S.abort) && ok;
+    phase ^= 1u;
+    tc::fence_after_sync();
+}
+
+// Density MLP (D -> 64 -> 16, ReLU; sigma = exp(o_0 + bias)) and colour MLP
+// ([o, SH(d)] 32 -> 64 -> 64 -> 3, ReLU, sigmoid) for the 128 rows of the
+// CTA; this thread's row is `feat`. All 128 threads must call it.
+template <int D, int FMT>
+__device__ __forceinline__ void tc_mlp(const TcShared &S, const float (&feat)[D], const float dir[3],
+                                       float density_bias, float &sigma, float rgb[3], uint32_t &phase,
+                                       bool &ok) {
+    using W = TcW<D>;
+    const int r = threadIdx.x;
+    const uint32_t taddr = S.tbase + ((uint32_t)(r & ~31) << 16);
+    {
+        uint32_t pk[D / 2];
+#pragma unroll
+        for (int i = 0; i < D / 2; ++i) pk[i] = pack2<FMT>(feat[2 * i], feat[2 * i + 1]);
+        store_row<D>(S.act, r, pk);
+    }
+    run_layer<D, 64, FMT>(S, W::w1, phase, ok);
+    {
+        uint32_t pk[32];
+#pragma unroll
+        for (int c = 0; c < 64; c += 16) {
+            float v[16];
+            tc::tmem_ld16(taddr + c, v);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) pk[c / 2 + i] = pack2<FMT>(fmaxf(v[2 * i], 0.f), fmaxf(v[2 * i + 1], 0.f));
+        }
+        store_row<64>(S.act, r, pk);
+    }
+    run_layer<64, 16, FMT>(S, W::w2, phase, ok);
+    {
+        float o[16], sh[16];
+        tc::tmem_ld16(taddr, o);
+        sigma = expf(o[0] + density_bias);
+        sh16(dir[0], dir[1], dir[2], sh);
+        uint32_t pk[16];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            pk[i] = pack2<FMT>(o[2 * i], o[2 * i + 1]);
+            pk[8 + i] = pack2<FMT>(sh[2 * i], sh[2 * i + 1]);
+        }
+        store_row<32>(S.act, r, pk);
+    }
+    run_layer<32, 64, FMT>(S, W::w3, phase, ok);
+    {
+        uint32_t pk[32];
+#pragma unroll
+        for (int c = 0; c < 64; c += 16) {
+            float v[16];
+            tc::tmem_ld16(taddr + c, v);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) pk[c / 2 + i] = pack2<FMT>(fmaxf(v[2 * i], 0.f), fmaxf(v[2 * i + 1], 0.f));
+        }
+        store_row<64>(S.act, r, pk);
+    }
+    run_layer<64, 64, FMT>(S, W::w4, phase, ok);
+    {
+        uint32_t pk[32];
+#pragma unroll
+        for (int c = 0; c < 64; c += 16) {
+            float v[16];
+            tc::tmem_ld16(taddr + c, v);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) pk[c / 2 + i] = pack2<FMT>(fmaxf(v[2 * i], 0.f), fmaxf(v[2 * i + 1], 0.f));
+        }
+        store_row<64>(S.act, r, pk);
+    }
+    run_layer<64, 16, FMT>(S, W::w5, phase, ok);
+    {
+        float z[16];
+        tc::tmem_ld16(taddr, z);
+        rgb[0] = 1.0f / (1.0f + expf(-z[0]));
+        rgb[1] = 1.0f / (1.0f + expf(-z[1]));
+        rgb[2] = 1.0f / (1.0f + expf(-z[2]));
+    }
+    tc::fence_before_sync();  // this tile's TMEM reads precede the next tile's MMAs
+}
+
+// Shared-memory carve-up, weight upload, mbarrier and TMEM set-up.
+template <int D>
+__device__ __forceinline__ TcShared tc_setup(unsigned char *smem, const uint4 *__restrict__ wimg,
+                                             float *&sT, const float *__restrict__ t_tab, int S_steps) {
+    using W = TcW<D>;
+    TcShared S;
+    S.w = smem;
+    S.act = smem + ((W::bytes + 1023) & ~1023);
+    sT = reinterpret_cast<float *>(S.act + 128 * 64 * 2);
+    const int nt = S_steps + 1;
+    unsigned char *misc = reinterpret_cast<unsigned char *>(sT + ((nt + 3) & ~3));
+    S.mbar = reinterpret_cast<uint64_t *>(misc);
+    uint32_t *holder = reinterpret_cast<uint32_t *>(misc + 8);
+    S.abort = reinterpret_cast<volatile int *>(misc + 12);
+    for (int i = threadIdx.x; i < W::bytes / 16; i += blockDim.x)
+        reinterpret_cast<uint4 *>(S.w)[i] = wimg[i];
+    if (t_tab)
+        for (int i = threadIdx.x; i < nt; i += blockDim.x) sT[i] = t_tab[i];
+    if (threadIdx.x == 0) {
+        tc::mbar_init(S.mbar, 1);
+        *S.abort = 0;
+    }
+    if (threadIdx.x < 32) {
+        tc::tmem_alloc(holder, kTmemCols);
+        tc::tmem_relinquish();
+    }
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    S.tbase = *holder;
+    return S;
+}
+
+__device__ __forceinline__ void tc_teardown(const TcShared &S, unsigned long long *status) {
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (threadIdx.x == 0 && *S.abort && status) atomicExch(status, (unsigned long long)(-VRNERF_ETIMEDOUT));
+    if (threadIdx.x < 32) tc::tmem_dealloc(S.tbase, kTmemCols);
+}
+
+__device__ __forceinline__ void finish_ray_tc(const RenderOut &out, long long pix, const float C[3],
+                                              float T, int n) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        out.lin[3 * pix + c] = pq_to_linear(C[c]);
+        if (out.pq) out.pq[3 * pix + c] = C[c];
+    }
+    if (out.T) out.T[pix] = T;
+    if (out.n) out.n[pix] = n;
+}
+
+template <int L, int FMT>
+__global__ void __launch_bounds__(kTcThreads)
+render_tc_kernel(const FieldView f, const RaySource src, const RenderOut out,
+                 unsigned long long *__restrict__ counter, const uint4 *__restrict__ wimg,
+                 unsigned long long *__restrict__ status) {
+    constexpr int D = 2 * L;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    float *sT;
+    const TcShared S = tc_setup<D>(smem, wimg, sT, f.t_tab, f.S);
+
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    long long ray = -1, pix = 0;
+    bool exhausted = false, ok = true;
+    MarchRay mr;
+    float r = 0.0f, T = 1.0f, C[3] = {0, 0, 0};
+    int n_eval = 0;
+    uint32_t phase = 0;
+    unsigned st_samples = 0, st_levels = 0, st_steps = 0, st_rays = 0;
+
+    while (true) {
+        bool have = false;
+        float p[3] = {0, 0, 0};
+        // ---- march to the next occupied sample, refilling finished slots ----
+        while (true) {
+            const bool need = ray < 0 && !exhausted;
+            const unsigned m = __ballot_sync(FULL, need);
+            if (m) {
+                const int leader = __ffs(m) - 1;
+                unsigned long long base = 0;
+                if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(m));
+                base = __shfl_sync(FULL, base, leader);
+                if (need) {
+                    const long long slot = (long long)base + __popc(m & ((1u << lane) - 1u));
+                    if (slot >= src.n_slots) {
+                        exhausted = true;
+                    } else if (slot_ray(src, f, slot, mr.o, mr.d, r, pix)) {
+                        march_init(f, mr);
+                        ray = slot;
+                        n_eval = 0;
+                        T = 1.0f;
+                        C[0] = C[1] = C[2] = 0.0f;
+                    }
+                }
+            }
+            if (ray >= 0 && !have) {
+                const int mres = march_next(f, sT, mr, p, 32, st_steps);
+                if (mres == MARCH_SAMPLE) {
+                    have = true;
+                } else if (mres == MARCH_END) {
+                    finish_ray_tc(out, pix, C, T, n_eval);
+                    ray = -1;
+                    ++st_rays;
+                }
+            }
+            if (__all_sync(FULL, have || exhausted)) break;
+        }
+        if (!__syncthreads_or(have) || *S.abort) break;
+        // ---- features, tensor-core MLPs, compositing ----
+        float feat[D];
+        float t = 0.0f, delta = 0.0f;
+        if (have) {
+            t = sT[mr.step];
+            delta = sT[mr.step + 1] - t;
+            st_levels += gather_features<L>(f, p, t * r * f.inv_ext, feat);
+            ++st_samples;
+        } else {
+#pragma unroll
+            for (int k = 0; k < D; ++k) feat[k] = 0.0f;
+        }
+        float sigma, rgb[3];
+        tc_mlp<D, FMT>(S, feat, mr.d, f.density_bias, sigma, rgb, phase, ok);
+        if (have) {
+            const float sd = sigma * delta;
+            const float w = T * (-expm1f(-sd));
+            C[0] += w * rgb[0];
+            C[1] += w * rgb[1];
+            C[2] += w * rgb[2];
+            T *= expf(-sd);
+            ++n_eval;
+            ++mr.step;
+            if (T < f.T_eps) {
+                finish_ray_tc(out, pix, C, T, n_eval);
+                ray = -1;
+                ++st_rays;
+            }
+        }
+    }
+    add_stats(out.stats, st_samples, st_levels, st_steps, st_rays);
+    tc_teardown(S, status);
+}
+
+template <int L, int FMT>
+__global__ void __launch_bounds__(kTcThreads)
+query_tc_kernel(const FieldView f, const float *__restrict__ pos, const float *__restrict__ dir,
+                const float *__restrict__ radius, int n, float *__restrict__ sigma_out,
+                float *__restrict__ rgb_out, float *__restrict__ feat_out, const uint4 *__restrict__ wimg,
+                unsigned long long *__restrict__ status) {
+    constexpr int D = 2 * L;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    float *sT;
+    const TcShared S = tc_setup<D>(smem, wimg, sT, nullptr, 0);
+    const int i = blockIdx.x * kTcThreads + threadIdx.x;
+    const bool valid = i < n;
+    float feat[D], dd[3] = {0, 0, 1};
+    if (valid) {
+        float p[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
+        dd[0] = dir[3 * i];
+        dd[1] = dir[3 * i + 1];
+        dd[2] = dir[3 * i + 2];
+        gather_features<L>(f, p, radius[i] * f.inv_ext, feat);
+    } else {
+#pragma unroll
+        for (int k = 0; k < D; ++k) feat[k] = 0.0f;
+    }
+    uint32_t phase = 0;
+    bool ok = true;
+    float sigma, rgb[3];
+    tc_mlp<D, FMT>(S, feat, dd, f.density_bias, sigma, rgb, phase, ok);
+    if (valid) {
+        sigma_out[i] = sigma;
+        for (int c = 0; c < 3; ++c) rgb_out[3 * i + c] = rgb[c];
+        if (feat_out)
+            for (int k = 0; k < D; ++k) feat_out[(long long)i * D + k] = feat[k];
+    }
+    tc_teardown(S, status);
+}
+
+// fp32 W1..W5 -> the K-major operand image of TcW<D>, fp16 or bf16.
+__global__ void build_tc_image_kernel(const float *__restrict__ mlp, int D, int fmt,
+                                      unsigned char *__restrict__ img) {
+    const int sizes[5][3] = {{64, D, 64}, {16, 64, 16}, {64, 32, 64}, {64, 64, 64}, {16, 64, 3}};
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    int off = 0, src = 0;
+    for (int m = 0; m < 5; ++m) {
+        const int N = sizes[m][0], K = sizes[m][1], rows = sizes[m][2];
+        if (e < N * K) {
+            const int row = e / K, col = e % K;
+            const float v = row < rows ? mlp[src + row * K + col] : 0.0f;
+            const int b = off + (row >> 3) * (K >> 3) * 128 + (col >> 3) * 128 + (row & 7) * 16 + (col & 7) * 2;
+            if (fmt == 0)
+                *reinterpret_cast<__half *>(img + b) = __float2half_rn(v);
+            else
+                *reinterpret_cast<__nv_bfloat16 *>(img + b) = __float2bfloat16_rn(v);
+            return;
+        }
+        e -= N * K;
+        off += N * K * 2;
+        src += rows * K;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static size_t tc_smem_bytes(int D, int S_steps) {
+    const size_t wb = (size_t)(64 * D * 2 + 16 * 64 * 2 + 64 * 32 * 2 + 64 * 64 * 2 + 16 * 64 * 2);
+    size_t b = ((wb + 1023) & ~(size_t)1023) + 128 * 64 * 2 + sizeof(float) * (size_t)((S_steps + 1 + 3) & ~3) + 64;
+    // at most 512 / kTmemCols CTAs per SM, so tcgen05.alloc never waits
+    const size_t floor_bytes = (size_t)(232448 / (512 / kTmemCols)) + 1024;
+    return b > floor_bytes ? b : floor_bytes;
+}
+
+static cudaError_t ensure_tc_image(vrnerf_field *F, int fmt, cudaStream_t st) {
+    const int D = F->view.d_in;
+    const size_t bytes = (size_t)(64 * D * 2 + 16 * 64 * 2 + 64 * 32 * 2 + 64 * 64 * 2 + 16 * 64 * 2);
+    if (F->tc_w && F->tc_prec == fmt && F->tc_version == F->mlp_version) return cudaSuccess;
+    if (!F->tc_w) {
+        cudaError_t e = cudaMalloc(&F->tc_w, bytes);
+        if (e != cudaSuccess) return e;
+        F->tc_w_bytes = bytes;
+    }
+    const int n = (int)(bytes / 2);
+    build_tc_image_kernel<<<(n + 255) / 256, 256, 0, st>>>(F->mlp, D, fmt, static_cast<unsigned char *>(F->tc_w));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    F->tc_prec = fmt;
+    F->tc_version = F->mlp_version;
+    return cudaSuccess;
+}
+
+template <typename K>
+static cudaError_t prepare(K kern, size_t smem, int &blocks_per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, kTcThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (blocks_per_sm < 1) return cudaErrorInvalidConfiguration;
+    if (blocks_per_sm > (int)(512 / kTmemCols)) return cudaErrorInvalidConfiguration;
+    return cudaSuccess;
+}
+
+template <int L, int FMT>
+static cudaError_t render_tc_t(vrnerf_field *F, const RaySource &src, const RenderOut &out, cudaStream_t st) {
+    const size_t smem = tc_smem_bytes(2 * L, F->view.S);
+    auto kern = render_tc_kernel<L, FMT>;
+    int bps = 0;
+    cudaError_t e = prepare(kern, smem, bps);
+    if (e != cudaSuccess) return e;
+    long long want = (src.n_slots + kTcThreads - 1) / kTcThreads;
+    long long grid = (long long)num_sms() * bps;
+    if (want < grid) grid = want;
+    if (grid < 1) grid = 1;
+    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(F->counter);
+    kern<<<(unsigned)grid, kTcThreads, smem, st>>>(F->view, src, out, cnt, static_cast<const uint4 *>(F->tc_w),
+                                                   cnt + 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_render_tc(vrnerf_field *F, const RaySource &src, const RenderOut &out, int prec,
+                             cudaStream_t st) {
+    if (prec != VRNERF_FP16 && prec != VRNERF_BF16) return cudaErrorNotSupported;
+    const int fmt = prec == VRNERF_BF16 ? 1 : 0;
+    cudaError_t e = ensure_tc_image(F, fmt, st);
+    if (e != cudaSuccess) return e;
+    if (F->view.L == 8)
+        return fmt ? render_tc_t<8, 1>(F, src, out, st) : render_tc_t<8, 0>(F, src, out, st);
+    return fmt ? render_tc_t<16, 1>(F, src, out, st) : render_tc_t<16, 0>(F, src, out, st);
+}
+
+template <int L, int FMT>
+static cudaError_t query_tc_t(vrnerf_field *F, const float *pos, const float *dir, const float *radius, int n,
+                              float *sigma, float *rgb, float *feat, cudaStream_t st) {
+    const size_t smem = tc_smem_bytes(2 * L, 0);
+    auto kern = query_tc_kernel<L, FMT>;
+    int bps = 0;
+    cudaError_t e = prepare(kern, smem, bps);
+    if (e != cudaSuccess) return e;
+    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(F->counter);
+    kern<<<(n + kTcThreads - 1) / kTcThreads, kTcThreads, smem, st>>>(
+        F->view, pos, dir, radius, n, sigma, rgb, feat, static_cast<const uint4 *>(F->tc_w), cnt + 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_query_tc(vrnerf_field *F, const float *pos, const float *dir, const float *radius, int n,
+                            float *sigma, float *rgb, float *feat, int prec, cudaStream_t st) {
+    if (prec != VRNERF_FP16 && prec != VRNERF_BF16) return cudaErrorNotSupported;
+    const int fmt = prec == VRNERF_BF16 ? 1 : 0;
+    cudaError_t e = ensure_tc_image(F, fmt, st);
+    if (e != cudaSuccess) return e;
+    if (F->view.L == 8)
+        return fmt ? query_tc_t<8, 1>(F, pos, dir, radius, n, sigma, rgb, feat, st)
+                   : query_tc_t<8, 0>(F, pos, dir, radius, n, sigma, rgb, feat, st);
+    return fmt ? query_tc_t<16, 1>(F, pos, dir, radius, n, sigma, rgb, feat, st)
+               : query_tc_t<16, 0>(F, pos, dir, radius, n, sigma, rgb, feat, st);
 }
 
 }  // namespace vrn

@@ -57,6 +57,7 @@ _SIGS = {
     "vrnerf_field_create": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_uint64, _VP]),
     "vrnerf_field_destroy": (None, [_VP]),
     "vrnerf_field_get_params": (ctypes.c_int, [_VP, _VP, _VP]),
+    "vrnerf_field_status": (ctypes.c_int, [_VP]),
     "vrnerf_field_set_occupancy": (ctypes.c_int, [_VP, _VP]),
     "vrnerf_render": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP]),
     "vrnerf_render_host": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP]),
@@ -187,6 +188,12 @@ def vrnerf_field_create(cfg, grid=None, mlp=None, occ_bits=None, seed=0) -> Fiel
 
 def vrnerf_field_destroy(field: Field):
     field.close()
+
+
+def vrnerf_field_status(field: Field):
+    """Raises VrnerfError if a kernel of the field recorded an error (e.g. a
+    bounded device wait that timed out); clears it."""
+    _check(load().vrnerf_field_status(field.h))
 
 
 def vrnerf_field_get_params(field: Field):

@@ -136,6 +136,41 @@ def test_march_visits_bit_exact(V, cube, room):
         f.close()
 
 
+def test_march_skip_stress_bit_exact(V, cube, room):
+    """Empty-space skipping must reproduce the per-sample occupancy rule on
+    arbitrary rays: random origins and directions, directions close to the
+    axes and to the diagonals, origins on voxel faces and pyramid-block
+    faces, origins outside the box."""
+    rng = np.random.default_rng(21)
+    for sc in (cube, room):
+        cfg = sc.cfg
+        f = V.Field(cfg, sc.grid, sc.mlp, sc.occ_bits)
+        F = O.Field(cfg, sc.grid, sc.mlp, sc.occ_bits)
+        lo, hi = np.array(cfg.aabb_min), np.array(cfg.aabb_max)
+        res = np.array(cfg.occ_res)
+        n = 12000
+        o = lo + (hi - lo) * rng.uniform(-0.05, 1.05, (n, 3))
+        # a third of the origins exactly on voxel or block faces
+        k = n // 3
+        cells = rng.integers(0, res, (k, 3)) // rng.choice([1, 2, 4, 8, 16], (k, 1)) * 1.0
+        o[:k] = lo + (hi - lo) * cells / res
+        d = rng.normal(size=(n, 3))
+        m = n // 4
+        d[k:k + m] = np.eye(3)[rng.integers(0, 3, m)] * rng.choice([-1, 1], (m, 1)) + \
+            rng.normal(scale=1e-4, size=(m, 3)) * rng.integers(0, 2, (m, 1))
+        d[k + m:k + 2 * m] = rng.choice([-1.0, 1.0], (m, 3)) + rng.normal(scale=1e-5, size=(m, 3))
+        d /= np.linalg.norm(d, axis=1, keepdims=True)
+        o, d = o.astype(np.float32), d.astype(np.float32)
+        cap = 64
+        ri, rv, cnt = F.march(o, d, cap)
+        gi, gv, gc = V.vrnerf_debug_march(f, _cuda(o), _cuda(d), cap)
+        gi, gv, gc = gi.cpu().numpy(), gv.cpu().numpy(), gc.cpu().numpy()
+        bad = np.nonzero((gc != cnt) | (gi != ri).any(1) | (gv != rv).any(1))[0]
+        assert bad.size == 0, (bad[:5], o[bad[:2]], d[bad[:2]], cnt[bad[:2]], gc[bad[:2]])
+        assert cnt.sum() > 10000
+        f.close()
+
+
 def test_query_parity(V, cube, room):
     rng = np.random.default_rng(13)
     for sc in (cube, room):

@@ -403,14 +403,25 @@ static cudaError_t ensure_tc_image(vrnerf_field *F, int fmt, cudaStream_t st) {
     return cudaSuccess;
 }
 
+// Resident CTAs per SM from the kernel's registers and shared memory (the
+// runtime's occupancy query under-reports kernels that allocate TMEM), capped
+// so that the CTAs on one SM never ask for more than its 512 TMEM columns.
 template <typename K>
 static cudaError_t prepare(K kern, size_t smem, int &blocks_per_sm) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, kTcThreads, smem);
-    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
+    int dev = 0, regs_sm = 65536, smem_sm = 233472;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    const int regs = ((fa.numRegs + 7) / 8) * 8 * kTcThreads;
+    const int by_regs = regs > 0 ? regs_sm / regs : 8;
+    const int by_smem = smem_sm / (int)(smem + fa.sharedSizeBytes + 1024);
+    blocks_per_sm = by_regs < by_smem ? by_regs : by_smem;
+    if (blocks_per_sm > (int)(512 / kTmemCols)) blocks_per_sm = (int)(512 / kTmemCols);
     if (blocks_per_sm < 1) return cudaErrorInvalidConfiguration;
-    if (blocks_per_sm > (int)(512 / kTmemCols)) return cudaErrorInvalidConfiguration;
     return cudaSuccess;
 }
 

@@ -24,6 +24,8 @@
 namespace vrn {
 
 constexpr int kTcThreads = 128;
+constexpr int kTcMinBlocks = 5;  // resident CTAs per SM the register budget is cut for
+constexpr int kTcChunk = 8;      // march iterations between warp refill points
 constexpr uint32_t kTmemCols = 64;
 
 template <int D>
@@ -223,7 +225,7 @@ __device__ __forceinline__ void finish_ray_tc(const RenderOut &out, long long pi
 }
 
 template <int L, int FMT>
-__global__ void __launch_bounds__(kTcThreads)
+__global__ void __launch_bounds__(kTcThreads, kTcMinBlocks)
 render_tc_kernel(const FieldView f, const RaySource src, const RenderOut out,
                  unsigned long long *__restrict__ counter, const uint4 *__restrict__ wimg,
                  unsigned long long *__restrict__ status) {
@@ -268,7 +270,7 @@ render_tc_kernel(const FieldView f, const RaySource src, const RenderOut out,
                 }
             }
             if (ray >= 0 && !have) {
-                const int mres = march_next(f, sT, mr, p, 32, st_steps);
+                const int mres = march_next(f, sT, mr, p, kTcChunk, st_steps);
                 if (mres == MARCH_SAMPLE) {
                     have = true;
                 } else if (mres == MARCH_END) {

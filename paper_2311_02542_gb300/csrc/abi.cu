@@ -190,6 +190,7 @@ void make_camera_source(const float *c2w, const float *K, const int32_t *res, in
 using namespace vrn;
 
 void vrnerf_field::release() {
+    release_train_scratch(this);
     void *ptrs[] = {grid,     mlp,      occ,         t_tab,  counter, tc_w,   grid_grad, mlp_grad,
                     grid_master, m_grid, v_grid, m_mlp, v_mlp, loss_acc, stage_cam, stage_out, mip};
     for (void *p : ptrs)

@@ -29,6 +29,7 @@ struct vrnerf_field {
     float *grid_master = nullptr;  // fp32 master copy when the grid is stored in fp16
     float *m_grid = nullptr, *v_grid = nullptr, *m_mlp = nullptr, *v_mlp = nullptr;
     float *loss_acc = nullptr;
+    void *train_scratch = nullptr;  // per-batch forward results (C, n, dL/dC)
     int adam_t = 0;
     // render_host staging
     float *stage_cam = nullptr, *stage_out = nullptr;
@@ -45,6 +46,7 @@ int fail(int code, const char *fmt, ...);
 int cuda_fail(cudaError_t e, const char *what);
 uint64_t grid_bytes(const vrnerf_field_desc &d);
 uint64_t grid_entries(const vrnerf_field_desc &d);
+void release_train_scratch(vrnerf_field *F);
 
 // render_tc.cu: tcgen05 tensor-core MLP path
 cudaError_t launch_render_tc(vrnerf_field *F, const RaySource &src, const RenderOut &out, int prec,

@@ -1,0 +1,143 @@
+"""GPU parity of the training path: L1 loss in PQ space, gradients through
+compositing, MLPs and the hash grid, and Adam -- against the fp64 oracle.
+
+Gradients: |gpu - oracle| <= 1e-4 |oracle| + 1e-5 max|oracle| element-wise
+(fp32 accumulation in any order against fp64), the loss within 1e-5
+relative. Adam on given gradients: within 1e-6 of the oracle's update.
+"""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2311_02542_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def V():
+    from paper_2311_02542_gb300 import vrnerf
+    vrnerf.load()
+    return vrnerf
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+
+
+def _crop_rays(sc, size=32, seed=5):
+    poses, intr = S.training_views(sc.occ, sc.cfg, n_views=4, seed=seed)
+    K = S.crop_camera(intr, 112, 112)[None]
+    o, d, r = O.camera_rays(sc.cfg, poses[:1], K, np.array([[size, size]], np.int32))
+    rng = np.random.default_rng(seed)
+    tgt = np.exp(rng.uniform(np.log(1e-3), np.log(1e3), (o.shape[0], 3))).astype(np.float32)
+    return o, d, r, tgt
+
+
+def _check_grads(gg, gm, rg, rm):
+    for got, ref in ((gm, rm), (gg.reshape(-1), rg.reshape(-1))):
+        scale = np.abs(ref).max()
+        assert scale > 0
+        ok = np.abs(got - ref) <= 1e-4 * np.abs(ref) + 1e-5 * scale
+        assert ok.all(), (np.count_nonzero(~ok), np.abs(got - ref)[~ok].max(), scale)
+
+
+@pytest.mark.parametrize("variant", ["room", "room_surface"])
+def test_backward_matches_oracle_on_32x32_crop(V, variant):
+    sc = S.make_scene(variant)
+    cfg = sc.cfg
+    f = V.Field(cfg, sc.grid, sc.mlp, sc.occ_bits)
+    F = O.Field(cfg, sc.grid, sc.mlp, sc.occ_bits)
+    o, d, r, tgt = _crop_rays(sc)
+    loss_ref, rg, rm = F.backward(o, d, r, tgt)
+    loss = V.vrnerf_backward(f, _cuda(o), _cuda(d), _cuda(r), _cuda(tgt))
+    gg, gm = V.vrnerf_field_get_grads(f)
+    assert loss == pytest.approx(loss_ref, rel=1e-5)
+    _check_grads(gg, gm, rg, rm)
+    f.close()
+
+
+def test_backward_unit_cube_with_termination(V):
+    sc = S.make_scene("unit_cube")
+    cfg = replace(sc.cfg, density_bias=4.0)
+    grid = (sc.grid * 50).astype(np.float32)  # features large enough to shape sigma and colour
+    f = V.Field(cfg, grid, sc.mlp, sc.occ_bits)
+    F = O.Field(cfg, grid, sc.mlp, sc.occ_bits)
+    c2w, K, res = S.camera_unit_cube(sc.occ, cfg, 1, 24, 24)
+    o, d, r = O.camera_rays(cfg, c2w, K, res)
+    tgt = np.exp(np.random.default_rng(7).uniform(-3, 3, (o.shape[0], 3))).astype(np.float32)
+    ref = F.render_rays(o, d, r)
+    assert (ref["n"] > 0).sum() > 100 and (ref["T"] < cfg.T_eps).any()
+    loss_ref, rg, rm = F.backward(o, d, r, tgt)
+    loss = V.vrnerf_backward(f, _cuda(o), _cuda(d), _cuda(r), _cuda(tgt))
+    gg, gm = V.vrnerf_field_get_grads(f)
+    assert loss == pytest.approx(loss_ref, rel=1e-5)
+    _check_grads(gg, gm, rg, rm)
+    f.close()
+
+
+def test_adam_step_matches_oracle(V):
+    sc = S.make_scene("unit_cube")
+    cfg = sc.cfg
+    f = V.Field(cfg, sc.grid, sc.mlp, sc.occ_bits)
+    rng = np.random.default_rng(8)
+    p_grid = sc.grid.astype(np.float64).reshape(-1).copy()
+    p_mlp = sc.mlp.astype(np.float64).copy()
+    mg, vg = np.zeros_like(p_grid), np.zeros_like(p_grid)
+    mm, vm = np.zeros_like(p_mlp), np.zeros_like(p_mlp)
+    for t in (1, 2, 3):
+        gg = (rng.normal(size=p_grid.size) * 1e-3 * (rng.uniform(size=p_grid.size) < 0.3)).astype(np.float32)
+        gm = (rng.normal(size=p_mlp.size) * 1e-2).astype(np.float32)
+        V.vrnerf_field_set_grads(f, gg, gm)
+        V.vrnerf_adam_step(f, 0.01, 0.005)
+        O.adam(p_grid, gg.astype(np.float64), mg, vg, t, 0.01)
+        O.adam(p_mlp, gm.astype(np.float64), mm, vm, t, 0.005)
+    g, m = V.vrnerf_field_get_params(f)
+    assert np.max(np.abs(g.reshape(-1) - p_grid)) < 1e-6
+    assert np.max(np.abs(m - p_mlp)) < 1e-6
+    f.close()
+
+
+def test_gpu_gradient_matches_its_own_finite_differences(V):
+    """Central differences of the GPU's own fp32 loss on the MLP weights with
+    the largest gradients (fp32 field, 128 rays)."""
+    sc = S.make_scene("unit_cube")
+    cfg = replace(sc.cfg, T_eps=0.0)
+    grid = (sc.grid * 50).astype(np.float32)
+    c2w, K, res = S.camera_unit_cube(sc.occ, cfg, 1, 16, 8)
+    o, d, r = O.camera_rays(cfg, c2w, K, res)
+    tgt = np.full((o.shape[0], 3), 1e-3, np.float32)
+    args = (_cuda(o), _cuda(d), _cuda(r), _cuda(tgt))
+    f = V.Field(cfg, grid, sc.mlp, sc.occ_bits)
+    V.vrnerf_backward(f, *args)
+    _, gm = V.vrnerf_field_get_grads(f)
+    f.close()
+    picks = np.argsort(-np.abs(gm))[:20]
+    h = 1e-2
+    for i in picks:
+        vals = []
+        for s in (+1, -1):
+            m = sc.mlp.copy()
+            m[i] += s * h
+            ff = V.Field(cfg, grid, m, sc.occ_bits)
+            vals.append(V.vrnerf_backward(ff, *args))
+            ff.close()
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert fd == pytest.approx(gm[i], rel=5e-2, abs=1e-5), (i, fd, gm[i])
+
+
+def test_train_steps_reduce_loss(V):
+    sc = S.make_scene("room")
+    cfg = sc.cfg
+    f = V.Field(cfg, sc.grid, sc.mlp, sc.occ_bits)
+    poses, intr = S.training_views(sc.occ, cfg, n_views=64)
+    o, d, r, tgt = S.training_batch(poses, intr, 1 << 14, seed=5, step=0)
+    args = (_cuda(o), _cuda(d), _cuda(r), _cuda(tgt))
+    losses = [V.vrnerf_train_step(f, *args, lr_grid=0.01, lr_mlp=0.005) for _ in range(30)]
+    assert np.isfinite(losses).all()
+    assert losses[-1] < 0.9 * losses[0], losses[::5]
+    V.vrnerf_field_status(f)
+    f.close()

@@ -219,6 +219,60 @@ int vrnerf_train_step(vrnerf_field *field, const float *rays_o, const float *ray
 int vrnerf_field_set_grads(vrnerf_field *field, const float *grid_grad_host,
                            const float *mlp_grad_host);
 
+/* ---------------------------------------------------------------------------
+ * Serving: continuous batching of render requests (stereo eye pairs and
+ * single views of any resolution) through one persistent tensor-core render
+ * kernel that keeps the field resident and takes rays of newly admitted
+ * requests while earlier ones are still on the GPU; the interactive VR
+ * rendering of Sec. 5 on one GPU.
+ * ------------------------------------------------------------------------- */
+typedef struct vrnerf_server vrnerf_server;
+
+typedef struct {
+    uint64_t completed;        /* requests finished since the last reset */
+    uint64_t rays;             /* their rays */
+    uint64_t kernel_launches;  /* persistent-kernel launches (it leaves when idle) */
+    uint64_t pending, inflight;
+    double p50_ms, p99_ms, max_ms; /* submit-to-output-on-host latency */
+    double wall_s;             /* since the first request after the last reset */
+} vrnerf_serve_stats;
+
+/* Starts a server for `field` on its device: a scheduler thread, two streams
+ * and an output arena of hbm_budget_bytes on the device. A request is
+ * admitted when its output (12 bytes per ray) fits in the arena's free space
+ * and the in-flight views fit the server's view ring (256); otherwise it
+ * waits in arrival order. precision: VRNERF_FP16 or VRNERF_BF16. The server
+ * owns the field until vrnerf_server_destroy: make no other call on the
+ * field meanwhile. EINVAL, ENOMEM. */
+int vrnerf_server_create(vrnerf_field *field, uint64_t hbm_budget_bytes, int32_t precision,
+                         vrnerf_server **out);
+
+/* Queues a request of n_views (1..16) views; every array is host memory and
+ * is copied, except out_host ([sum W*H][3] linear colour, may be NULL),
+ * which must stay valid until vrnerf_poll reports the request. Non-blocking.
+ * *ticket identifies the request. EINVAL (bad view, or output larger than
+ * the whole budget), EBUSY (1024 requests already waiting). */
+int vrnerf_submit(vrnerf_server *server, int32_t n_views, const float *cameras_host,
+                  const float *intrinsics_host, const int32_t *resolution_host, float *out_host,
+                  uint64_t *ticket);
+
+/* Waits up to timeout_ms for the request; VRNERF_OK when its output is in
+ * out_host (the ticket is then released; *latency_ms, if non-NULL, gets the
+ * submit-to-done time), ETIMEDOUT if not yet done, ECANCELED if it was
+ * cancelled (ticket released), ENOTFOUND for an unknown ticket. */
+int vrnerf_poll(vrnerf_server *server, uint64_t ticket, int32_t timeout_ms, double *latency_ms);
+
+/* Cancels a request: a waiting request is dropped, a running one finishes on
+ * the GPU but its output is not copied. Poll it to release the ticket. */
+int vrnerf_cancel(vrnerf_server *server, uint64_t ticket);
+
+/* Latency percentiles and throughput of the requests finished so far. */
+int vrnerf_server_stats(vrnerf_server *server, vrnerf_serve_stats *out);
+int vrnerf_server_reset_stats(vrnerf_server *server);
+
+/* Stops the scheduler, lets the kernel drain and frees the server. */
+void vrnerf_server_destroy(vrnerf_server *server);
+
 /* The fp32 render of vrnerf_render for callers that cannot allocate GPU
  * memory: it calls no cudaMalloc, cudaFree or other allocating routine.
  * The paper has no counterpart; this exists for callers such as a VR

@@ -1,0 +1,691 @@
+// serve.cu -- continuous-batching render server.
+//
+// The paper renders each VR frame as soon as it is asked for (Sec. 5: dual
+// 2K x 2K eye buffers at interactive rates); on one GB300 a stream of stereo
+// and single-view requests of mixed resolution is served by ONE persistent
+// tensor-core render kernel that keeps the field resident and takes work as
+// it arrives:
+//  - the host scheduler admits a request when its output fits in the HBM
+//    budget (a pre-allocated arena) and the view ring has room, writes its
+//    views (camera, intrinsics, resolution, output slice) into a ring in
+//    device memory and publishes the total number of ray slots in a control
+//    block in host-mapped memory;
+//  - the kernel's warps take ray slots from a device counter, never past the
+//    published total; a slot maps to (view, pixel) by a search over the
+//    ring. Rays of different requests share 128-row MLP tiles, so requests
+//    that arrive while others are on the GPU overlap with them on the device;
+//  - every thread counts the slots it finished per view and adds them to
+//    that view's counter in host-mapped memory after a system-scope fence,
+//    so the host sees a view complete only after its output is written; the
+//    host then copies the output slice to the request's buffer;
+//  - when a CTA has no rays and nothing is published, it polls with
+//    __nanosleep and leaves after an idle time limit (or on stop); the host
+//    relaunches the kernel when new work arrives and none is running.
+// No device-side wait is unbounded.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "tc_mlp.cuh"
+
+namespace vrn {
+
+constexpr int kRing = 256;  // views the ring holds; in-flight views stay below this
+
+struct ServeView {
+    float c2w[12];
+    float K[4];
+    int W, H, tiles_x, pad;
+    unsigned long long slot_begin, slot_end;
+    float *out;            // device [W*H][3]
+    unsigned int *done;    // host-mapped: finished slots of this view
+};
+
+struct ServeCtl {                  // host-mapped
+    unsigned long long published;  // ray slots published so far
+    unsigned int n_views;          // views published so far
+    int stop;
+};
+
+__device__ __forceinline__ unsigned long long ld_acquire_sys_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned int ld_acquire_sys_u32(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_acquire_sys_s32(const int *p) {
+    int v;
+    asm volatile("ld.acquire.sys.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T *ldcg_ptr(T *const *p) {
+    return reinterpret_cast<T *>(__ldcg(reinterpret_cast<const unsigned long long *>(p)));
+}
+
+// Index of the ring view holding slot s (views are published in slot order).
+__device__ __forceinline__ int find_view(const ServeView *__restrict__ ring, unsigned int n_views,
+                                         unsigned long long s) {
+    const unsigned int lo = n_views > (unsigned)kRing ? n_views - kRing : 0u;
+    for (unsigned int i = n_views; i > lo; --i) {
+        const ServeView *v = ring + ((i - 1) % kRing);
+        if (__ldcg(&v->slot_begin) <= s) return (int)((i - 1) % kRing);
+    }
+    return -1;
+}
+
+template <int L, int FMT>
+__global__ void __launch_bounds__(kTcThreads, kTcMinBlocks)
+serve_kernel(const FieldView f, const ServeView *__restrict__ ring, const ServeCtl *__restrict__ ctl,
+             unsigned long long *__restrict__ next_slot, const uint4 *__restrict__ wimg,
+             unsigned long long idle_ns, unsigned long long *__restrict__ status) {
+    constexpr int D = 2 * L;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    float *sT;
+    const TcShared S = tc_setup<D>(smem, wimg, sT, f.t_tab, f.S);
+    __shared__ int s_quit;
+
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    bool live = false, ok = true;
+    MarchRay mr;
+    float r = 0.0f, T = 1.0f, C[3] = {0, 0, 0};
+    float *dst = nullptr;
+    int view = -1, cnt_view = -1;
+    unsigned int cnt = 0;  // finished slots of cnt_view not yet reported
+    uint32_t phase = 0;
+    unsigned tested = 0;
+
+    auto flush = [&]() {
+        if (cnt && cnt_view >= 0) {
+            __threadfence_system();
+            atomicAdd_system(ldcg_ptr(&ring[cnt_view].done), cnt);
+        }
+        cnt = 0;
+    };
+    auto count_slot = [&](int v) {
+        if (v != cnt_view) {
+            flush();
+            cnt_view = v;
+        }
+        ++cnt;
+    };
+    auto finish = [&]() {
+        dst[0] = pq_to_linear(C[0]);
+        dst[1] = pq_to_linear(C[1]);
+        dst[2] = pq_to_linear(C[2]);
+        count_slot(view);
+        live = false;
+    };
+
+    while (true) {
+        bool have = false, starved = false;
+        float p[3] = {0, 0, 0};
+        while (true) {
+            const bool need = !live && !starved;
+            const unsigned m = __ballot_sync(FULL, need);
+            if (m) {
+                const int leader = __ffs(m) - 1;
+                unsigned long long base = 0, got = 0;
+                unsigned int nv = 0;
+                if (lane == leader) {
+                    const unsigned long long pub = ld_acquire_sys_u64(&ctl->published);
+                    nv = ld_acquire_sys_u32(&ctl->n_views);
+                    unsigned long long cur = atomicAdd(next_slot, 0ull);
+                    for (int tries = 0; tries < 64 && cur < pub; ++tries) {
+                        const unsigned long long want = min((unsigned long long)__popc(m), pub - cur);
+                        const unsigned long long prev = atomicCAS(next_slot, cur, cur + want);
+                        if (prev == cur) {
+                            base = cur;
+                            got = want;
+                            break;
+                        }
+                        cur = prev;
+                    }
+                }
+                base = __shfl_sync(FULL, base, leader);
+                got = __shfl_sync(FULL, got, leader);
+                nv = __shfl_sync(FULL, nv, leader);
+                if (need) {
+                    const unsigned rank = __popc(m & ((1u << lane) - 1u));
+                    if (rank >= got) {
+                        starved = true;
+                    } else {
+                        const unsigned long long slot = base + rank;
+                        const int v = find_view(ring, nv, slot);
+                        if (v >= 0) {
+                            const ServeView *sv = ring + v;
+                            const int q = (int)(slot - __ldcg(&sv->slot_begin));
+                            const int W = __ldcg(&sv->W), H = __ldcg(&sv->H), tx = __ldcg(&sv->tiles_x);
+                            const int tile = q >> 5, ln = q & 31;
+                            const int px = (tile % tx) * kTileW + (ln & (kTileW - 1));
+                            const int py = (tile / tx) * kTileH + (ln >> 3);
+                            if (px < W && py < H) {
+                                float c2w[12], K[4];
+#pragma unroll
+                                for (int k = 0; k < 12; ++k) c2w[k] = __ldcg(&sv->c2w[k]);
+#pragma unroll
+                                for (int k = 0; k < 4; ++k) K[k] = __ldcg(&sv->K[k]);
+                                camera_ray(c2w, K, px, py, mr.o, mr.d);
+                                r = __fdiv_rn(f.radius_scale, K[0]);
+                                march_init(f, mr);
+                                dst = ldcg_ptr(&sv->out) + 3ll * ((long long)py * W + px);
+                                view = v;
+                                live = true;
+                                T = 1.0f;
+                                C[0] = C[1] = C[2] = 0.0f;
+                            } else {
+                                count_slot(v);  // padding slot of the 8x4 tiling
+                            }
+                        }
+                    }
+                }
+            }
+            if (live && !have) {
+                const int mres = march_next(f, sT, mr, p, kTcChunk, tested);
+                if (mres == MARCH_SAMPLE) have = true;
+                else if (mres == MARCH_END) finish();
+            }
+            if (__all_sync(FULL, have || starved)) break;
+        }
+        if (!__syncthreads_or(have)) {
+            // nothing to shade in this CTA: report, then wait for work or stop
+            flush();
+            if (threadIdx.x == 0) {
+                s_quit = 0;
+                const uint64_t t0 = tc::globaltimer_ns();
+                while (true) {
+                    if (ld_acquire_sys_s32(&ctl->stop)) { s_quit = 1; break; }
+                    if (atomicAdd(next_slot, 0ull) < ld_acquire_sys_u64(&ctl->published)) break;
+                    if (tc::globaltimer_ns() - t0 > idle_ns) { s_quit = 1; break; }
+                    __nanosleep(2000);
+                }
+            }
+            __syncthreads();
+            const bool quit = s_quit != 0 && !__syncthreads_or(live);
+            if (quit || *S.abort) break;
+            continue;
+        }
+        if (*S.abort) break;
+        float feat[D];
+        float delta = 0.0f;
+        if (have) {
+            const float t = sT[mr.step];
+            delta = sT[mr.step + 1] - t;
+            gather_features<L>(f, p, t * r * f.inv_ext, feat);
+        } else {
+#pragma unroll
+            for (int k = 0; k < D; ++k) feat[k] = 0.0f;
+        }
+        float sigma, rgb[3];
+        tc_mlp<D, FMT>(S, feat, mr.d, f.density_bias, sigma, rgb, phase, ok);
+        if (have) {
+            const float sd = sigma * delta;
+            const float w = T * (-expm1f(-sd));
+            C[0] += w * rgb[0];
+            C[1] += w * rgb[1];
+            C[2] += w * rgb[2];
+            T *= expf(-sd);
+            ++mr.step;
+            if (T < f.T_eps) finish();
+        }
+    }
+    flush();
+    tc_teardown(S, status);
+}
+
+template <int L, int FMT>
+static cudaError_t launch_serve_t(vrnerf_field *F, const ServeView *ring, const ServeCtl *ctl,
+                                  unsigned long long *next_slot, unsigned long long idle_ns, cudaStream_t st) {
+    const size_t smem = tc_smem_bytes(2 * L, F->view.S);
+    auto kern = serve_kernel<L, FMT>;
+    int bps = 0;
+    cudaError_t e = prepare_tc(kern, smem, bps);
+    if (e != cudaSuccess) return e;
+    unsigned long long *status = reinterpret_cast<unsigned long long *>(F->counter) + 1;
+    kern<<<num_sms() * bps, kTcThreads, smem, st>>>(F->view, ring, ctl, next_slot,
+                                                    static_cast<const uint4 *>(F->tc_w), idle_ns, status);
+    return cudaGetLastError();
+}
+
+}  // namespace vrn
+
+using namespace vrn;
+
+// ---------------------------------------------------------------------------
+// host scheduler
+// ---------------------------------------------------------------------------
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Req {
+    uint64_t ticket = 0;
+    int n = 0;
+    std::vector<float> c2w, K;
+    std::vector<int32_t> res;
+    float *out_host = nullptr;
+    uint64_t rays = 0, bytes = 0;
+    size_t arena_off = 0;
+    Clock::time_point t_submit, t_done;
+    int views_left = 0;
+    std::vector<int> ring_idx;
+    cudaEvent_t copied = nullptr;
+    int state = 0;  // 0 pending, 1 in flight, 2 copying, 3 done, 4 cancelled
+    bool cancel = false;
+};
+
+struct Arena {  // first-fit sub-allocator over one device buffer (the HBM budget)
+    size_t size = 0;
+    std::map<size_t, size_t> free_;  // offset -> length
+    void init(size_t n) {
+        size = n;
+        free_.clear();
+        free_[0] = n;
+    }
+    bool alloc(size_t n, size_t &off) {
+        n = (n + 255) & ~(size_t)255;
+        for (auto it = free_.begin(); it != free_.end(); ++it)
+            if (it->second >= n) {
+                off = it->first;
+                const size_t rest = it->second - n;
+                free_.erase(it);
+                if (rest) free_[off + n] = rest;
+                return true;
+            }
+        return false;
+    }
+    void release(size_t off, size_t n) {
+        n = (n + 255) & ~(size_t)255;
+        auto it = free_.emplace(off, n).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+};
+
+}  // namespace
+
+struct vrnerf_server {
+    vrnerf_field *F = nullptr;
+    int prec = VRNERF_FP16;
+    uint64_t budget = 0;
+    int max_pending = 1024;
+    unsigned long long idle_ns = 20000000ull;
+    cudaStream_t kst = nullptr, cst = nullptr;
+    ServeView *ring_d = nullptr;
+    ServeView *ring_h = nullptr;  // pinned staging
+    ServeCtl *ctl_h = nullptr, *ctl_d = nullptr;
+    unsigned int *done_h = nullptr, *done_d = nullptr;
+    unsigned long long *next_slot = nullptr;
+    unsigned char *arena_d = nullptr;
+    Arena arena;
+    cudaEvent_t kernel_done = nullptr;
+    bool kernel_launched = false;
+    unsigned long long published = 0;
+    unsigned int n_views = 0, oldest_live_view = 0;
+    std::vector<unsigned long long> view_slots;  // per ring entry: slots of the view
+    std::vector<Req *> view_req;                 // per ring entry
+    std::mutex mu;
+    std::condition_variable cv, done_cv;
+    std::deque<Req *> pending;
+    std::vector<Req *> inflight;
+    std::map<uint64_t, Req *> by_ticket;
+    std::vector<double> latencies_ms;
+    uint64_t next_ticket = 1, rays_done = 0, completed = 0, launches = 0;
+    Clock::time_point t_first;
+    bool have_first = false;
+    std::atomic<bool> quit{false};
+    int error = 0;
+    std::thread worker;
+
+    void run();
+    bool admit_locked(std::vector<int> &new_views);
+    void publish(const std::vector<int> &new_views);
+    void poll_completions();
+    int ensure_kernel();
+};
+
+bool vrnerf_server::admit_locked(std::vector<int> &new_views) {
+    bool any = false;
+    while (!pending.empty()) {
+        Req *q = pending.front();
+        if (q->cancel) {
+            pending.pop_front();
+            q->state = 4;
+            done_cv.notify_all();
+            continue;
+        }
+        if (n_views + q->n - oldest_live_view >= (unsigned)kRing) break;
+        size_t off = 0;
+        if (!arena.alloc(q->bytes, off)) break;  // HBM budget: wait for earlier requests
+        pending.pop_front();
+        q->arena_off = off;
+        q->state = 1;
+        q->views_left = q->n;
+        size_t pix_off = 0;
+        for (int v = 0; v < q->n; ++v) {
+            const int idx = (int)(n_views % kRing);
+            ServeView &sv = ring_h[idx];
+            memcpy(sv.c2w, q->c2w.data() + 12 * v, sizeof sv.c2w);
+            memcpy(sv.K, q->K.data() + 4 * v, sizeof sv.K);
+            sv.W = q->res[2 * v];
+            sv.H = q->res[2 * v + 1];
+            sv.tiles_x = (sv.W + kTileW - 1) / kTileW;
+            const unsigned long long slots =
+                (unsigned long long)sv.tiles_x * ((sv.H + kTileH - 1) / kTileH) * 32ull;
+            sv.slot_begin = published;
+            sv.slot_end = published + slots;
+            sv.out = reinterpret_cast<float *>(arena_d + off) + 3 * pix_off;
+            sv.done = done_d + idx;
+            done_h[idx] = 0;
+            view_slots[idx] = slots;
+            view_req[idx] = q;
+            q->ring_idx.push_back(idx);
+            published += slots;
+            pix_off += (size_t)sv.W * sv.H;
+            ++n_views;
+            new_views.push_back(idx);
+        }
+        inflight.push_back(q);
+        any = true;
+    }
+    return any;
+}
+
+void vrnerf_server::publish(const std::vector<int> &new_views) {
+    // view descriptors -> device ring, then the new totals -> control block
+    for (int idx : new_views)
+        cudaMemcpyAsync(ring_d + idx, ring_h + idx, sizeof(ServeView), cudaMemcpyHostToDevice, cst);
+    cudaStreamSynchronize(cst);
+    __atomic_store_n(&ctl_h->n_views, n_views, __ATOMIC_RELEASE);
+    __atomic_store_n(&ctl_h->published, published, __ATOMIC_RELEASE);
+}
+
+int vrnerf_server::ensure_kernel() {
+    if (kernel_launched && cudaEventQuery(kernel_done) != cudaSuccess) return VRNERF_OK;  // still running
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaError_t e = ensure_tc_image(F, prec == VRNERF_BF16 ? 1 : 0, kst);
+    if (e == cudaSuccess) {
+        const int fmt = prec == VRNERF_BF16 ? 1 : 0;
+        if (F->view.L == 8)
+            e = fmt ? launch_serve_t<8, 1>(F, ring_d, ctl_d, next_slot, idle_ns, kst)
+                    : launch_serve_t<8, 0>(F, ring_d, ctl_d, next_slot, idle_ns, kst);
+        else
+            e = fmt ? launch_serve_t<16, 1>(F, ring_d, ctl_d, next_slot, idle_ns, kst)
+                    : launch_serve_t<16, 0>(F, ring_d, ctl_d, next_slot, idle_ns, kst);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(kernel_done, kst);
+    if (e != cudaSuccess) return cuda_fail(e, "serve kernel launch");
+    kernel_launched = true;
+    ++launches;
+    return VRNERF_OK;
+}
+
+void vrnerf_server::poll_completions() {
+    std::vector<Req *> finished;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        for (Req *q : inflight) {
+            if (q->state == 1) {
+                bool all = true;
+                for (int idx : q->ring_idx)
+                    if (__atomic_load_n(&done_h[idx], __ATOMIC_ACQUIRE) < view_slots[idx]) all = false;
+                if (all) {
+                    if (q->out_host)
+                        cudaMemcpyAsync(q->out_host, arena_d + q->arena_off, q->rays * 12, cudaMemcpyDeviceToHost, cst);
+                    cudaEventRecord(q->copied, cst);
+                    q->state = 2;
+                }
+            }
+            if (q->state == 2 && cudaEventQuery(q->copied) == cudaSuccess) finished.push_back(q);
+        }
+        for (Req *q : finished) {
+            q->t_done = Clock::now();
+            q->state = q->cancel ? 4 : 3;
+            arena.release(q->arena_off, q->bytes);
+            for (int idx : q->ring_idx) view_req[idx] = nullptr;
+            inflight.erase(std::find(inflight.begin(), inflight.end(), q));
+            latencies_ms.push_back(std::chrono::duration<double, std::milli>(q->t_done - q->t_submit).count());
+            rays_done += q->rays;
+            ++completed;
+        }
+        // the oldest view still referenced bounds ring reuse
+        while (oldest_live_view < n_views && !view_req[oldest_live_view % kRing]) ++oldest_live_view;
+    }
+    if (!finished.empty()) done_cv.notify_all();
+}
+
+void vrnerf_server::run() {
+    cudaSetDevice(F->device);
+    while (!quit.load()) {
+        std::vector<int> nv;
+        bool work;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            if (pending.empty() && inflight.empty())
+                cv.wait_for(lk, std::chrono::milliseconds(5));
+            admit_locked(nv);
+            work = !inflight.empty();
+        }
+        if (!nv.empty()) publish(nv);
+        if (work) {
+            int rc = ensure_kernel();
+            if (rc) {
+                std::lock_guard<std::mutex> lk(mu);
+                error = rc;
+            }
+        }
+        poll_completions();
+        if (work) std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
+
+extern "C" {
+
+int vrnerf_server_create(vrnerf_field *F, uint64_t hbm_budget_bytes, int32_t precision, vrnerf_server **out) {
+    if (!F || !out) return fail(VRNERF_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (precision != VRNERF_FP16 && precision != VRNERF_BF16)
+        return fail(VRNERF_EINVAL, "the server renders with the fp16 or bf16 tensor-core path");
+    if (hbm_budget_bytes < (1u << 20)) return fail(VRNERF_EINVAL, "budget below 1 MiB");
+    vrnerf_server *S = new vrnerf_server();
+    S->F = F;
+    S->prec = precision;
+    S->budget = hbm_budget_bytes;
+    S->view_slots.assign(kRing, 0);
+    S->view_req.assign(kRing, nullptr);
+    cudaError_t e = cudaSetDevice(F->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->kst, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->cst, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&S->ring_d, sizeof(ServeView) * kRing);
+    if (e == cudaSuccess) e = cudaMallocHost(&S->ring_h, sizeof(ServeView) * kRing);
+    if (e == cudaSuccess) e = cudaHostAlloc(&S->ctl_h, sizeof(ServeCtl), cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostAlloc(&S->done_h, sizeof(unsigned int) * kRing, cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(&S->ctl_d, S->ctl_h, 0);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(&S->done_d, S->done_h, 0);
+    if (e == cudaSuccess) e = cudaMalloc(&S->next_slot, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(S->next_slot, 0, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&S->arena_d, hbm_budget_bytes);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->kernel_done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        vrnerf_server_destroy(S);
+        return fail(VRNERF_ENOMEM, "server resources: %s", cudaGetErrorString(e));
+    }
+    memset(S->ctl_h, 0, sizeof(ServeCtl));
+    memset(S->done_h, 0, sizeof(unsigned int) * kRing);
+    S->arena.init(hbm_budget_bytes);
+    S->worker = std::thread([S] { S->run(); });
+    *out = S;
+    return VRNERF_OK;
+}
+
+int vrnerf_submit(vrnerf_server *S, int32_t n_views, const float *cameras_host, const float *intrinsics_host,
+                  const int32_t *resolution_host, float *out_host, uint64_t *ticket) {
+    if (!S || !cameras_host || !intrinsics_host || !resolution_host || !ticket)
+        return fail(VRNERF_EINVAL, "NULL argument");
+    if (n_views < 1 || n_views > 16) return fail(VRNERF_EINVAL, "a request holds 1 to 16 views");
+    Req *q = new Req();
+    q->n = n_views;
+    q->c2w.assign(cameras_host, cameras_host + 12 * n_views);
+    q->K.assign(intrinsics_host, intrinsics_host + 4 * n_views);
+    q->res.assign(resolution_host, resolution_host + 2 * n_views);
+    for (int v = 0; v < n_views; ++v) {
+        if (q->res[2 * v] < 1 || q->res[2 * v] > 16384 || q->res[2 * v + 1] < 1 || q->res[2 * v + 1] > 16384 ||
+            !(q->K[4 * v] > 0.0f) || !(q->K[4 * v + 1] > 0.0f)) {
+            delete q;
+            return fail(VRNERF_EINVAL, "view %d: bad resolution or focal length", v);
+        }
+        q->rays += (uint64_t)q->res[2 * v] * q->res[2 * v + 1];
+    }
+    q->bytes = q->rays * 12;
+    if (q->bytes > S->budget) {
+        delete q;
+        return fail(VRNERF_EINVAL, "request needs %llu bytes, more than the server's HBM budget",
+                    (unsigned long long)q->rays * 12);
+    }
+    q->out_host = out_host;
+    if (cudaEventCreateWithFlags(&q->copied, cudaEventDisableTiming) != cudaSuccess) {
+        delete q;
+        return fail(VRNERF_ENOMEM, "event");
+    }
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->error) {
+        cudaEventDestroy(q->copied);
+        delete q;
+        return fail(S->error, "server failed: %s", "kernel launch error");
+    }
+    if ((int)S->pending.size() >= S->max_pending) {
+        cudaEventDestroy(q->copied);
+        delete q;
+        return fail(VRNERF_EBUSY, "admission queue full");
+    }
+    q->ticket = S->next_ticket++;
+    q->t_submit = Clock::now();
+    if (!S->have_first) {
+        S->t_first = q->t_submit;
+        S->have_first = true;
+    }
+    S->pending.push_back(q);
+    S->by_ticket[q->ticket] = q;
+    *ticket = q->ticket;
+    S->cv.notify_all();
+    return VRNERF_OK;
+}
+
+int vrnerf_poll(vrnerf_server *S, uint64_t ticket, int32_t timeout_ms, double *latency_ms) {
+    if (!S) return fail(VRNERF_EINVAL, "NULL argument");
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->by_ticket.find(ticket);
+    if (it == S->by_ticket.end()) return fail(VRNERF_ENOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    Req *q = it->second;
+    auto deadline = Clock::now() + std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms);
+    while (q->state < 3 && !S->error) {
+        if (S->done_cv.wait_until(lk, deadline) == std::cv_status::timeout && q->state < 3) break;
+    }
+    if (q->state < 3) {
+        if (S->error) return fail(S->error, "server failed");
+        return fail(VRNERF_ETIMEDOUT, "request %llu not finished", (unsigned long long)ticket);
+    }
+    const int state = q->state;
+    if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(q->t_done - q->t_submit).count();
+    S->by_ticket.erase(it);
+    cudaEventDestroy(q->copied);
+    delete q;
+    return state == 4 ? fail(VRNERF_ECANCELED, "request %llu was cancelled", (unsigned long long)ticket)
+                      : VRNERF_OK;
+}
+
+int vrnerf_cancel(vrnerf_server *S, uint64_t ticket) {
+    if (!S) return fail(VRNERF_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->by_ticket.find(ticket);
+    if (it == S->by_ticket.end()) return fail(VRNERF_ENOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    // pending: dropped at admission; in flight: rendered, but not copied out
+    it->second->cancel = true;
+    if (it->second->state <= 1) it->second->out_host = nullptr;
+    S->cv.notify_all();
+    return VRNERF_OK;
+}
+
+int vrnerf_server_stats(vrnerf_server *S, vrnerf_serve_stats *st) {
+    if (!S || !st) return fail(VRNERF_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    memset(st, 0, sizeof *st);
+    st->completed = S->completed;
+    st->rays = S->rays_done;
+    st->kernel_launches = S->launches;
+    st->pending = S->pending.size();
+    st->inflight = S->inflight.size();
+    std::vector<double> l = S->latencies_ms;
+    if (!l.empty()) {
+        std::sort(l.begin(), l.end());
+        st->p50_ms = l[(size_t)(0.50 * (l.size() - 1))];
+        st->p99_ms = l[(size_t)(0.99 * (l.size() - 1))];
+        st->max_ms = l.back();
+    }
+    if (S->have_first)
+        st->wall_s = std::chrono::duration<double>(Clock::now() - S->t_first).count();
+    return VRNERF_OK;
+}
+
+int vrnerf_server_reset_stats(vrnerf_server *S) {
+    if (!S) return fail(VRNERF_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->latencies_ms.clear();
+    S->rays_done = 0;
+    S->completed = 0;
+    S->launches = 0;
+    S->have_first = false;
+    return VRNERF_OK;
+}
+
+void vrnerf_server_destroy(vrnerf_server *S) {
+    if (!S) return;
+    if (S->worker.joinable()) {
+        S->quit.store(true);
+        S->cv.notify_all();
+        S->worker.join();
+    }
+    if (S->ctl_h) __atomic_store_n(&S->ctl_h->stop, 1, __ATOMIC_RELEASE);
+    if (S->kst) cudaStreamSynchronize(S->kst);
+    if (S->cst) cudaStreamSynchronize(S->cst);
+    for (auto &kv : S->by_ticket) {
+        if (kv.second->copied) cudaEventDestroy(kv.second->copied);
+        delete kv.second;
+    }
+    if (S->kernel_done) cudaEventDestroy(S->kernel_done);
+    if (S->arena_d) cudaFree(S->arena_d);
+    if (S->next_slot) cudaFree(S->next_slot);
+    if (S->done_h) cudaFreeHost(S->done_h);
+    if (S->ctl_h) cudaFreeHost(S->ctl_h);
+    if (S->ring_h) cudaFreeHost(S->ring_h);
+    if (S->ring_d) cudaFree(S->ring_d);
+    if (S->kst) cudaStreamDestroy(S->kst);
+    if (S->cst) cudaStreamDestroy(S->cst);
+    delete S;
+}
+
+}  // extern "C"

@@ -1,0 +1,254 @@
+// tc_mlp.cuh -- the density and colour MLPs (Sec. 6) on tcgen05 tensor
+// cores for one 128-row tile per CTA, shared by the render, query and
+// serving kernels: operand layout, per-layer issue / commit / wait, TMEM
+// epilogues, CTA set-up and tear-down, and the host-side launch helpers.
+#pragma once
+#include "field.h"
+#include "tc.cuh"
+
+namespace vrn {
+
+constexpr int kTcThreads = 128;
+constexpr int kTcMinBlocks = 5;  // resident CTAs per SM the register budget is cut for
+constexpr int kTcChunk = 8;      // march iterations between warp refill points
+constexpr uint32_t kTmemCols = 64;
+
+template <int D>
+struct TcW {  // byte offsets of the weight image (K-major operands)
+    static constexpr int w1 = 0;                 // [64][D]
+    static constexpr int w2 = w1 + 64 * D * 2;   // [16][64]
+    static constexpr int w3 = w2 + 16 * 64 * 2;  // [64][32]
+    static constexpr int w4 = w3 + 64 * 32 * 2;  // [64][64]
+    static constexpr int w5 = w4 + 64 * 64 * 2;  // [16][64], rows 3..15 zero
+    static constexpr int bytes = w5 + 16 * 64 * 2;
+};
+
+struct TcShared {
+    unsigned char *w;     // weight image
+    unsigned char *act;   // 128 x 64 operand tile
+    uint64_t *mbar;
+    volatile int *abort;
+    uint32_t tbase;       // TMEM base address (lane 0, column 0)
+};
+
+template <int FMT>
+__device__ __forceinline__ uint32_t pack2(float a, float b) {
+    if (FMT == 0) {
+        __half2 h = __floats2half2_rn(a, b);
+        return *reinterpret_cast<uint32_t *>(&h);
+    } else {
+        __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<uint32_t *>(&h);
+    }
+}
+
+// Row r of a 128 x K operand tile (K-major core matrices).
+template <int K>
+__device__ __forceinline__ void store_row(unsigned char *base, int r, const uint32_t (&pk)[K / 2]) {
+#pragma unroll
+    for (int j = 0; j < K / 8; ++j) {
+        uint4 v = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+        *reinterpret_cast<uint4 *>(base + (r >> 3) * (K / 8) * 128 + j * 128 + (r & 7) * 16) = v;
+    }
+}
+
+template <int K, int N, int FMT>
+__device__ __forceinline__ void issue_layer(uint32_t a_addr, uint32_t b_addr, uint32_t tmem) {
+    constexpr uint32_t sbo = (K / 8) * 128;
+    constexpr uint32_t idesc = tc::idesc_f16(N, FMT);
+#pragma unroll
+    for (int ks = 0; ks < K / 16; ++ks)
+        tc::mma_f16(tmem, tc::smem_desc(a_addr + ks * 256, 128, sbo), tc::smem_desc(b_addr + ks * 256, 128, sbo),
+                    idesc, ks > 0 ? 1u : 0u);
+}
+
+// Runs one layer: the tile's rows are written; all threads sync, thread 0
+// issues and commits, everyone waits for the accumulators.
+template <int K, int N, int FMT>
+__device__ __forceinline__ void run_layer(const TcShared &S, int w_off, uint32_t &phase, bool &ok) {
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        tc::fence_after_sync();
+        issue_layer<K, N, FMT>(tc::smem_u32(S.act), tc::smem_u32(S.w) + w_off, S.tbase);
+        tc::mma_commit(S.mbar);
+    }
+    ok = tc::mbar_wait_bounded(S.mbar, phase, S.abort) && ok;
+    phase ^= 1u;
+    tc::fence_after_sync();
+}
+
+// Density MLP (D -> 64 -> 16, ReLU; sigma = exp(o_0 + bias)) and colour MLP
+// ([o, SH(d)] 32 -> 64 -> 64 -> 3, ReLU, sigmoid) for the 128 rows of the
+// CTA; this thread's row is `feat`. All 128 threads must call it.
+template <int D, int FMT>
+__device__ __forceinline__ void tc_mlp(const TcShared &S, const float (&feat)[D], const float dir[3],
+                                       float density_bias, float &sigma, float rgb[3], uint32_t &phase,
+                                       bool &ok) {
+    using W = TcW<D>;
+    const int r = threadIdx.x;
+    const uint32_t taddr = S.tbase + ((uint32_t)(r & ~31) << 16);
+    {
+        uint32_t pk[D / 2];
+#pragma unroll
+        for (int i = 0; i < D / 2; ++i) pk[i] = pack2<FMT>(feat[2 * i], feat[2 * i + 1]);
+        store_row<D>(S.act, r, pk);
+    }
+    run_layer<D, 64, FMT>(S, W::w1, phase, ok);
+    {
+        uint32_t pk[32];
+#pragma unroll
+        for (int c = 0; c < 64; c += 16) {
+            float v[16];
+            tc::tmem_ld16(taddr + c, v);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) pk[c / 2 + i] = pack2<FMT>(fmaxf(v[2 * i], 0.f), fmaxf(v[2 * i + 1], 0.f));
+        }
+        store_row<64>(S.act, r, pk);
+    }
+    run_layer<64, 16, FMT>(S, W::w2, phase, ok);
+    {
+        float o[16], sh[16];
+        tc::tmem_ld16(taddr, o);
+        sigma = expf(o[0] + density_bias);
+        sh16(dir[0], dir[1], dir[2], sh);
+        uint32_t pk[16];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            pk[i] = pack2<FMT>(o[2 * i], o[2 * i + 1]);
+            pk[8 + i] = pack2<FMT>(sh[2 * i], sh[2 * i + 1]);
+        }
+        store_row<32>(S.act, r, pk);
+    }
+    run_layer<32, 64, FMT>(S, W::w3, phase, ok);
+    {
+        uint32_t pk[32];
+#pragma unroll
+        for (int c = 0; c < 64; c += 16) {
+            float v[16];
+            tc::tmem_ld16(taddr + c, v);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) pk[c / 2 + i] = pack2<FMT>(fmaxf(v[2 * i], 0.f), fmaxf(v[2 * i + 1], 0.f));
+        }
+        store_row<64>(S.act, r, pk);
+    }
+    run_layer<64, 64, FMT>(S, W::w4, phase, ok);
+    {
+        uint32_t pk[32];
+#pragma unroll
+        for (int c = 0; c < 64; c += 16) {
+            float v[16];
+            tc::tmem_ld16(taddr + c, v);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) pk[c / 2 + i] = pack2<FMT>(fmaxf(v[2 * i], 0.f), fmaxf(v[2 * i + 1], 0.f));
+        }
+        store_row<64>(S.act, r, pk);
+    }
+    run_layer<64, 16, FMT>(S, W::w5, phase, ok);
+    {
+        float z[16];
+        tc::tmem_ld16(taddr, z);
+        rgb[0] = 1.0f / (1.0f + expf(-z[0]));
+        rgb[1] = 1.0f / (1.0f + expf(-z[1]));
+        rgb[2] = 1.0f / (1.0f + expf(-z[2]));
+    }
+    tc::fence_before_sync();  // this tile's TMEM reads precede the next tile's MMAs
+}
+
+// Shared-memory carve-up, weight upload, mbarrier and TMEM set-up.
+template <int D>
+__device__ __forceinline__ TcShared tc_setup(unsigned char *smem, const uint4 *__restrict__ wimg,
+                                             float *&sT, const float *__restrict__ t_tab, int S_steps) {
+    using W = TcW<D>;
+    TcShared S;
+    S.w = smem;
+    S.act = smem + ((W::bytes + 1023) & ~1023);
+    sT = reinterpret_cast<float *>(S.act + 128 * 64 * 2);
+    const int nt = S_steps + 1;
+    unsigned char *misc = reinterpret_cast<unsigned char *>(sT + ((nt + 3) & ~3));
+    S.mbar = reinterpret_cast<uint64_t *>(misc);
+    uint32_t *holder = reinterpret_cast<uint32_t *>(misc + 8);
+    S.abort = reinterpret_cast<volatile int *>(misc + 12);
+    for (int i = threadIdx.x; i < W::bytes / 16; i += blockDim.x)
+        reinterpret_cast<uint4 *>(S.w)[i] = wimg[i];
+    if (t_tab)
+        for (int i = threadIdx.x; i < nt; i += blockDim.x) sT[i] = t_tab[i];
+    if (threadIdx.x == 0) {
+        tc::mbar_init(S.mbar, 1);
+        *S.abort = 0;
+    }
+    if (threadIdx.x < 32) {
+        tc::tmem_alloc(holder, kTmemCols);
+        tc::tmem_relinquish();
+    }
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    S.tbase = *holder;
+    return S;
+}
+
+__device__ __forceinline__ void tc_teardown(const TcShared &S, unsigned long long *status) {
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (threadIdx.x == 0 && *S.abort && status) atomicExch(status, (unsigned long long)(-VRNERF_ETIMEDOUT));
+    if (threadIdx.x < 32) tc::tmem_dealloc(S.tbase, kTmemCols);
+}
+
+
+// fp32 W1..W5 -> the K-major operand image of TcW<D>, fp16 or bf16.
+__global__ void build_tc_image_kernel(const float *__restrict__ mlp, int D, int fmt,
+                                      unsigned char *__restrict__ img);
+
+inline size_t tc_smem_bytes(int D, int S_steps) {
+    const size_t wb = (size_t)(64 * D * 2 + 16 * 64 * 2 + 64 * 32 * 2 + 64 * 64 * 2 + 16 * 64 * 2);
+    size_t b = ((wb + 1023) & ~(size_t)1023) + 128 * 64 * 2 + sizeof(float) * (size_t)((S_steps + 1 + 3) & ~3) + 64;
+    // at most 512 / kTmemCols CTAs per SM, so tcgen05.alloc never waits
+    const size_t floor_bytes = (size_t)(232448 / (512 / kTmemCols)) + 1024;
+    return b > floor_bytes ? b : floor_bytes;
+}
+
+inline cudaError_t ensure_tc_image(vrnerf_field *F, int fmt, cudaStream_t st) {
+    const int D = F->view.d_in;
+    const size_t bytes = (size_t)(64 * D * 2 + 16 * 64 * 2 + 64 * 32 * 2 + 64 * 64 * 2 + 16 * 64 * 2);
+    if (F->tc_w && F->tc_prec == fmt && F->tc_version == F->mlp_version) return cudaSuccess;
+    if (!F->tc_w) {
+        cudaError_t e = cudaMalloc(&F->tc_w, bytes);
+        if (e != cudaSuccess) return e;
+        F->tc_w_bytes = bytes;
+    }
+    const int n = (int)(bytes / 2);
+    build_tc_image_kernel<<<(n + 255) / 256, 256, 0, st>>>(F->mlp, D, fmt, static_cast<unsigned char *>(F->tc_w));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    F->tc_prec = fmt;
+    F->tc_version = F->mlp_version;
+    return cudaSuccess;
+}
+
+// Resident CTAs per SM from the kernel's registers and shared memory (the
+// runtime's occupancy query under-reports kernels that allocate TMEM), capped
+// so that the CTAs on one SM never ask for more than its 512 TMEM columns.
+template <typename K>
+inline cudaError_t prepare_tc(K kern, size_t smem, int &blocks_per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
+    int dev = 0, regs_sm = 65536, smem_sm = 233472;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    const int regs = ((fa.numRegs + 7) / 8) * 8 * kTcThreads;
+    const int by_regs = regs > 0 ? regs_sm / regs : 8;
+    const int by_smem = smem_sm / (int)(smem + fa.sharedSizeBytes + 1024);
+    blocks_per_sm = by_regs < by_smem ? by_regs : by_smem;
+    if (blocks_per_sm > (int)(512 / kTmemCols)) blocks_per_sm = (int)(512 / kTmemCols);
+    if (blocks_per_sm < 1) return cudaErrorInvalidConfiguration;
+    return cudaSuccess;
+}
+
+}  // namespace vrn

@@ -71,7 +71,21 @@ _SIGS = {
     "vrnerf_adam_step": (ctypes.c_int, [_VP, _F, _F, _VP]),
     "vrnerf_train_step": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _I32, _F, _F, _VP, _VP]),
     "vrnerf_render_noalloc": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _I32, _VP, _VP]),
+    "vrnerf_server_create": (ctypes.c_int, [_VP, ctypes.c_uint64, _I32, _VP]),
+    "vrnerf_submit": (ctypes.c_int, [_VP, _I32, _VP, _VP, _VP, _VP, _VP]),
+    "vrnerf_poll": (ctypes.c_int, [_VP, ctypes.c_uint64, _I32, _VP]),
+    "vrnerf_cancel": (ctypes.c_int, [_VP, ctypes.c_uint64]),
+    "vrnerf_server_stats": (ctypes.c_int, [_VP, _VP]),
+    "vrnerf_server_reset_stats": (ctypes.c_int, [_VP]),
+    "vrnerf_server_destroy": (None, [_VP]),
 }
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_uint64), ("rays", ctypes.c_uint64),
+                ("kernel_launches", ctypes.c_uint64), ("pending", ctypes.c_uint64),
+                ("inflight", ctypes.c_uint64), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double), ("wall_s", ctypes.c_double)]
 
 _lib = None
 
@@ -343,3 +357,59 @@ def vrnerf_render_noalloc(cfg, grid, mlp, occ_bits, cameras, intrinsics, resolut
                                         _ptr(_dev(cameras)), _ptr(_dev(intrinsics)), _ptr(res),
                                         res.shape[0], _ptr(_dev(out)), _stream(stream)))
     return out
+
+
+class Server:
+    """Continuous-batching render server (vrnerf_server_*). Holds references
+    to the host arrays of every request until it is polled."""
+
+    def __init__(self, field: Field, hbm_budget_bytes: int, precision=FP16):
+        self.field = field
+        h = ctypes.c_void_p()
+        p = PRECISIONS.get(precision, precision) if isinstance(precision, str) else int(precision)
+        _check(load().vrnerf_server_create(field.h, ctypes.c_uint64(int(hbm_budget_bytes)), p,
+                                           ctypes.byref(h)))
+        self.h = h
+        self._keep = {}
+
+    def submit(self, cameras, intrinsics, resolution, out=None):
+        cams = np.ascontiguousarray(cameras, np.float32).reshape(-1, 3, 4)
+        K = np.ascontiguousarray(intrinsics, np.float32).reshape(-1, 4)
+        res = np.ascontiguousarray(resolution, np.int32).reshape(-1, 2)
+        t = ctypes.c_uint64()
+        _check(load().vrnerf_submit(self.h, cams.shape[0], _ptr(cams), _ptr(K), _ptr(res),
+                                    _ptr(out) if out is not None else None, ctypes.byref(t)))
+        self._keep[t.value] = out
+        return t.value
+
+    def poll(self, ticket, timeout_ms=10000):
+        lat = ctypes.c_double()
+        rc = load().vrnerf_poll(self.h, ctypes.c_uint64(ticket), int(timeout_ms), ctypes.byref(lat))
+        if rc in (OK, ECANCELED):
+            self._keep.pop(ticket, None)
+        _check(rc)
+        return lat.value
+
+    def cancel(self, ticket):
+        _check(load().vrnerf_cancel(self.h, ctypes.c_uint64(ticket)))
+
+    def stats(self):
+        st = ServerStats()
+        _check(load().vrnerf_server_stats(self.h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def reset_stats(self):
+        _check(load().vrnerf_server_reset_stats(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().vrnerf_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        if _lib is not None:
+            self.close()
+
+
+def vrnerf_server_create(field: Field, hbm_budget_bytes: int, precision=FP16) -> Server:
+    return Server(field, hbm_budget_bytes, precision)

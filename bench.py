@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--variant", default="room", choices=["room", "room_surface"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--serving-requests", type=int, default=300,
+                    help="requests of the Poisson serving stream (0: skip)")
+    ap.add_argument("--train-steps", type=int, default=5, help="timed 2^20-ray train steps (0: skip)")
     ap.add_argument("--profile-case", action="store_true",
                     help="small case for ncu: two renders of a 1024x1024 window of the room frame")
     return ap.parse_args()
@@ -175,6 +178,96 @@ def reference_arm(args):
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def serving_bench(V, field, sc, n_req, warm=30, rate_hz=36.0 / 0.7, seed=4, in_flight=24):
+    """Poisson stream of render requests (70 % stereo 2 x 2048^2, 30 % single
+    views of side 512 / 1024 / 1536, random 6-DoF poses in the room) through
+    the continuous-batching server; outputs are copied to pinned host buffers.
+    Returns per-request latency percentiles and throughput."""
+    import queue
+    import threading
+
+    import torch
+    from paper_2311_02542_gb300 import synth as S
+    reqs = S.request_stream(sc.occ, sc.cfg, n_req + warm, seed=seed, rate_hz=rate_hz)
+    srv = V.Server(field, 6 << 30, V.FP16)
+    maxr = max(r.rays for r in reqs)
+    bufs = [torch.empty((maxr, 3), dtype=torch.float32, pin_memory=True).numpy()
+            for _ in range(in_flight)]
+    free, done, lat = queue.Queue(), queue.Queue(), {}
+    for i in range(in_flight):
+        free.put(i)
+
+    def poller():
+        while True:
+            item = done.get()
+            if item is None:
+                return
+            i, t, b = item
+            lat[i] = srv.poll(t, 120000)
+            free.put(b)
+
+    th = threading.Thread(target=poller)
+    th.start()
+    t0 = time.perf_counter()
+    t_meas = t0
+    for i, r in enumerate(reqs):
+        wait = t0 + r.arrival_s - time.perf_counter()
+        if wait > 0 and rate_hz < 1e5:
+            time.sleep(wait)
+        if i == warm:
+            srv.reset_stats()
+            t_meas = time.perf_counter()
+        b = free.get()
+        done.put((i, srv.submit(r.c2w, r.intrinsics, r.resolution, bufs[b][:r.rays]), b))
+    done.put(None)
+    th.join()
+    wall = time.perf_counter() - t_meas
+    st = srv.stats()
+    srv.close()
+    meas = range(warm, len(reqs))
+    st_lat = np.array([lat[i] for i in meas if reqs[i].stereo])
+    all_lat = np.array([lat[i] for i in meas])
+    rays = sum(reqs[i].rays for i in meas)
+    return {"requests": len(meas), "offered_req_s": round(rate_hz, 2) if rate_hz < 1e5 else "saturating",
+            "stereo_p50_ms": round(float(np.percentile(st_lat, 50)), 3),
+            "stereo_p99_ms": round(float(np.percentile(st_lat, 99)), 3),
+            "all_p50_ms": round(float(np.percentile(all_lat, 50)), 3),
+            "all_p99_ms": round(float(np.percentile(all_lat, 99)), 3),
+            "Mrays_s": round(rays / wall / 1e6, 2), "wall_s": round(wall, 2),
+            "kernel_launches": int(st["kernel_launches"]),
+            "note": "latency = submit to image in pinned host memory; fp16 tensor-core MLP"}
+
+
+def train_bench(V, sc, steps):
+    """Training step on a 2^20-ray batch drawn from 64 synthetic HDR views
+    (targets log-uniform in [1e-3, 1e3]); forward, loss, backward, Adam."""
+    import torch
+    from paper_2311_02542_gb300 import synth as S
+    field = V.Field(sc.cfg, sc.grid, sc.mlp, sc.occ_bits)
+    poses, intr = S.training_views(sc.occ, sc.cfg, n_views=64)
+    batches = []
+    for k in range(2):
+        o, d, r, tgt = S.training_batch(poses, intr, 1 << 20, seed=5, step=k)
+        batches.append([torch.from_numpy(a).cuda() for a in (o, d, r, tgt)])
+    for k in range(2):
+        V.vrnerf_train_step(field, *batches[k % 2])
+    torch.cuda.synchronize()
+    ts, losses = [], []
+    for k in range(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        V.vrnerf_train_step(field, *batches[k % 2], want_loss=False)
+        b.record()
+        ts.append((a, b))
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ts]))
+    loss = V.vrnerf_backward(field, *batches[0])
+    field.close()
+    return {"batch_rays": 1 << 20, "ms_per_step": round(ms, 3),
+            "Mrays_s": round((1 << 20) / (ms * 1e-3) / 1e6, 2), "loss": round(float(loss), 6),
+            "steps": steps, "mlp": "fp32 (CUDA cores)"}
 
 
 def profile_case(args):
@@ -335,6 +428,12 @@ def main():
         "clocks": clocks,
         "wall_s_timed": round(wall, 3),
     }
+    if args.serving_requests > 0:
+        line["serving"] = serving_bench(V, field, sc, args.serving_requests)
+        line["serving_saturated"] = serving_bench(V, field, sc, max(60, args.serving_requests // 3),
+                                                  warm=10, rate_hz=1e9)
+    if args.train_steps > 0:
+        line["train_step"] = train_bench(V, sc, args.train_steps)
     if rank == 0 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
         crays, cdt = run_oracle_sample(sc, c2w, K, args.cpu_seconds, threads)

@@ -115,8 +115,8 @@ def test_serving_cancel_unknown_and_timeout(V, room):
 def test_serving_relaunches_after_idle_exit(V, room):
     f = V.Field(room.cfg, room.grid, room.mlp, room.occ_bits)
     c2w, K, res = S.camera_room(room.occ, room.cfg, 2, 64, 64)
-    srv = V.Server(f, 16 << 20, "fp16")
     ref = _alone(V, f, c2w, K, res)
+    srv = V.Server(f, 16 << 20, "fp16")
     for _ in range(3):
         out = np.zeros((64 * 64, 3), np.float32)
         srv.poll(srv.submit(c2w, K, res, out), 20000)

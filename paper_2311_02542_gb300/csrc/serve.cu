@@ -10,10 +10,11 @@
 //    views (camera, intrinsics, resolution, output slice) into a ring in
 //    device memory and publishes the total number of ray slots in a control
 //    block in host-mapped memory;
-//  - the kernel's warps take ray slots from a device counter, never past the
-//    published total; a slot maps to (view, pixel) by a search over the
-//    ring. Rays of different requests share 128-row MLP tiles, so requests
-//    that arrive while others are on the GPU overlap with them on the device;
+//  - the kernel's warps take ray slots by fetch-and-add on the slot counter of
+//    the oldest published view that still has slots (a monotonic view cursor
+//    skips exhausted views; overshoot on an exhausted view is ignored). Rays
+//    of different requests share 128-row MLP tiles, so requests that arrive
+//    while others are on the GPU overlap with them on the device;
 //  - every thread counts the slots it finished per view and adds them to
 //    that view's counter in host-mapped memory after a system-scope fence,
 //    so the host sees a view complete only after its output is written; the
@@ -46,10 +47,11 @@ struct ServeView {
     unsigned long long slot_begin, slot_end;
     float *out;            // device [W*H][3]
     unsigned int *done;    // host-mapped: finished slots of this view
+    unsigned long long taken;  // slots handed out (fetch-and-add; may overshoot)
 };
 
 struct ServeCtl {                  // host-mapped
-    unsigned long long published;  // ray slots published so far
+    unsigned long long published;  // ray slots published so far (statistics)
     unsigned int n_views;          // views published so far
     int stop;
 };
@@ -75,21 +77,10 @@ __device__ __forceinline__ T *ldcg_ptr(T *const *p) {
     return reinterpret_cast<T *>(__ldcg(reinterpret_cast<const unsigned long long *>(p)));
 }
 
-// Index of the ring view holding slot s (views are published in slot order).
-__device__ __forceinline__ int find_view(const ServeView *__restrict__ ring, unsigned int n_views,
-                                         unsigned long long s) {
-    const unsigned int lo = n_views > (unsigned)kRing ? n_views - kRing : 0u;
-    for (unsigned int i = n_views; i > lo; --i) {
-        const ServeView *v = ring + ((i - 1) % kRing);
-        if (__ldcg(&v->slot_begin) <= s) return (int)((i - 1) % kRing);
-    }
-    return -1;
-}
-
 template <int L, int FMT>
 __global__ void __launch_bounds__(kTcThreads, kTcMinBlocks)
-serve_kernel(const FieldView f, const ServeView *__restrict__ ring, const ServeCtl *__restrict__ ctl,
-             unsigned long long *__restrict__ next_slot, const uint4 *__restrict__ wimg,
+serve_kernel(const FieldView f, ServeView *__restrict__ ring, const ServeCtl *__restrict__ ctl,
+             unsigned int *__restrict__ cursor, const uint4 *__restrict__ wimg,
              unsigned long long idle_ns, unsigned long long *__restrict__ status) {
     constexpr int D = 2 * L;
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -139,56 +130,56 @@ serve_kernel(const FieldView f, const ServeView *__restrict__ ring, const ServeC
             if (m) {
                 const int leader = __ffs(m) - 1;
                 unsigned long long base = 0, got = 0;
-                unsigned int nv = 0;
+                int v = -1;
                 if (lane == leader) {
-                    const unsigned long long pub = ld_acquire_sys_u64(&ctl->published);
-                    nv = ld_acquire_sys_u32(&ctl->n_views);
-                    unsigned long long cur = atomicAdd(next_slot, 0ull);
-                    for (int tries = 0; tries < 64 && cur < pub; ++tries) {
-                        const unsigned long long want = min((unsigned long long)__popc(m), pub - cur);
-                        const unsigned long long prev = atomicCAS(next_slot, cur, cur + want);
-                        if (prev == cur) {
-                            base = cur;
-                            got = want;
+                    // take up to popc(m) slots from the oldest view that has any left
+                    const unsigned int nv = ld_acquire_sys_u32(&ctl->n_views);
+                    unsigned int c = atomicAdd(cursor, 0u);
+                    for (int tries = 0; tries < 2 * kRing && c < nv; ++tries) {
+                        ServeView *sv = ring + (c % kRing);
+                        const unsigned long long total =
+                            (unsigned long long)__ldcg(&sv->tiles_x) * ((__ldcg(&sv->H) + kTileH - 1) / kTileH) * 32ull;
+                        const unsigned long long start = atomicAdd(&sv->taken, (unsigned long long)__popc(m));
+                        if (start < total) {
+                            base = start;
+                            got = min((unsigned long long)__popc(m), total - start);
+                            v = (int)(c % kRing);
                             break;
                         }
-                        cur = prev;
+                        atomicMax(cursor, c + 1);
+                        c = max(c + 1, atomicAdd(cursor, 0u));
                     }
                 }
                 base = __shfl_sync(FULL, base, leader);
                 got = __shfl_sync(FULL, got, leader);
-                nv = __shfl_sync(FULL, nv, leader);
+                v = __shfl_sync(FULL, v, leader);
                 if (need) {
                     const unsigned rank = __popc(m & ((1u << lane) - 1u));
                     if (rank >= got) {
                         starved = true;
                     } else {
-                        const unsigned long long slot = base + rank;
-                        const int v = find_view(ring, nv, slot);
-                        if (v >= 0) {
-                            const ServeView *sv = ring + v;
-                            const int q = (int)(slot - __ldcg(&sv->slot_begin));
-                            const int W = __ldcg(&sv->W), H = __ldcg(&sv->H), tx = __ldcg(&sv->tiles_x);
-                            const int tile = q >> 5, ln = q & 31;
-                            const int px = (tile % tx) * kTileW + (ln & (kTileW - 1));
-                            const int py = (tile / tx) * kTileH + (ln >> 3);
-                            if (px < W && py < H) {
-                                float c2w[12], K[4];
+                        const ServeView *sv = ring + v;
+                        const int q = (int)(base + rank);
+                        const int W = __ldcg(&sv->W), H = __ldcg(&sv->H), tx = __ldcg(&sv->tiles_x);
+                        const int tile = q >> 5, ln = q & 31;
+                        const int px = (tile % tx) * kTileW + (ln & (kTileW - 1));
+                        const int py = (tile / tx) * kTileH + (ln >> 3);
+                        if (px < W && py < H) {
+                            float c2w[12], K[4];
 #pragma unroll
-                                for (int k = 0; k < 12; ++k) c2w[k] = __ldcg(&sv->c2w[k]);
+                            for (int k = 0; k < 12; ++k) c2w[k] = __ldcg(&sv->c2w[k]);
 #pragma unroll
-                                for (int k = 0; k < 4; ++k) K[k] = __ldcg(&sv->K[k]);
-                                camera_ray(c2w, K, px, py, mr.o, mr.d);
-                                r = __fdiv_rn(f.radius_scale, K[0]);
-                                march_init(f, mr);
-                                dst = ldcg_ptr(&sv->out) + 3ll * ((long long)py * W + px);
-                                view = v;
-                                live = true;
-                                T = 1.0f;
-                                C[0] = C[1] = C[2] = 0.0f;
-                            } else {
-                                count_slot(v);  // padding slot of the 8x4 tiling
-                            }
+                            for (int k = 0; k < 4; ++k) K[k] = __ldcg(&sv->K[k]);
+                            camera_ray(c2w, K, px, py, mr.o, mr.d);
+                            r = __fdiv_rn(f.radius_scale, K[0]);
+                            march_init(f, mr);
+                            dst = ldcg_ptr(&sv->out) + 3ll * ((long long)py * W + px);
+                            view = v;
+                            live = true;
+                            T = 1.0f;
+                            C[0] = C[1] = C[2] = 0.0f;
+                        } else {
+                            count_slot(v);  // padding slot of the 8x4 tiling
                         }
                     }
                 }
@@ -208,7 +199,7 @@ serve_kernel(const FieldView f, const ServeView *__restrict__ ring, const ServeC
                 const uint64_t t0 = tc::globaltimer_ns();
                 while (true) {
                     if (ld_acquire_sys_s32(&ctl->stop)) { s_quit = 1; break; }
-                    if (atomicAdd(next_slot, 0ull) < ld_acquire_sys_u64(&ctl->published)) break;
+                    if (atomicAdd(cursor, 0u) < ld_acquire_sys_u32(&ctl->n_views)) break;
                     if (tc::globaltimer_ns() - t0 > idle_ns) { s_quit = 1; break; }
                     __nanosleep(2000);
                 }
@@ -247,15 +238,15 @@ serve_kernel(const FieldView f, const ServeView *__restrict__ ring, const ServeC
 }
 
 template <int L, int FMT>
-static cudaError_t launch_serve_t(vrnerf_field *F, const ServeView *ring, const ServeCtl *ctl,
-                                  unsigned long long *next_slot, unsigned long long idle_ns, cudaStream_t st) {
+static cudaError_t launch_serve_t(vrnerf_field *F, ServeView *ring, const ServeCtl *ctl,
+                                  unsigned int *cursor, unsigned long long idle_ns, cudaStream_t st) {
     const size_t smem = tc_smem_bytes(2 * L, F->view.S);
     auto kern = serve_kernel<L, FMT>;
     int bps = 0;
     cudaError_t e = prepare_tc(kern, smem, bps);
     if (e != cudaSuccess) return e;
     unsigned long long *status = reinterpret_cast<unsigned long long *>(F->counter) + 1;
-    kern<<<num_sms() * bps, kTcThreads, smem, st>>>(F->view, ring, ctl, next_slot,
+    kern<<<num_sms() * bps, kTcThreads, smem, st>>>(F->view, ring, ctl, cursor,
                                                     static_cast<const uint4 *>(F->tc_w), idle_ns, status);
     return cudaGetLastError();
 }
@@ -338,7 +329,7 @@ struct vrnerf_server {
     ServeView *ring_h = nullptr;  // pinned staging
     ServeCtl *ctl_h = nullptr, *ctl_d = nullptr;
     unsigned int *done_h = nullptr, *done_d = nullptr;
-    unsigned long long *next_slot = nullptr;
+    unsigned int *cursor = nullptr;  // device: oldest view that may have slots left
     unsigned char *arena_d = nullptr;
     Arena arena;
     cudaEvent_t kernel_done = nullptr;
@@ -377,7 +368,8 @@ bool vrnerf_server::admit_locked(std::vector<int> &new_views) {
             done_cv.notify_all();
             continue;
         }
-        if (n_views + q->n - oldest_live_view >= (unsigned)kRing) break;
+        // a ring entry is rewritten only long after its previous view finished
+        if (n_views + q->n - oldest_live_view >= (unsigned)kRing / 2) break;
         size_t off = 0;
         if (!arena.alloc(q->bytes, off)) break;  // HBM budget: wait for earlier requests
         pending.pop_front();
@@ -399,6 +391,7 @@ bool vrnerf_server::admit_locked(std::vector<int> &new_views) {
             sv.slot_end = published + slots;
             sv.out = reinterpret_cast<float *>(arena_d + off) + 3 * pix_off;
             sv.done = done_d + idx;
+            sv.taken = 0;
             done_h[idx] = 0;
             view_slots[idx] = slots;
             view_req[idx] = q;
@@ -431,11 +424,11 @@ int vrnerf_server::ensure_kernel() {
     if (e == cudaSuccess) {
         const int fmt = prec == VRNERF_BF16 ? 1 : 0;
         if (F->view.L == 8)
-            e = fmt ? launch_serve_t<8, 1>(F, ring_d, ctl_d, next_slot, idle_ns, kst)
-                    : launch_serve_t<8, 0>(F, ring_d, ctl_d, next_slot, idle_ns, kst);
+            e = fmt ? launch_serve_t<8, 1>(F, ring_d, ctl_d, cursor, idle_ns, kst)
+                    : launch_serve_t<8, 0>(F, ring_d, ctl_d, cursor, idle_ns, kst);
         else
-            e = fmt ? launch_serve_t<16, 1>(F, ring_d, ctl_d, next_slot, idle_ns, kst)
-                    : launch_serve_t<16, 0>(F, ring_d, ctl_d, next_slot, idle_ns, kst);
+            e = fmt ? launch_serve_t<16, 1>(F, ring_d, ctl_d, cursor, idle_ns, kst)
+                    : launch_serve_t<16, 0>(F, ring_d, ctl_d, cursor, idle_ns, kst);
     }
     if (e == cudaSuccess) e = cudaEventRecord(kernel_done, kst);
     if (e != cudaSuccess) return cuda_fail(e, "serve kernel launch");
@@ -526,8 +519,8 @@ int vrnerf_server_create(vrnerf_field *F, uint64_t hbm_budget_bytes, int32_t pre
     if (e == cudaSuccess) e = cudaHostAlloc(&S->done_h, sizeof(unsigned int) * kRing, cudaHostAllocMapped);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer(&S->ctl_d, S->ctl_h, 0);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer(&S->done_d, S->done_h, 0);
-    if (e == cudaSuccess) e = cudaMalloc(&S->next_slot, sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMemset(S->next_slot, 0, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&S->cursor, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(S->cursor, 0, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMalloc(&S->arena_d, hbm_budget_bytes);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->kernel_done, cudaEventDisableTiming);
     if (e != cudaSuccess) {
@@ -678,7 +671,7 @@ void vrnerf_server_destroy(vrnerf_server *S) {
     }
     if (S->kernel_done) cudaEventDestroy(S->kernel_done);
     if (S->arena_d) cudaFree(S->arena_d);
-    if (S->next_slot) cudaFree(S->next_slot);
+    if (S->cursor) cudaFree(S->cursor);
     if (S->done_h) cudaFreeHost(S->done_h);
     if (S->ctl_h) cudaFreeHost(S->ctl_h);
     if (S->ring_h) cudaFreeHost(S->ring_h);

@@ -40,14 +40,15 @@ namespace vrn {
 
 constexpr int kRing = 256;  // views the ring holds; in-flight views stay below this
 
-struct ServeView {
+struct __align__(16) ServeView {
     float c2w[12];
     float K[4];
     int W, H, tiles_x, pad;
     unsigned long long slot_begin, slot_end;
     float *out;            // device [W*H][3]
-    unsigned int *done;    // host-mapped: finished slots of this view
+    unsigned int *done;    // host-mapped flag: set to the slot count when the view is finished
     unsigned long long taken;  // slots handed out (fetch-and-add; may overshoot)
+    unsigned long long finished;  // slots finished (device counter)
 };
 
 struct ServeCtl {                  // host-mapped
@@ -98,11 +99,20 @@ serve_kernel(const FieldView f, ServeView *__restrict__ ring, const ServeCtl *__
     unsigned int cnt = 0;  // finished slots of cnt_view not yet reported
     uint32_t phase = 0;
     unsigned tested = 0;
+    unsigned int nv_seen = 0;  // published views last read from the control block
 
+    // Reports this thread's finished slots of cnt_view; the thread that
+    // completes the view raises the view's host-visible flag.
     auto flush = [&]() {
         if (cnt && cnt_view >= 0) {
-            __threadfence_system();
-            atomicAdd_system(ldcg_ptr(&ring[cnt_view].done), cnt);
+            ServeView *sv = ring + cnt_view;
+            __threadfence();  // this thread's pixels before its count
+            const unsigned long long total =
+                (unsigned long long)__ldcg(&sv->tiles_x) * ((__ldcg(&sv->H) + kTileH - 1) / kTileH) * 32ull;
+            if (atomicAdd(&sv->finished, (unsigned long long)cnt) + cnt == total) {
+                __threadfence_system();
+                atomicExch_system(ldcg_ptr(&sv->done), (unsigned int)total);
+            }
         }
         cnt = 0;
     };
@@ -133,8 +143,9 @@ serve_kernel(const FieldView f, ServeView *__restrict__ ring, const ServeCtl *__
                 int v = -1;
                 if (lane == leader) {
                     // take up to popc(m) slots from the oldest view that has any left
-                    const unsigned int nv = ld_acquire_sys_u32(&ctl->n_views);
                     unsigned int c = atomicAdd(cursor, 0u);
+                    if (c >= nv_seen) nv_seen = ld_acquire_sys_u32(&ctl->n_views);
+                    const unsigned int nv = nv_seen;
                     for (int tries = 0; tries < 2 * kRing && c < nv; ++tries) {
                         ServeView *sv = ring + (c % kRing);
                         const unsigned long long total =
@@ -166,10 +177,20 @@ serve_kernel(const FieldView f, ServeView *__restrict__ ring, const ServeCtl *__
                         const int py = (tile / tx) * kTileH + (ln >> 3);
                         if (px < W && py < H) {
                             float c2w[12], K[4];
+                            const float4 *cv = reinterpret_cast<const float4 *>(sv->c2w);
 #pragma unroll
-                            for (int k = 0; k < 12; ++k) c2w[k] = __ldcg(&sv->c2w[k]);
-#pragma unroll
-                            for (int k = 0; k < 4; ++k) K[k] = __ldcg(&sv->K[k]);
+                            for (int k = 0; k < 3; ++k) {
+                                const float4 t4 = __ldcg(cv + k);
+                                c2w[4 * k] = t4.x;
+                                c2w[4 * k + 1] = t4.y;
+                                c2w[4 * k + 2] = t4.z;
+                                c2w[4 * k + 3] = t4.w;
+                            }
+                            const float4 k4 = __ldcg(cv + 3);
+                            K[0] = k4.x;
+                            K[1] = k4.y;
+                            K[2] = k4.z;
+                            K[3] = k4.w;
                             camera_ray(c2w, K, px, py, mr.o, mr.d);
                             r = __fdiv_rn(f.radius_scale, K[0]);
                             march_init(f, mr);
@@ -392,6 +413,7 @@ bool vrnerf_server::admit_locked(std::vector<int> &new_views) {
             sv.out = reinterpret_cast<float *>(arena_d + off) + 3 * pix_off;
             sv.done = done_d + idx;
             sv.taken = 0;
+            sv.finished = 0;
             done_h[idx] = 0;
             view_slots[idx] = slots;
             view_req[idx] = q;

@@ -42,7 +42,7 @@ render_tc_kernel(const FieldView f, const RaySource src, const RenderOut out,
     constexpr int D = 2 * L;
     extern __shared__ __align__(1024) unsigned char smem[];
     float *sT;
-    const TcShared S = tc_setup<D>(smem, wimg, sT, f.t_tab, f.S);
+    const TcShared S = tc_setup<D, FMT>(smem, wimg, sT, f.t_tab, f.S);
 
     constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -105,7 +105,7 @@ render_tc_kernel(const FieldView f, const RaySource src, const RenderOut out,
             for (int k = 0; k < D; ++k) feat[k] = 0.0f;
         }
         float sigma, rgb[3];
-        tc_mlp<D, FMT>(S, feat, mr.d, f.density_bias, sigma, rgb, phase, ok);
+        tc_mlp_any<D, FMT>(S, feat, mr.d, f.density_bias, sigma, rgb, phase, ok);
         if (have) {
             const float sd = sigma * delta;
             const float w = T * (-expm1f(-sd));
@@ -135,7 +135,7 @@ query_tc_kernel(const FieldView f, const float *__restrict__ pos, const float *_
     constexpr int D = 2 * L;
     extern __shared__ __align__(1024) unsigned char smem[];
     float *sT;
-    const TcShared S = tc_setup<D>(smem, wimg, sT, nullptr, 0);
+    const TcShared S = tc_setup<D, FMT>(smem, wimg, sT, nullptr, 0);
     const int i = blockIdx.x * kTcThreads + threadIdx.x;
     const bool valid = i < n;
     float feat[D], dd[3] = {0, 0, 1};
@@ -152,7 +152,7 @@ query_tc_kernel(const FieldView f, const float *__restrict__ pos, const float *_
     uint32_t phase = 0;
     bool ok = true;
     float sigma, rgb[3];
-    tc_mlp<D, FMT>(S, feat, dd, f.density_bias, sigma, rgb, phase, ok);
+    tc_mlp_any<D, FMT>(S, feat, dd, f.density_bias, sigma, rgb, phase, ok);
     if (valid) {
         sigma_out[i] = sigma;
         for (int c = 0; c < 3; ++c) rgb_out[3 * i + c] = rgb[c];
@@ -186,6 +186,46 @@ __global__ void build_tc_image_kernel(const float *__restrict__ mlp, int D, int 
     }
 }
 
+// fp32 W1..W5 -> the fp8-mode image (TcW8): W1, W5 fp16; W2..W4 e4m3 with a
+// power-of-two scale per matrix (max |w| * s in [128, 256)); one CTA per matrix.
+__global__ void build_tc_image_fp8_kernel(const float *__restrict__ mlp, int D, unsigned char *__restrict__ img) {
+    const int m = blockIdx.x;
+    const int Ns[5] = {64, 16, 64, 64, 16}, Ks[5] = {D, 64, 32, 64, 64}, Rs[5] = {64, 16, 64, 64, 3};
+    const int w2 = 64 * D * 2, w3 = w2 + 16 * 64, w4 = w3 + 64 * 32, w5 = w4 + 64 * 64, sc = w5 + 16 * 64 * 2;
+    const int offs[5] = {0, w2, w3, w4, w5};
+    int src = 0;
+    for (int i = 0; i < m; ++i) src += Rs[i] * Ks[i];
+    const int N = Ns[m], K = Ks[m], R = Rs[m];
+    unsigned char *dst = img + offs[m];
+    if (m == 0 || m == 4) {
+        for (int e = threadIdx.x; e < N * K; e += blockDim.x) {
+            const int row = e / K, col = e % K;
+            const float v = row < R ? mlp[src + row * K + col] : 0.0f;
+            *reinterpret_cast<__half *>(dst + (row >> 3) * (K >> 3) * 128 + (col >> 3) * 128 + (row & 7) * 16 +
+                                        (col & 7) * 2) = __float2half_rn(v);
+        }
+        return;
+    }
+    __shared__ float red[256];
+    float mx = 0.0f;
+    for (int e = threadIdx.x; e < R * K; e += blockDim.x) mx = fmaxf(mx, fabsf(mlp[src + e]));
+    red[threadIdx.x] = mx;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + st]);
+        __syncthreads();
+    }
+    float s, inv;
+    row_scale(red[0], s, inv);
+    for (int e = threadIdx.x; e < N * K; e += blockDim.x) {
+        const int row = e / K, col = e % K;
+        const float v = row < R ? mlp[src + row * K + col] * s : 0.0f;
+        dst[(row >> 3) * (K >> 4) * 128 + (col >> 4) * 128 + (row & 7) * 16 + (col & 15)] =
+            (unsigned char)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+    }
+    if (threadIdx.x == 0) reinterpret_cast<float *>(img + sc)[m - 1] = inv;
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -206,15 +246,19 @@ static cudaError_t render_tc_t(vrnerf_field *F, const RaySource &src, const Rend
     return cudaGetLastError();
 }
 
+static int fmt_of(int prec) { return prec == VRNERF_BF16 ? 1 : (prec == VRNERF_FP8 ? 2 : 0); }
+
 cudaError_t launch_render_tc(vrnerf_field *F, const RaySource &src, const RenderOut &out, int prec,
                              cudaStream_t st) {
-    if (prec != VRNERF_FP16 && prec != VRNERF_BF16) return cudaErrorNotSupported;
-    const int fmt = prec == VRNERF_BF16 ? 1 : 0;
+    if (prec != VRNERF_FP16 && prec != VRNERF_BF16 && prec != VRNERF_FP8) return cudaErrorNotSupported;
+    const int fmt = fmt_of(prec);
     cudaError_t e = ensure_tc_image(F, fmt, st);
     if (e != cudaSuccess) return e;
     if (F->view.L == 8)
-        return fmt ? render_tc_t<8, 1>(F, src, out, st) : render_tc_t<8, 0>(F, src, out, st);
-    return fmt ? render_tc_t<16, 1>(F, src, out, st) : render_tc_t<16, 0>(F, src, out, st);
+        return fmt == 1 ? render_tc_t<8, 1>(F, src, out, st)
+                        : (fmt == 2 ? render_tc_t<8, 2>(F, src, out, st) : render_tc_t<8, 0>(F, src, out, st));
+    return fmt == 1 ? render_tc_t<16, 1>(F, src, out, st)
+                    : (fmt == 2 ? render_tc_t<16, 2>(F, src, out, st) : render_tc_t<16, 0>(F, src, out, st));
 }
 
 template <int L, int FMT>
@@ -233,15 +277,17 @@ static cudaError_t query_tc_t(vrnerf_field *F, const float *pos, const float *di
 
 cudaError_t launch_query_tc(vrnerf_field *F, const float *pos, const float *dir, const float *radius, int n,
                             float *sigma, float *rgb, float *feat, int prec, cudaStream_t st) {
-    if (prec != VRNERF_FP16 && prec != VRNERF_BF16) return cudaErrorNotSupported;
-    const int fmt = prec == VRNERF_BF16 ? 1 : 0;
+    if (prec != VRNERF_FP16 && prec != VRNERF_BF16 && prec != VRNERF_FP8) return cudaErrorNotSupported;
+    const int fmt = fmt_of(prec);
     cudaError_t e = ensure_tc_image(F, fmt, st);
     if (e != cudaSuccess) return e;
     if (F->view.L == 8)
-        return fmt ? query_tc_t<8, 1>(F, pos, dir, radius, n, sigma, rgb, feat, st)
-                   : query_tc_t<8, 0>(F, pos, dir, radius, n, sigma, rgb, feat, st);
-    return fmt ? query_tc_t<16, 1>(F, pos, dir, radius, n, sigma, rgb, feat, st)
-               : query_tc_t<16, 0>(F, pos, dir, radius, n, sigma, rgb, feat, st);
+        return fmt == 1 ? query_tc_t<8, 1>(F, pos, dir, radius, n, sigma, rgb, feat, st)
+                        : (fmt == 2 ? query_tc_t<8, 2>(F, pos, dir, radius, n, sigma, rgb, feat, st)
+                                    : query_tc_t<8, 0>(F, pos, dir, radius, n, sigma, rgb, feat, st));
+    return fmt == 1 ? query_tc_t<16, 1>(F, pos, dir, radius, n, sigma, rgb, feat, st)
+                    : (fmt == 2 ? query_tc_t<16, 2>(F, pos, dir, radius, n, sigma, rgb, feat, st)
+                                : query_tc_t<16, 0>(F, pos, dir, radius, n, sigma, rgb, feat, st));
 }
 
 }  // namespace vrn

@@ -86,7 +86,7 @@ serve_kernel(const FieldView f, ServeView *__restrict__ ring, const ServeCtl *__
     constexpr int D = 2 * L;
     extern __shared__ __align__(1024) unsigned char smem[];
     float *sT;
-    const TcShared S = tc_setup<D>(smem, wimg, sT, f.t_tab, f.S);
+    const TcShared S = tc_setup<D, FMT>(smem, wimg, sT, f.t_tab, f.S);
     __shared__ int s_quit;
 
     constexpr unsigned FULL = 0xffffffffu;
@@ -242,7 +242,7 @@ serve_kernel(const FieldView f, ServeView *__restrict__ ring, const ServeCtl *__
             for (int k = 0; k < D; ++k) feat[k] = 0.0f;
         }
         float sigma, rgb[3];
-        tc_mlp<D, FMT>(S, feat, mr.d, f.density_bias, sigma, rgb, phase, ok);
+        tc_mlp_any<D, FMT>(S, feat, mr.d, f.density_bias, sigma, rgb, phase, ok);
         if (have) {
             const float sd = sigma * delta;
             const float w = T * (-expm1f(-sd));

@@ -3,6 +3,8 @@
 // serving kernels: operand layout, per-layer issue / commit / wait, TMEM
 // epilogues, CTA set-up and tear-down, and the host-side launch helpers.
 #pragma once
+#include <cuda_fp8.h>
+
 #include "field.h"
 #include "tc.cuh"
 
@@ -21,6 +23,24 @@ struct TcW {  // byte offsets of the weight image (K-major operands)
     static constexpr int w4 = w3 + 64 * 32 * 2;  // [64][64]
     static constexpr int w5 = w4 + 64 * 64 * 2;  // [16][64], rows 3..15 zero
     static constexpr int bytes = w5 + 16 * 64 * 2;
+};
+
+// Weight image of the fp8 mode: W1 and W5 fp16, W2..W4 e4m3 (K-major,
+// 16-byte core-matrix rows), then the inverse weight scales of W2..W4.
+template <int D>
+struct TcW8 {
+    static constexpr int w1 = 0;                  // [64][D] fp16
+    static constexpr int w2 = w1 + 64 * D * 2;    // [16][64] e4m3
+    static constexpr int w3 = w2 + 16 * 64;       // [64][32] e4m3
+    static constexpr int w4 = w3 + 64 * 32;       // [64][64] e4m3
+    static constexpr int w5 = w4 + 64 * 64;       // [16][64] fp16
+    static constexpr int scales = w5 + 16 * 64 * 2;  // float inv_s2, inv_s3, inv_s4, pad
+    static constexpr int bytes = scales + 16;
+};
+
+template <int D, int FMT>
+struct TcImage {
+    static constexpr int bytes = FMT == 2 ? TcW8<D>::bytes : TcW<D>::bytes;
 };
 
 struct TcShared {
@@ -60,6 +80,66 @@ __device__ __forceinline__ void issue_layer(uint32_t a_addr, uint32_t b_addr, ui
     for (int ks = 0; ks < K / 16; ++ks)
         tc::mma_f16(tmem, tc::smem_desc(a_addr + ks * 256, 128, sbo), tc::smem_desc(b_addr + ks * 256, 128, sbo),
                     idesc, ks > 0 ? 1u : 0u);
+}
+
+// e4m3 operands: 16 elements per core-matrix row, K = 32 per instruction.
+template <int K, int N>
+__device__ __forceinline__ void issue_layer_e4m3(uint32_t a_addr, uint32_t b_addr, uint32_t tmem) {
+    constexpr uint32_t sbo = (K / 16) * 128;
+    constexpr uint32_t idesc = tc::idesc_e4m3(N);
+#pragma unroll
+    for (int ks = 0; ks < K / 32; ++ks)
+        tc::mma_f8(tmem, tc::smem_desc(a_addr + ks * 256, 128, sbo), tc::smem_desc(b_addr + ks * 256, 128, sbo),
+                   idesc, ks > 0 ? 1u : 0u);
+}
+
+template <int K, int N>
+__device__ __forceinline__ void run_layer_e4m3(const TcShared &S, int w_off, uint32_t &phase, bool &ok) {
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        tc::fence_after_sync();
+        issue_layer_e4m3<K, N>(tc::smem_u32(S.act), tc::smem_u32(S.w) + w_off, S.tbase);
+        tc::mma_commit(S.mbar);
+    }
+    ok = tc::mbar_wait_bounded(S.mbar, phase, S.abort) && ok;
+    phase ^= 1u;
+    tc::fence_after_sync();
+}
+
+// Power-of-two scale that maps the row maximum m into [128, 256) (e4m3
+// holds up to 448), and its inverse.
+__device__ __forceinline__ void row_scale(float m, float &s, float &inv) {
+    const int e = (int)((__float_as_uint(m) >> 23) & 255u);
+    if (m > 0.0f && e > 0 && e < 255) {
+        const int k = 7 - (e - 127);                   // s = 2^k, m * s in [128, 256)
+        const int kk = k > 126 ? 126 : (k < -126 ? -126 : k);
+        s = __uint_as_float((uint32_t)(127 + kk) << 23);
+        inv = __uint_as_float((uint32_t)(127 - kk) << 23);
+    } else {
+        s = 1.0f;
+        inv = 1.0f;
+    }
+}
+
+// Row r of a 128 x K e4m3 operand (16-byte core-matrix rows): K / 16 chunks.
+template <int K>
+__device__ __forceinline__ void store_row_e4m3(unsigned char *base, int r, const float *v, float s) {
+#pragma unroll
+    for (int j = 0; j < K / 16; ++j) {
+        uint32_t w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const __nv_fp8x2_storage_t lo = __nv_cvt_float2_to_fp8x2(
+                make_float2(v[16 * j + 4 * q] * s, v[16 * j + 4 * q + 1] * s), __NV_SATFINITE, __NV_E4M3);
+            const __nv_fp8x2_storage_t hi = __nv_cvt_float2_to_fp8x2(
+                make_float2(v[16 * j + 4 * q + 2] * s, v[16 * j + 4 * q + 3] * s), __NV_SATFINITE, __NV_E4M3);
+            w[q] = (uint32_t)lo | ((uint32_t)hi << 16);
+        }
+        *reinterpret_cast<uint4 *>(base + (r >> 3) * (K / 16) * 128 + j * 128 + (r & 7) * 16) =
+            make_uint4(w[0], w[1], w[2], w[3]);
+    }
 }
 
 // Runs one layer: the tile's rows are written; all threads sync, thread 0
@@ -156,11 +236,116 @@ __device__ __forceinline__ void tc_mlp(const TcShared &S, const float (&feat)[D]
     tc::fence_before_sync();  // this tile's TMEM reads precede the next tile's MMAs
 }
 
-// Shared-memory carve-up, weight upload, mbarrier and TMEM set-up.
+// fp8 mode: the density MLP's output layer and the colour MLP's two hidden
+// layers (W2, W3, W4) take e4m3 operands with a power-of-two scale per row
+// (this thread's sample) and per weight matrix, undone on the fp32
+// accumulator; the first layer (W1) and the colour output (W5) stay fp16.
 template <int D>
+__device__ __forceinline__ void tc_mlp_fp8(const TcShared &S, const float (&feat)[D], const float dir[3],
+                                           float density_bias, float &sigma, float rgb[3], uint32_t &phase,
+                                           bool &ok) {
+    using W = TcW8<D>;
+    const int r = threadIdx.x;
+    const uint32_t taddr = S.tbase + ((uint32_t)(r & ~31) << 16);
+    const float *inv_w = reinterpret_cast<const float *>(S.w + W::scales);
+    {
+        uint32_t pk[D / 2];
+#pragma unroll
+        for (int i = 0; i < D / 2; ++i) pk[i] = pack2<0>(feat[2 * i], feat[2 * i + 1]);
+        store_row<D>(S.act, r, pk);
+    }
+    run_layer<D, 64, 0>(S, W::w1, phase, ok);
+    float s_in, inv_in;
+    {
+        float h[64], m = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 64; c += 16) {
+            float v[16];
+            tc::tmem_ld16(taddr + c, v);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                h[c + i] = fmaxf(v[i], 0.0f);
+                m = fmaxf(m, h[c + i]);
+            }
+        }
+        row_scale(m, s_in, inv_in);
+        store_row_e4m3<64>(S.act, r, h, s_in);
+    }
+    run_layer_e4m3<64, 16>(S, W::w2, phase, ok);
+    {
+        float o[16], x[32];
+        tc::tmem_ld16(taddr, o);
+        const float k = inv_in * inv_w[0];
+        float m = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            o[i] *= k;
+            x[i] = o[i];
+        }
+        sigma = expf(o[0] + density_bias);
+        sh16(dir[0], dir[1], dir[2], x + 16);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) m = fmaxf(m, fabsf(x[i]));
+        row_scale(m, s_in, inv_in);
+        store_row_e4m3<32>(S.act, r, x, s_in);
+    }
+    run_layer_e4m3<32, 64>(S, W::w3, phase, ok);
+    {
+        float h[64], m = 0.0f;
+        const float k = inv_in * inv_w[1];
+#pragma unroll
+        for (int c = 0; c < 64; c += 16) {
+            float v[16];
+            tc::tmem_ld16(taddr + c, v);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                h[c + i] = fmaxf(v[i] * k, 0.0f);
+                m = fmaxf(m, h[c + i]);
+            }
+        }
+        row_scale(m, s_in, inv_in);
+        store_row_e4m3<64>(S.act, r, h, s_in);
+    }
+    run_layer_e4m3<64, 64>(S, W::w4, phase, ok);
+    {
+        uint32_t pk[32];
+        const float k = inv_in * inv_w[2];
+#pragma unroll
+        for (int c = 0; c < 64; c += 16) {
+            float v[16];
+            tc::tmem_ld16(taddr + c, v);
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                pk[c / 2 + i] = pack2<0>(fmaxf(v[2 * i] * k, 0.f), fmaxf(v[2 * i + 1] * k, 0.f));
+        }
+        store_row<64>(S.act, r, pk);
+    }
+    run_layer<64, 16, 0>(S, W::w5, phase, ok);
+    {
+        float z[16];
+        tc::tmem_ld16(taddr, z);
+        rgb[0] = 1.0f / (1.0f + expf(-z[0]));
+        rgb[1] = 1.0f / (1.0f + expf(-z[1]));
+        rgb[2] = 1.0f / (1.0f + expf(-z[2]));
+    }
+    tc::fence_before_sync();
+}
+
+template <int D, int FMT>
+__device__ __forceinline__ void tc_mlp_any(const TcShared &S, const float (&feat)[D], const float dir[3],
+                                           float density_bias, float &sigma, float rgb[3], uint32_t &phase,
+                                           bool &ok) {
+    if constexpr (FMT == 2)
+        tc_mlp_fp8<D>(S, feat, dir, density_bias, sigma, rgb, phase, ok);
+    else
+        tc_mlp<D, FMT>(S, feat, dir, density_bias, sigma, rgb, phase, ok);
+}
+
+// Shared-memory carve-up, weight upload, mbarrier and TMEM set-up.
+template <int D, int FMT = 0>
 __device__ __forceinline__ TcShared tc_setup(unsigned char *smem, const uint4 *__restrict__ wimg,
                                              float *&sT, const float *__restrict__ t_tab, int S_steps) {
-    using W = TcW<D>;
+    using W = TcImage<D, FMT>;
     TcShared S;
     S.w = smem;
     S.act = smem + ((W::bytes + 1023) & ~1023);
@@ -202,6 +387,8 @@ __device__ __forceinline__ void tc_teardown(const TcShared &S, unsigned long lon
 // fp32 W1..W5 -> the K-major operand image of TcW<D>, fp16 or bf16.
 __global__ void build_tc_image_kernel(const float *__restrict__ mlp, int D, int fmt,
                                       unsigned char *__restrict__ img);
+// fp32 W1..W5 -> the image of TcW8<D> (one CTA per weight matrix).
+__global__ void build_tc_image_fp8_kernel(const float *__restrict__ mlp, int D, unsigned char *__restrict__ img);
 
 inline size_t tc_smem_bytes(int D, int S_steps) {
     const size_t wb = (size_t)(64 * D * 2 + 16 * 64 * 2 + 64 * 32 * 2 + 64 * 64 * 2 + 16 * 64 * 2);
@@ -220,8 +407,12 @@ inline cudaError_t ensure_tc_image(vrnerf_field *F, int fmt, cudaStream_t st) {
         if (e != cudaSuccess) return e;
         F->tc_w_bytes = bytes;
     }
-    const int n = (int)(bytes / 2);
-    build_tc_image_kernel<<<(n + 255) / 256, 256, 0, st>>>(F->mlp, D, fmt, static_cast<unsigned char *>(F->tc_w));
+    if (fmt == 2) {
+        build_tc_image_fp8_kernel<<<5, 256, 0, st>>>(F->mlp, D, static_cast<unsigned char *>(F->tc_w));
+    } else {
+        const int n = (int)(bytes / 2);
+        build_tc_image_kernel<<<(n + 255) / 256, 256, 0, st>>>(F->mlp, D, fmt, static_cast<unsigned char *>(F->tc_w));
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     F->tc_prec = fmt;

@@ -368,6 +368,21 @@ def main():
     # plain fp32 path on the same frame
     ms32 = timed(V.FP32, max(3, args.steps // 2), 2) if tuned != V.FP32 else ms
 
+    # precision sweep on the same frame: throughput, and PQ-space PSNR against
+    # the fp32 render (the tests hold each precision to >= 50 dB against the
+    # fp64 CPU oracle on 256^2 crops)
+    ref_pq = torch.empty((rays, 3), device=dev)
+    V.vrnerf_render(field, cams, intr, res, out=out, precision=V.FP32, out_pq=ref_pq)
+    sweep = {}
+    for name in ("fp32", "fp16", "bf16", "fp8"):
+        p = V.PRECISIONS[name]
+        t = timed(p, max(3, args.steps // 4), 2)
+        pq = torch.empty((rays, 3), device=dev)
+        V.vrnerf_render(field, cams, intr, res, out=out, precision=p, out_pq=pq)
+        mse = float(((pq - ref_pq).double() ** 2).mean())
+        sweep[name] = {"Mrays_s": round(rays / (float(t.mean()) * 1e-3) / 1e6, 2),
+                       "psnr_pq_vs_fp32_db": (round(10 * np.log10(1.0 / mse), 2) if mse > 0 else "inf")}
+
     # stereo 2 x 2048^2 frame latency (tuned)
     st_c2w = S.stereo_pair(c2w[0])
     st_K = np.concatenate([K, K])
@@ -413,6 +428,7 @@ def main():
         "work": {"samples_per_ray": round(n_samples / rays, 3),
                  "levels_per_sample": round(n_levels / max(n_samples, 1), 3),
                  "steps_per_ray": round(n_steps / rays, 2), "rays_finished": n_rays_done},
+        "precision_sweep": sweep,
         "plain_fp32": {"value": round(world * rays / (float(ms32.mean()) * 1e-3) / 1e6, 3),
                        "unit": "Mrays/s", "ms_per_step": round(float(ms32.mean()), 4)},
         "stereo_2x2048": {"p50_ms": round(float(np.percentile(st_ms, 50)), 4),

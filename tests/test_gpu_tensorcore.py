@@ -140,5 +140,9 @@ def test_precision_sweep_psnr(V, room, variant):
         ref = F.render(c2w, Kc, res)
         for prec in ("fp32", "fp16", "bf16", "fp8"):
             _, pq, _ = render(V, f, c2w, Kc, res, prec)
-            assert psnr_pq(pq, ref["pq"]) >= 50.0, prec
+            p = psnr_pq(pq, ref["pq"])
+            err = np.abs(pq - ref["pq"])
+            print(f"precision-sweep {variant} crop=({x0},{y0}) {prec}: PQ-PSNR {p:.2f} dB, "
+                  f"max |err| {err.max():.3e}, mean |err| {err.mean():.3e}")
+            assert p >= 50.0, prec
     f.close()

@@ -107,22 +107,9 @@ void derive_view(const vrnerf_field_desc &d, FieldView &f, std::vector<float> &t
     f.density_bias = d.density_bias;
     f.radius_scale = d.radius_scale;
     f.n_mlp = 64 * f.d_in + 16 * 64 + 64 * 32 + 64 * 64 + 3 * 64;
-    // occupancy pyramid: level m has ceil(res / 2^m) blocks a side, up to one block
-    int res_max = max(d.occ_res[0], max(d.occ_res[1], d.occ_res[2]));
-    f.n_mip = 0;
-    while ((1 << f.n_mip) < res_max && f.n_mip < kMaxMip - 1) ++f.n_mip;
-    long long words = 0;
-    for (int m = 1; m <= f.n_mip; ++m) {
-        const long long rx = (d.occ_res[0] + (1 << m) - 1) >> m, ry = (d.occ_res[1] + (1 << m) - 1) >> m,
-                        rz = (d.occ_res[2] + (1 << m) - 1) >> m;
-        f.mip_off[m] = (int)words;
-        f.mip_rx[m] = (int)rx;
-        f.mip_ry[m] = (int)ry;
-        words += (rx * ry * rz + 31) / 32;
-    }
-    f.mip_words = (int)words;
+    const int res_max = max(d.occ_res[0], max(d.occ_res[1], d.occ_res[2]));
     // Skipping is exact when skip_eps exceeds the rounding error of the fp32
-    // grid coordinate of a sample and of a block-exit distance, both below
+    // grid coordinate of a sample and of a cube-exit distance, both below
     // 2^-24 (c (t_far + 2 A + ext) + res) up to a small factor (A: largest
     // |coordinate| of the box, c: largest voxels per unit); keep a 16x margin.
     f.skip_eps = 1.0f / 16.0f;
@@ -192,7 +179,7 @@ using namespace vrn;
 void vrnerf_field::release() {
     release_train_scratch(this);
     void *ptrs[] = {grid,     mlp,      occ,         t_tab,  counter, tc_w,   grid_grad, mlp_grad,
-                    grid_master, m_grid, v_grid, m_mlp, v_mlp, loss_acc, stage_cam, stage_out, mip};
+                    grid_master, m_grid, v_grid, m_mlp, v_mlp, loss_acc, stage_cam, stage_out, dist};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     grid = nullptr;
@@ -200,7 +187,7 @@ void vrnerf_field::release() {
     occ = nullptr;
     t_tab = nullptr;
     counter = nullptr;
-    mip = nullptr;
+    dist = nullptr;
     tc_w = nullptr;
     grid_grad = mlp_grad = grid_master = m_grid = v_grid = m_mlp = v_mlp = loss_acc = nullptr;
     stage_cam = stage_out = nullptr;
@@ -276,7 +263,7 @@ int vrnerf_field_create(const vrnerf_field_desc *desc, const void *grid_host, co
         (e = cudaMalloc(&F->occ, nocc * sizeof(uint32_t))) != cudaSuccess ||
         (e = cudaMalloc(&F->t_tab, t_tab.size() * sizeof(float))) != cudaSuccess ||
         (e = cudaMalloc(&F->counter, 64)) != cudaSuccess ||
-        (e = cudaMalloc(&F->mip, sizeof(uint32_t) * (size_t)(F->view.mip_words > 0 ? F->view.mip_words : 1))) != cudaSuccess) {
+        (e = cudaMalloc(&F->dist, (size_t)desc->occ_res[0] * desc->occ_res[1] * desc->occ_res[2])) != cudaSuccess) {
         vrnerf_field_destroy(F);
         cudaGetLastError();
         return fail(VRNERF_ENOMEM, "device allocation failed: %s", cudaGetErrorString(e));
@@ -303,8 +290,8 @@ int vrnerf_field_create(const vrnerf_field_desc *desc, const void *grid_host, co
     F->view.mlp = F->mlp;
     F->view.occ = F->occ;
     F->view.t_tab = F->t_tab;
-    F->view.mip = F->mip;
-    if (e == cudaSuccess) e = launch_build_mip(F->view, F->mip, 0);
+    F->view.dist = F->dist;
+    if (e == cudaSuccess) e = launch_build_dist(F->view, F->dist, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         vrnerf_field_destroy(F);
@@ -359,7 +346,7 @@ int vrnerf_field_set_occupancy(vrnerf_field *F, const uint32_t *occ) {
     ABI_GUARD_BEGIN
     if (!F || !occ) return fail(VRNERF_EINVAL, "NULL argument");
     cudaError_t e = cudaMemcpy(F->occ, occ, occ_words(F->desc) * 4, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = launch_build_mip(F->view, F->mip, 0);
+    if (e == cudaSuccess) e = launch_build_dist(F->view, F->dist, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "set_occupancy");
     return VRNERF_OK;

@@ -17,7 +17,7 @@ constexpr int kMaxLevels = 16;
 constexpr int kMaxViews = 256;
 constexpr int kTileW = 8;   // rays of one warp cover an 8 x 4 pixel tile
 constexpr int kTileH = 4;
-constexpr int kMaxMip = 12;  // occupancy pyramid levels 1..11 (res <= 2048)
+constexpr int kDistCap = 32;  // the occupancy distance field saturates at this many voxels
 
 // Everything a kernel needs to read the field; passed by value.
 struct FieldView {
@@ -34,16 +34,12 @@ struct FieldView {
     float inv_ext;
     float two_s, inv_ln_f, lod_bias, T_eps, density_bias, radius_scale;
     int n_mlp;
-    // empty-space skipping: occupancy pyramid, level m >= 1 holds one bit per
-    // block of 2^m voxels a side (set when any voxel of the block is occupied)
-    const uint32_t *mip;      // all levels, concatenated
-    int skip;                 // 0: test every sample
-    int n_mip;                // levels 1 .. n_mip present
-    int mip_off[kMaxMip];     // word offset of level m
-    int mip_rx[kMaxMip], mip_ry[kMaxMip];
-    float skip_eps;           // margin (voxels) kept from block faces
+    // empty-space skipping: per voxel, the Chebyshev (L-infinity) distance in
+    // voxels to the nearest occupied voxel, saturated at kDistCap; 0 = occupied
+    const uint8_t *dist;
+    int skip;                 // 0: test every sample against the occupancy bits
+    float skip_eps;           // margin (voxels) kept from the faces of an empty cube
     float ln_tn, inv_ln_q;    // ln t_near and S / ln(t_far / t_near)
-    int mip_words;            // total words of levels 1..n_mip
 };
 
 // One launch's rays: either camera views (pixels in 8x4 tiles) or explicit arrays.
@@ -131,14 +127,16 @@ __device__ __forceinline__ bool occupied(const uint32_t *__restrict__ occ, int v
 //
 // The evaluated samples are defined per sample: sample i is evaluated iff its
 // fp32 position falls in an occupied voxel, and the march ends at the first
-// sample outside the grid. The skip never changes that set. From a sample in
-// an empty voxel it takes the largest empty pyramid block around the voxel
-// (clipped to the grid), shrinks it by skip_eps voxels on every face, and
-// jumps to the first sample at or past the ray's exit from the shrunken
-// block. Every sample jumped over lies, exactly, at least skip_eps inside the
-// block; skip_eps is far above the rounding error of the fp32 position and of
-// the exit distance (checked when the field is created), so each of those
-// samples would have been found, one by one, in an empty voxel of the block.
+// sample outside the grid. The skip never changes that set. A sample's voxel
+// v has distance d = dist[v] to the nearest occupied voxel (L-infinity, in
+// voxels), so every voxel u with max_k |u_k - v_k| <= d - 1 is empty: the
+// cube [v - (d-1), v + d) of grid coordinates (clipped to the grid) holds no
+// occupied voxel. The march shrinks that cube by skip_eps voxels on every
+// face and jumps to the first sample at or past the ray's exit from it.
+// Every sample jumped over lies, exactly, at least skip_eps inside the cube;
+// skip_eps is far above the rounding error of the fp32 position and of the
+// exit distance (checked when the field is created), so each of those
+// samples would have been found, one by one, in an empty voxel of the cube.
 // ---------------------------------------------------------------------------
 struct MarchRay {
     float o[3], d[3];
@@ -156,12 +154,6 @@ __device__ __forceinline__ void march_init(const FieldView &f, MarchRay &m) {
     m.step = 0;
 }
 
-__device__ __forceinline__ bool mip_occupied(const FieldView &f, int m, const int v[3]) {
-    const int bx = v[0] >> m, by = v[1] >> m, bz = v[2] >> m;
-    const int i = bx + f.mip_rx[m] * (by + f.mip_ry[m] * bz);
-    return (__ldg(f.mip + f.mip_off[m] + (i >> 5)) >> (i & 31)) & 1u;
-}
-
 // First sample index j >= lo whose distance is >= t (S if none).
 __device__ __forceinline__ int first_sample_at(const FieldView &f, const float *__restrict__ sT,
                                                float t, int lo) {
@@ -176,7 +168,7 @@ enum { MARCH_END = 0, MARCH_SAMPLE = 1, MARCH_MORE = 2 };
 
 // Advances m.step to the next evaluated sample (MARCH_SAMPLE, p set,
 // m.step = its index), to the end of the ray (MARCH_END), or stops after
-// max_iter iterations (MARCH_MORE). tested counts canonical sample tests.
+// max_iter iterations (MARCH_MORE). tested counts sample tests.
 __device__ __forceinline__ int march_next(const FieldView &f, const float *__restrict__ sT,
                                           MarchRay &m, float p[3], int max_iter,
                                           unsigned &tested) {
@@ -186,19 +178,18 @@ __device__ __forceinline__ int march_next(const FieldView &f, const float *__res
         int vox, v[3];
         if (!sample_voxel(f, m.o, m.d, t, p, vox, v)) return MARCH_END;
         ++tested;
-        if (occupied(f.occ, vox)) return MARCH_SAMPLE;
         if (!f.skip) {
+            if (occupied(f.occ, vox)) return MARCH_SAMPLE;
             ++m.step;
             continue;
         }
-        int lev = 0;
-        while (lev < f.n_mip && !mip_occupied(f, lev + 1, v)) ++lev;
+        const int dv = (int)__ldg(f.dist + vox);
+        if (dv == 0) return MARCH_SAMPLE;
         float t_in = -INFINITY, t_out = INFINITY;
         bool ok = true;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const int lo_i = (v[k] >> lev) << lev;
-            const int hi_i = min(lo_i + (1 << lev), f.res[k]);
+            const int lo_i = max(v[k] - (dv - 1), 0), hi_i = min(v[k] + dv, f.res[k]);
             const float lo = (float)lo_i + f.skip_eps, hi = (float)hi_i - f.skip_eps;
             if (m.inv_s[k] != 0.0f) {
                 const float ta = (lo - m.g0[k]) * m.inv_s[k], tb = (hi - m.g0[k]) * m.inv_s[k];

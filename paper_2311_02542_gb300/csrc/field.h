@@ -18,7 +18,7 @@ struct vrnerf_field {
     uint32_t *occ = nullptr;
     float *t_tab = nullptr;       // [S+1]
     void *counter = nullptr;      // ray-slot counter of the persistent kernels (scratch)
-    uint32_t *mip = nullptr;      // occupancy pyramid (levels 1..n_mip)
+    uint8_t *dist = nullptr;      // occupancy distance field (one byte per voxel)
     // tensor-core weight images, rebuilt when the fp32 weights change
     void *tc_w = nullptr;
     size_t tc_w_bytes = 0;

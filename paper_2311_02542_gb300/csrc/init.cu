@@ -6,6 +6,8 @@
 // mix(key + (k + 1) * 0x9E3779B97F4A7C15); u_k = (draw_k >> 40) * 2^-24.
 // Grid: U(lo, hi) in fp64 rounded to fp32 (then fp16 for fp16 storage).
 // Weight matrix m (stream 2 + m): Xavier-uniform (2 u - 1) sqrt(6 / (in + out)).
+#include <utility>
+
 #include "internal.h"
 
 namespace vrn {
@@ -75,49 +77,60 @@ cudaError_t launch_seeded_mlp(float *mlp, const int (*shapes)[2], int n_mats, ui
     return cudaSuccess;
 }
 
-// Level m of the occupancy pyramid from level m - 1: bit = OR of the (up to)
-// 2x2x2 child bits. One thread per output word.
-__global__ void mip_level_kernel(const uint32_t *__restrict__ prev, int prx, int pry, int prz,
-                                 uint32_t *__restrict__ out, int rx, int ry, int rz) {
-    const long long n = (long long)rx * ry * rz;
-    const long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (w * 32 >= n) return;
-    uint32_t bits = 0;
-    for (int b = 0; b < 32; ++b) {
-        const long long i = w * 32 + b;
-        if (i >= n) break;
-        const int bx = (int)(i % rx), by = (int)((i / rx) % ry), bz = (int)(i / ((long long)rx * ry));
-        uint32_t any = 0;
-        for (int c = 0; c < 8; ++c) {
-            const int cx = 2 * bx + (c & 1), cy = 2 * by + ((c >> 1) & 1), cz = 2 * bz + (c >> 2);
-            if (cx < prx && cy < pry && cz < prz) {
-                const long long j = cx + (long long)prx * (cy + (long long)pry * cz);
-                any |= (prev[j >> 5] >> (j & 31)) & 1u;
-            }
-        }
-        bits |= any << b;
+// Occupancy distance field: dist[v] = min(kDistCap, L-infinity distance in
+// voxels from v to the nearest occupied voxel), 0 for occupied voxels. After r
+// dilations of the occupancy by the 3x3x3 cube, a voxel is covered iff an
+// occupied voxel lies within distance r; its distance is the first r that
+// covers it. Each dilation is three separable 3-tap passes.
+__global__ void dist_init_kernel(const uint32_t *__restrict__ occ, long long n, uint8_t *__restrict__ mask,
+                                 uint8_t *__restrict__ dist) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const uint8_t o = (occ[i >> 5] >> (i & 31)) & 1u;
+        mask[i] = o;
+        dist[i] = o ? 0 : (uint8_t)kDistCap;
     }
-    out[w] = bits;
 }
 
-cudaError_t launch_build_mip(const FieldView &f, uint32_t *mip, cudaStream_t st) {
-    const uint32_t *prev = f.occ;
-    int prx = f.res[0], pry = f.res[1], prz = f.res[2];
-    for (int m = 1; m <= f.n_mip; ++m) {
-        const int rx = (f.res[0] + (1 << m) - 1) >> m, ry = (f.res[1] + (1 << m) - 1) >> m,
-                  rz = (f.res[2] + (1 << m) - 1) >> m;
-        const long long words = ((long long)rx * ry * rz + 31) / 32;
-        uint32_t *out = mip + f.mip_off[m];
-        mip_level_kernel<<<(unsigned)((words + 127) / 128), 128, 0, st>>>(prev, prx, pry, prz, out, rx,
-                                                                         ry, rz);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        prev = out;
-        prx = rx;
-        pry = ry;
-        prz = rz;
+__global__ void dilate_axis_kernel(const uint8_t *__restrict__ in, uint8_t *__restrict__ out, int rx, int ry,
+                                   int rz, int axis) {
+    const long long n = (long long)rx * ry * rz;
+    const long long stride = axis == 0 ? 1 : (axis == 1 ? rx : (long long)rx * ry);
+    const int len = axis == 0 ? rx : (axis == 1 ? ry : rz);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)((i / stride) % len);
+        uint8_t v = in[i];
+        if (c > 0) v |= in[i - stride];
+        if (c + 1 < len) v |= in[i + stride];
+        out[i] = v;
     }
-    return cudaSuccess;
+}
+
+__global__ void dist_assign_kernel(const uint8_t *__restrict__ mask, long long n, int r, uint8_t *__restrict__ dist) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        if (mask[i] && dist[i] == (uint8_t)kDistCap) dist[i] = (uint8_t)r;
+}
+
+cudaError_t launch_build_dist(const FieldView &f, uint8_t *dist, cudaStream_t st) {
+    const int rx = f.res[0], ry = f.res[1], rz = f.res[2];
+    const long long n = (long long)rx * ry * rz;
+    uint8_t *a = nullptr, *b = nullptr;
+    cudaError_t e = cudaMallocAsync(&a, (size_t)n, st);
+    if (e == cudaSuccess) e = cudaMallocAsync(&b, (size_t)n, st);
+    const int grid = num_sms() * 8;
+    if (e == cudaSuccess) {
+        dist_init_kernel<<<grid, 256, 0, st>>>(f.occ, n, a, dist);
+        for (int r = 1; r < kDistCap && e == cudaSuccess; ++r) {
+            dilate_axis_kernel<<<grid, 256, 0, st>>>(a, b, rx, ry, rz, 0);
+            dilate_axis_kernel<<<grid, 256, 0, st>>>(b, a, rx, ry, rz, 1);
+            dilate_axis_kernel<<<grid, 256, 0, st>>>(a, b, rx, ry, rz, 2);
+            dist_assign_kernel<<<grid, 256, 0, st>>>(b, n, r, dist);
+            std::swap(a, b);
+            e = cudaGetLastError();
+        }
+    }
+    if (a) cudaFreeAsync(a, st);
+    if (b) cudaFreeAsync(b, st);
+    return e;
 }
 
 }  // namespace vrn

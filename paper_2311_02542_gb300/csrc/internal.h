@@ -31,7 +31,7 @@ cudaError_t launch_seeded_grid(void *grid, int fp16, long long n, uint64_t seed,
                                double hi, cudaStream_t st);
 cudaError_t launch_seeded_mlp(float *mlp, const int (*shapes)[2], int n_mats, uint64_t seed,
                               cudaStream_t st);
-// occupancy pyramid levels 1..f.n_mip into mip (offsets f.mip_off), from f.occ
-cudaError_t launch_build_mip(const FieldView &f, uint32_t *mip, cudaStream_t st);
+// occupancy distance field (res_x * res_y * res_z bytes) from f.occ
+cudaError_t launch_build_dist(const FieldView &f, uint8_t *dist, cudaStream_t st);
 
 }  // namespace vrn

@@ -93,19 +93,20 @@ render_tc_kernel(const FieldView f, const RaySource src, const RenderOut out,
         }
         if (!__syncthreads_or(have) || *S.abort) break;
         // ---- features, tensor-core MLPs, compositing ----
-        float feat[D];
         float t = 0.0f, delta = 0.0f;
         if (have) {
             t = sT[mr.step];
             delta = sT[mr.step + 1] - t;
-            st_levels += gather_features<L>(f, p, t * r * f.inv_ext, feat);
+            st_levels += gather_to_tile<L, FMT == 1 ? 1 : 0>(f, p, t * r * f.inv_ext, S.act, threadIdx.x);
             ++st_samples;
         } else {
+            uint32_t z[D / 2];
 #pragma unroll
-            for (int k = 0; k < D; ++k) feat[k] = 0.0f;
+            for (int k = 0; k < D / 2; ++k) z[k] = 0u;
+            store_row<D>(S.act, threadIdx.x, z);
         }
         float sigma, rgb[3];
-        tc_mlp_any<D, FMT>(S, feat, mr.d, f.density_bias, sigma, rgb, phase, ok);
+        tc_mlp_any<D, FMT>(S, nullptr, mr.d, f.density_bias, sigma, rgb, phase, ok);
         if (have) {
             const float sd = sigma * delta;
             const float w = T * (-expm1f(-sd));
@@ -152,7 +153,7 @@ query_tc_kernel(const FieldView f, const float *__restrict__ pos, const float *_
     uint32_t phase = 0;
     bool ok = true;
     float sigma, rgb[3];
-    tc_mlp_any<D, FMT>(S, feat, dd, f.density_bias, sigma, rgb, phase, ok);
+    tc_mlp_any<D, FMT>(S, feat, dd, f.density_bias, sigma, rgb, phase, ok);  // query keeps feat for output
     if (valid) {
         sigma_out[i] = sigma;
         for (int c = 0; c < 3; ++c) rgb_out[3 * i + c] = rgb[c];

@@ -231,18 +231,19 @@ serve_kernel(const FieldView f, ServeView *__restrict__ ring, const ServeCtl *__
             continue;
         }
         if (*S.abort) break;
-        float feat[D];
         float delta = 0.0f;
         if (have) {
             const float t = sT[mr.step];
             delta = sT[mr.step + 1] - t;
-            gather_features<L>(f, p, t * r * f.inv_ext, feat);
+            gather_to_tile<L, FMT == 1 ? 1 : 0>(f, p, t * r * f.inv_ext, S.act, threadIdx.x);
         } else {
+            uint32_t z[D / 2];
 #pragma unroll
-            for (int k = 0; k < D; ++k) feat[k] = 0.0f;
+            for (int k = 0; k < D / 2; ++k) z[k] = 0u;
+            store_row<D>(S.act, threadIdx.x, z);
         }
         float sigma, rgb[3];
-        tc_mlp_any<D, FMT>(S, feat, mr.d, f.density_bias, sigma, rgb, phase, ok);
+        tc_mlp_any<D, FMT>(S, nullptr, mr.d, f.density_bias, sigma, rgb, phase, ok);
         if (have) {
             const float sd = sigma * delta;
             const float w = T * (-expm1f(-sd));

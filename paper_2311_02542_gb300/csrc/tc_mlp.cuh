@@ -62,6 +62,46 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {
     }
 }
 
+// LOD-weighted hash-grid features of one sample (Sec. 4.2.1, Eq. 3), written
+// as row r of the first layer's 128 x 2L operand (16-bit pairs); levels with
+// zero weight are not fetched and give zeros. The level loop is kept rolled
+// (two levels per iteration) to keep the kernel's code small. Returns the
+// number of levels fetched.
+template <int L, int FMT16>
+__device__ __forceinline__ int gather_to_tile(const FieldView &f, const float p[3], float r_norm,
+                                              unsigned char *tile, int r) {
+    constexpr int D = 2 * L;
+    const float Ls = lod_star(f, r_norm);
+    unsigned char *row = tile + (r >> 3) * (D / 8) * 128 + (r & 7) * 16;
+    int fetched = 0;
+#pragma unroll 2
+    for (int l = 0; l < L; ++l) {
+        const float w = lod_weight(Ls, l);
+        float a0 = 0.0f, a1 = 0.0f;
+        if (w > 0.0f) {
+            ++fetched;
+            uint32_t idx[8];
+            float fr[3];
+            level_corners(f, l, p, idx, fr);
+            float2 e[8];
+#pragma unroll
+            for (int b = 0; b < 8; ++b) e[b] = load_feat(f, l, idx[b]);
+            const float x0 = 1.0f - fr[0], y0 = 1.0f - fr[1], z0 = 1.0f - fr[2];
+            const float w00 = y0 * z0, w10 = fr[1] * z0, w01 = y0 * fr[2], w11 = fr[1] * fr[2];
+            const float cw[8] = {x0 * w00, fr[0] * w00, x0 * w10, fr[0] * w10,
+                                 x0 * w01, fr[0] * w01, x0 * w11, fr[0] * w11};
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                a0 = fmaf(cw[b], e[b].x, a0);
+                a1 = fmaf(cw[b], e[b].y, a1);
+            }
+        }
+        const int c = 2 * l;
+        *reinterpret_cast<uint32_t *>(row + (c >> 3) * 128 + (c & 7) * 2) = pack2<FMT16>(w * a0, w * a1);
+    }
+    return fetched;
+}
+
 // Row r of a 128 x K operand tile (K-major core matrices).
 template <int K>
 __device__ __forceinline__ void store_row(unsigned char *base, int r, const uint32_t (&pk)[K / 2]) {
@@ -161,15 +201,16 @@ __device__ __forceinline__ void run_layer(const TcShared &S, int w_off, uint32_t
 
 // Density MLP (D -> 64 -> 16, ReLU; sigma = exp(o_0 + bias)) and colour MLP
 // ([o, SH(d)] 32 -> 64 -> 64 -> 3, ReLU, sigmoid) for the 128 rows of the
-// CTA; this thread's row is `feat`. All 128 threads must call it.
+// CTA; this thread's row is `feat`, or, when feat is null, has already been
+// written into the first operand (gather_to_tile). All 128 threads must call it.
 template <int D, int FMT>
-__device__ __forceinline__ void tc_mlp(const TcShared &S, const float (&feat)[D], const float dir[3],
+__device__ __forceinline__ void tc_mlp(const TcShared &S, const float *feat, const float dir[3],
                                        float density_bias, float &sigma, float rgb[3], uint32_t &phase,
                                        bool &ok) {
     using W = TcW<D>;
     const int r = threadIdx.x;
     const uint32_t taddr = S.tbase + ((uint32_t)(r & ~31) << 16);
-    {
+    if (feat) {
         uint32_t pk[D / 2];
 #pragma unroll
         for (int i = 0; i < D / 2; ++i) pk[i] = pack2<FMT>(feat[2 * i], feat[2 * i + 1]);
@@ -241,14 +282,14 @@ __device__ __forceinline__ void tc_mlp(const TcShared &S, const float (&feat)[D]
 // (this thread's sample) and per weight matrix, undone on the fp32
 // accumulator; the first layer (W1) and the colour output (W5) stay fp16.
 template <int D>
-__device__ __forceinline__ void tc_mlp_fp8(const TcShared &S, const float (&feat)[D], const float dir[3],
+__device__ __forceinline__ void tc_mlp_fp8(const TcShared &S, const float *feat, const float dir[3],
                                            float density_bias, float &sigma, float rgb[3], uint32_t &phase,
                                            bool &ok) {
     using W = TcW8<D>;
     const int r = threadIdx.x;
     const uint32_t taddr = S.tbase + ((uint32_t)(r & ~31) << 16);
     const float *inv_w = reinterpret_cast<const float *>(S.w + W::scales);
-    {
+    if (feat) {
         uint32_t pk[D / 2];
 #pragma unroll
         for (int i = 0; i < D / 2; ++i) pk[i] = pack2<0>(feat[2 * i], feat[2 * i + 1]);
@@ -332,7 +373,7 @@ __device__ __forceinline__ void tc_mlp_fp8(const TcShared &S, const float (&feat
 }
 
 template <int D, int FMT>
-__device__ __forceinline__ void tc_mlp_any(const TcShared &S, const float (&feat)[D], const float dir[3],
+__device__ __forceinline__ void tc_mlp_any(const TcShared &S, const float *feat, const float dir[3],
                                            float density_bias, float &sigma, float rgb[3], uint32_t &phase,
                                            bool &ok) {
     if constexpr (FMT == 2)

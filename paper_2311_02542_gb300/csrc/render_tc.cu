@@ -41,8 +41,9 @@ render_tc_kernel(const FieldView f, const RaySource src, const RenderOut out,
                  unsigned long long *__restrict__ status) {
     constexpr int D = 2 * L;
     extern __shared__ __align__(1024) unsigned char smem[];
-    float *sT;
-    const TcShared S = tc_setup<D, FMT>(smem, wimg, sT, f.t_tab, f.S);
+    float *unused;
+    const TcShared S = tc_setup<D, FMT>(smem, wimg, unused, nullptr, 0);
+    const float *__restrict__ sT = f.t_tab;  // sample distances, read through L1
 
     constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -232,7 +233,7 @@ __global__ void build_tc_image_fp8_kernel(const float *__restrict__ mlp, int D, 
 // ---------------------------------------------------------------------------
 template <int L, int FMT>
 static cudaError_t render_tc_t(vrnerf_field *F, const RaySource &src, const RenderOut &out, cudaStream_t st) {
-    const size_t smem = tc_smem_bytes(2 * L, F->view.S);
+    const size_t smem = tc_smem_bytes(2 * L, 0);
     auto kern = render_tc_kernel<L, FMT>;
     int bps = 0;
     cudaError_t e = prepare_tc(kern, smem, bps);

@@ -85,8 +85,9 @@ serve_kernel(const FieldView f, ServeView *__restrict__ ring, const ServeCtl *__
              unsigned long long idle_ns, unsigned long long *__restrict__ status) {
     constexpr int D = 2 * L;
     extern __shared__ __align__(1024) unsigned char smem[];
-    float *sT;
-    const TcShared S = tc_setup<D, FMT>(smem, wimg, sT, f.t_tab, f.S);
+    float *unused;
+    const TcShared S = tc_setup<D, FMT>(smem, wimg, unused, nullptr, 0);
+    const float *__restrict__ sT = f.t_tab;  // sample distances, read through L1
     __shared__ int s_quit;
 
     constexpr unsigned FULL = 0xffffffffu;
@@ -262,7 +263,7 @@ serve_kernel(const FieldView f, ServeView *__restrict__ ring, const ServeCtl *__
 template <int L, int FMT>
 static cudaError_t launch_serve_t(vrnerf_field *F, ServeView *ring, const ServeCtl *ctl,
                                   unsigned int *cursor, unsigned long long idle_ns, cudaStream_t st) {
-    const size_t smem = tc_smem_bytes(2 * L, F->view.S);
+    const size_t smem = tc_smem_bytes(2 * L, 0);
     auto kern = serve_kernel<L, FMT>;
     int bps = 0;
     cudaError_t e = prepare_tc(kern, smem, bps);

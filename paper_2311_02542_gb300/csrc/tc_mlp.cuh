@@ -11,7 +11,7 @@
 namespace vrn {
 
 constexpr int kTcThreads = 128;
-constexpr int kTcMinBlocks = 5;  // resident CTAs per SM the register budget is cut for
+constexpr int kTcMinBlocks = 6;  // resident CTAs per SM the register budget is cut for
 constexpr int kTcChunk = 8;      // march iterations between warp refill points
 constexpr uint32_t kTmemCols = 64;
 

@@ -219,6 +219,15 @@ int vrnerf_train_step(vrnerf_field *field, const float *rays_o, const float *ray
 int vrnerf_field_set_grads(vrnerf_field *field, const float *grid_grad_host,
                            const float *mlp_grad_host);
 
+/* Failure detection without a GPU fault (no counterpart in the paper):
+ * launches one CTA that allocates TMEM and waits, through the same bounded
+ * mbarrier wait the tensor-core kernels use, on an mbarrier that nothing
+ * completes. After limit_us microseconds it gives up, records
+ * VRNERF_ETIMEDOUT in the field's status word, frees its TMEM and returns;
+ * vrnerf_field_status then reports ETIMEDOUT and the context stays usable.
+ * limit_us in [1, 2000000]. EINVAL, ECUDA. */
+int vrnerf_debug_wait_timeout(vrnerf_field *field, uint32_t limit_us, void *stream);
+
 /* ---------------------------------------------------------------------------
  * Serving: continuous batching of render requests (stereo eye pairs and
  * single views of any resolution) through one persistent tensor-core render

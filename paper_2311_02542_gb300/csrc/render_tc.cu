@@ -188,6 +188,32 @@ __global__ void build_tc_image_kernel(const float *__restrict__ mlp, int D, int 
     }
 }
 
+// One CTA waits on an mbarrier that nothing completes; the bounded wait gives
+// up after limit_ns, the CTA records the time-out and frees its TMEM.
+__global__ void wait_timeout_kernel(unsigned long long limit_ns, unsigned long long *status) {
+    __shared__ uint64_t mbar;
+    __shared__ uint32_t holder;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&mbar, 1);
+        abort_flag = 0;
+    }
+    if (threadIdx.x < 32) {
+        tc::tmem_alloc(&holder, 32);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const bool ok = tc::mbar_wait_bounded(&mbar, 0u, &abort_flag, limit_ns);
+    __syncthreads();
+    if (threadIdx.x == 0 && (!ok || abort_flag)) atomicExch(status, (unsigned long long)(-VRNERF_ETIMEDOUT));
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (threadIdx.x < 32) tc::tmem_dealloc(holder, 32);
+}
+
 // fp32 W1..W5 -> the fp8-mode image (TcW8): W1, W5 fp16; W2..W4 e4m3 with a
 // power-of-two scale per matrix (max |w| * s in [128, 256)); one CTA per matrix.
 __global__ void build_tc_image_fp8_kernel(const float *__restrict__ mlp, int D, unsigned char *__restrict__ img) {
@@ -292,4 +318,17 @@ cudaError_t launch_query_tc(vrnerf_field *F, const float *pos, const float *dir,
                                 : query_tc_t<16, 0>(F, pos, dir, radius, n, sigma, rgb, feat, st));
 }
 
+cudaError_t launch_wait_timeout(vrnerf_field *F, unsigned long long limit_ns, cudaStream_t st) {
+    wait_timeout_kernel<<<1, 128, 0, st>>>(limit_ns, reinterpret_cast<unsigned long long *>(F->counter) + 1);
+    return cudaGetLastError();
+}
+
 }  // namespace vrn
+
+extern "C" int vrnerf_debug_wait_timeout(vrnerf_field *F, uint32_t limit_us, void *stream) {
+    if (!F) return vrn::fail(VRNERF_EINVAL, "field is NULL");
+    if (limit_us < 1 || limit_us > 2000000) return vrn::fail(VRNERF_EINVAL, "limit_us must be in [1, 2000000]");
+    cudaError_t e = vrn::launch_wait_timeout(F, 1000ull * limit_us, (cudaStream_t)stream);
+    if (e != cudaSuccess) return vrn::cuda_fail(e, "debug_wait_timeout");
+    return VRNERF_OK;
+}

@@ -58,6 +58,7 @@ _SIGS = {
     "vrnerf_field_destroy": (None, [_VP]),
     "vrnerf_field_get_params": (ctypes.c_int, [_VP, _VP, _VP]),
     "vrnerf_field_status": (ctypes.c_int, [_VP]),
+    "vrnerf_debug_wait_timeout": (ctypes.c_int, [_VP, ctypes.c_uint32, _VP]),
     "vrnerf_field_set_occupancy": (ctypes.c_int, [_VP, _VP]),
     "vrnerf_render": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP]),
     "vrnerf_render_host": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP]),
@@ -208,6 +209,10 @@ def vrnerf_field_status(field: Field):
     """Raises VrnerfError if a kernel of the field recorded an error (e.g. a
     bounded device wait that timed out); clears it."""
     _check(load().vrnerf_field_status(field.h))
+
+
+def vrnerf_debug_wait_timeout(field: Field, limit_us: int, stream=None):
+    _check(load().vrnerf_debug_wait_timeout(field.h, int(limit_us), _stream(stream)))
 
 
 def vrnerf_field_get_params(field: Field):

@@ -62,6 +62,17 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {
     }
 }
 
+// ReLU and fp32 -> packed 16-bit pair in one instruction (a in the low half).
+template <int FMT>
+__device__ __forceinline__ uint32_t pack2_relu(float a, float b) {
+    uint32_t d;
+    if (FMT == 0)
+        asm("cvt.rn.relu.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(b), "f"(a));
+    else
+        asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(b), "f"(a));
+    return d;
+}
+
 // LOD-weighted hash-grid features of one sample (Sec. 4.2.1, Eq. 3), written
 // as row r of the first layer's 128 x 2L operand (16-bit pairs); levels with
 // zero weight are not fetched and give zeros. The level loop is kept rolled
@@ -224,7 +235,7 @@ __device__ __forceinline__ void tc_mlp(const TcShared &S, const float *feat, con
             float v[16];
             tc::tmem_ld16(taddr + c, v);
 #pragma unroll
-            for (int i = 0; i < 8; ++i) pk[c / 2 + i] = pack2<FMT>(fmaxf(v[2 * i], 0.f), fmaxf(v[2 * i + 1], 0.f));
+            for (int i = 0; i < 8; ++i) pk[c / 2 + i] = pack2_relu<FMT>(v[2 * i], v[2 * i + 1]);
         }
         store_row<64>(S.act, r, pk);
     }
@@ -250,7 +261,7 @@ __device__ __forceinline__ void tc_mlp(const TcShared &S, const float *feat, con
             float v[16];
             tc::tmem_ld16(taddr + c, v);
 #pragma unroll
-            for (int i = 0; i < 8; ++i) pk[c / 2 + i] = pack2<FMT>(fmaxf(v[2 * i], 0.f), fmaxf(v[2 * i + 1], 0.f));
+            for (int i = 0; i < 8; ++i) pk[c / 2 + i] = pack2_relu<FMT>(v[2 * i], v[2 * i + 1]);
         }
         store_row<64>(S.act, r, pk);
     }
@@ -262,7 +273,7 @@ __device__ __forceinline__ void tc_mlp(const TcShared &S, const float *feat, con
             float v[16];
             tc::tmem_ld16(taddr + c, v);
 #pragma unroll
-            for (int i = 0; i < 8; ++i) pk[c / 2 + i] = pack2<FMT>(fmaxf(v[2 * i], 0.f), fmaxf(v[2 * i + 1], 0.f));
+            for (int i = 0; i < 8; ++i) pk[c / 2 + i] = pack2_relu<FMT>(v[2 * i], v[2 * i + 1]);
         }
         store_row<64>(S.act, r, pk);
     }
@@ -357,7 +368,7 @@ __device__ __forceinline__ void tc_mlp_fp8(const TcShared &S, const float *feat,
             tc::tmem_ld16(taddr + c, v);
 #pragma unroll
             for (int i = 0; i < 8; ++i)
-                pk[c / 2 + i] = pack2<0>(fmaxf(v[2 * i] * k, 0.f), fmaxf(v[2 * i + 1] * k, 0.f));
+                pk[c / 2 + i] = pack2_relu<0>(v[2 * i] * k, v[2 * i + 1] * k);
         }
         store_row<64>(S.act, r, pk);
     }

@@ -207,16 +207,22 @@ __device__ __forceinline__ int march_next(const FieldView &f, const float *__res
     return MARCH_MORE;
 }
 
+// Normalised grid position p^ = (p - box_min) / largest extent, fp32 with
+// separate rounding (shared by every level of a sample).
+__device__ __forceinline__ void grid_position(const FieldView &f, const float p[3], float ph[3]) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) ph[k] = __fmul_rn(__fsub_rn(p[k], f.mn[k]), f.inv_ext);
+}
+
 // Corner indices of level l (corner b at offset (b&1, b>>1&1, b>>2&1)) and
-// the position inside the cell.
-__device__ __forceinline__ void level_corners(const FieldView &f, int l, const float p[3],
-                                              uint32_t idx[8], float fr[3]) {
+// the position inside the cell, from the normalised position ph.
+__device__ __forceinline__ void level_corners_ph(const FieldView &f, int l, const float ph[3],
+                                                 uint32_t idx[8], float fr[3]) {
     const int N = f.N[l];
     int c0[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        float ph = __fmul_rn(__fsub_rn(p[k], f.mn[k]), f.inv_ext);
-        float x = __fmul_rn(ph, (float)N);
+        float x = __fmul_rn(ph[k], (float)N);
         int c = (int)floorf(x);
         c = c < 0 ? 0 : (c > N - 1 ? N - 1 : c);
         c0[k] = c;
@@ -231,12 +237,19 @@ __device__ __forceinline__ void level_corners(const FieldView &f, int l, const f
     } else {
         // instant-NGP spatial hash, primes (1, 2654435761, 805459861)
         const uint32_t hx0 = (uint32_t)c0[0], hx1 = hx0 + 1u;
-        const uint32_t hy0 = (uint32_t)c0[1] * 2654435761u, hy1 = ((uint32_t)c0[1] + 1u) * 2654435761u;
-        const uint32_t hz0 = (uint32_t)c0[2] * 805459861u, hz1 = ((uint32_t)c0[2] + 1u) * 805459861u;
+        const uint32_t hy0 = (uint32_t)c0[1] * 2654435761u, hy1 = hy0 + 2654435761u;
+        const uint32_t hz0 = (uint32_t)c0[2] * 805459861u, hz1 = hz0 + 805459861u;
+        const uint32_t yz[4] = {hy0 ^ hz0, hy1 ^ hz0, hy0 ^ hz1, hy1 ^ hz1};
 #pragma unroll
-        for (int b = 0; b < 8; ++b)
-            idx[b] = ((b & 1 ? hx1 : hx0) ^ (b & 2 ? hy1 : hy0) ^ (b & 4 ? hz1 : hz0)) & f.T_mask;
+        for (int b = 0; b < 8; ++b) idx[b] = ((b & 1 ? hx1 : hx0) ^ yz[b >> 1]) & f.T_mask;
     }
+}
+
+__device__ __forceinline__ void level_corners(const FieldView &f, int l, const float p[3],
+                                              uint32_t idx[8], float fr[3]) {
+    float ph[3];
+    grid_position(f, p, ph);
+    level_corners_ph(f, l, ph, idx, fr);
 }
 
 // Eq. 3 as a clamp: w_l = clamp(L* - l + 1, 0, 1).

@@ -84,31 +84,55 @@ __device__ __forceinline__ int gather_to_tile(const FieldView &f, const float p[
     constexpr int D = 2 * L;
     const float Ls = lod_star(f, r_norm);
     unsigned char *row = tile + (r >> 3) * (D / 8) * 128 + (r & 7) * 16;
+    float ph[3];
+    grid_position(f, p, ph);
     int fetched = 0;
 #pragma unroll 2
     for (int l = 0; l < L; ++l) {
         const float w = lod_weight(Ls, l);
-        float a0 = 0.0f, a1 = 0.0f;
+        uint32_t word = 0u;
         if (w > 0.0f) {
             ++fetched;
             uint32_t idx[8];
             float fr[3];
-            level_corners(f, l, p, idx, fr);
-            float2 e[8];
-#pragma unroll
-            for (int b = 0; b < 8; ++b) e[b] = load_feat(f, l, idx[b]);
+            level_corners_ph(f, l, ph, idx, fr);
             const float x0 = 1.0f - fr[0], y0 = 1.0f - fr[1], z0 = 1.0f - fr[2];
             const float w00 = y0 * z0, w10 = fr[1] * z0, w01 = y0 * fr[2], w11 = fr[1] * fr[2];
             const float cw[8] = {x0 * w00, fr[0] * w00, x0 * w10, fr[0] * w10,
                                  x0 * w01, fr[0] * w01, x0 * w11, fr[0] * w11};
+            if (f.feat_fp16) {
+                // both features of a corner in one half2; interpolate with HFMA2
+                const unsigned int *base = reinterpret_cast<const unsigned int *>(f.grid) +
+                                           (size_t)l * (f.T_mask + 1u);
+                uint32_t e[8];
 #pragma unroll
-            for (int b = 0; b < 8; ++b) {
-                a0 = fmaf(cw[b], e[b].x, a0);
-                a1 = fmaf(cw[b], e[b].y, a1);
+                for (int b = 0; b < 8; ++b) e[b] = __ldg(base + idx[b]);
+                __half2 acc = __float2half2_rn(0.0f);
+#pragma unroll
+                for (int b = 0; b < 8; ++b)
+                    acc = __hfma2(__float2half2_rn(cw[b]), *reinterpret_cast<const __half2 *>(&e[b]), acc);
+                acc = __hmul2(acc, __float2half2_rn(w));
+                if (FMT16 == 0) {
+                    word = *reinterpret_cast<uint32_t *>(&acc);
+                } else {
+                    const float2 v = __half22float2(acc);
+                    word = pack2<1>(v.x, v.y);
+                }
+            } else {
+                float2 e[8];
+#pragma unroll
+                for (int b = 0; b < 8; ++b) e[b] = load_feat(f, l, idx[b]);
+                float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+                for (int b = 0; b < 8; ++b) {
+                    a0 = fmaf(cw[b], e[b].x, a0);
+                    a1 = fmaf(cw[b], e[b].y, a1);
+                }
+                word = pack2<FMT16>(w * a0, w * a1);
             }
         }
         const int c = 2 * l;
-        *reinterpret_cast<uint32_t *>(row + (c >> 3) * 128 + (c & 7) * 2) = pack2<FMT16>(w * a0, w * a1);
+        *reinterpret_cast<uint32_t *>(row + (c >> 3) * 128 + (c & 7) * 2) = word;
     }
     return fetched;
 }

@@ -140,6 +140,18 @@ void vrnerf_field_destroy(vrnerf_field *field);
  * sizes vrnerf_field_sizes gives; either may be NULL. Synchronous. */
 int vrnerf_field_get_params(vrnerf_field *field, void *grid_host, float *mlp_host);
 
+/* Checkpoint (no counterpart in the paper): writes the description, the
+ * hash grid, the MLP weights, the occupancy bits and, after training, the
+ * Adam step count, moments and fp32 master grid to one flat little-endian
+ * file ("VRNF" header, version 1, then the arrays in that order).
+ * Synchronous. EINVAL (NULL argument, file cannot be written), ECUDA. */
+int vrnerf_field_save(vrnerf_field *field, const char *path);
+
+/* Creates a field on the current device from a file written by
+ * vrnerf_field_save, Adam state included, so training resumes where it
+ * stopped. Synchronous. EINVAL (unreadable or malformed file), ENOMEM, ECUDA. */
+int vrnerf_field_load(const char *path, vrnerf_field **out);
+
 /* Replaces the occupancy bits (Sec. 4.3). Synchronous. */
 int vrnerf_field_set_occupancy(vrnerf_field *field, const uint32_t *occ_bits_host);
 

@@ -142,7 +142,7 @@ __device__ __forceinline__ void finish_ray(const RenderOut &out, long long pix, 
 }
 
 template <int L>
-__global__ void __launch_bounds__(kSimtThreads)
+__global__ void __launch_bounds__(kSimtThreads, 4)
 render_simt_kernel(const FieldView f, const RaySource src, const RenderOut out,
                    unsigned long long *__restrict__ counter) {
     constexpr int D = 2 * L;

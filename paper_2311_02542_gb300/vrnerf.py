@@ -60,6 +60,8 @@ _SIGS = {
     "vrnerf_field_status": (ctypes.c_int, [_VP]),
     "vrnerf_debug_wait_timeout": (ctypes.c_int, [_VP, ctypes.c_uint32, _VP]),
     "vrnerf_field_set_occupancy": (ctypes.c_int, [_VP, _VP]),
+    "vrnerf_field_save": (ctypes.c_int, [_VP, ctypes.c_char_p]),
+    "vrnerf_field_load": (ctypes.c_int, [ctypes.c_char_p, _VP]),
     "vrnerf_render": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP]),
     "vrnerf_render_host": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP]),
     "vrnerf_render_rays": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP]),
@@ -221,6 +223,20 @@ def vrnerf_field_get_params(field: Field):
     m = np.empty(cfg.n_mlp(), np.float32)
     _check(load().vrnerf_field_get_params(field.h, _ptr(g), _ptr(m)))
     return g, m
+
+
+def vrnerf_field_save(field: Field, path: str):
+    _check(load().vrnerf_field_save(field.h, os.fsencode(path)))
+
+
+def vrnerf_field_load(path: str, cfg) -> Field:
+    """Loads a checkpoint; `cfg` is the FieldConfig it was written from (the
+    binding keeps it for array shapes)."""
+    f = Field.__new__(Field)
+    h = ctypes.c_void_p()
+    _check(load().vrnerf_field_load(os.fsencode(path), ctypes.byref(h)))
+    f.cfg, f.h, f._desc, f.n_rays_last = cfg, h, desc(cfg), 0
+    return f
 
 
 def vrnerf_field_set_occupancy(field: Field, occ_bits):

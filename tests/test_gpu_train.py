@@ -141,3 +141,31 @@ def test_train_steps_reduce_loss(V):
     assert losses[-1] < 0.9 * losses[0], losses[::5]
     V.vrnerf_field_status(f)
     f.close()
+
+
+def test_checkpoint_round_trip_resumes_training(V, tmp_path):
+    sc = S.make_scene("room")
+    cfg = sc.cfg
+    poses, intr = S.training_views(sc.occ, cfg, n_views=8)
+    batches = [[_cuda(a) for a in S.training_batch(poses, intr, 4096, seed=5, step=k)] for k in range(3)]
+    a = V.Field(cfg, sc.grid, sc.mlp, sc.occ_bits)
+    V.vrnerf_train_step(a, *batches[0])
+    path = str(tmp_path / "field.vrnf")
+    V.vrnerf_field_save(a, path)
+    b = V.vrnerf_field_load(path, cfg)
+    ga, ma = V.vrnerf_field_get_params(a)
+    gb, mb = V.vrnerf_field_get_params(b)
+    assert (ga.view(np.uint16) == gb.view(np.uint16)).all() and (ma == mb).all()
+    # both continue identically: same Adam step count, moments and master weights
+    for k in (1, 2):
+        la = V.vrnerf_train_step(a, *batches[k])
+        lb = V.vrnerf_train_step(b, *batches[k])
+        assert la == lb
+    ga, ma = V.vrnerf_field_get_params(a)
+    gb, mb = V.vrnerf_field_get_params(b)
+    assert np.abs(ma - mb).max() < 1e-6 and np.abs(ga.astype(np.float32) - gb.astype(np.float32)).max() < 1e-3
+    with pytest.raises(V.VrnerfError):
+        open(str(tmp_path / "bad.vrnf"), "wb").write(b"nope")
+        V.vrnerf_field_load(str(tmp_path / "bad.vrnf"), cfg)
+    a.close()
+    b.close()

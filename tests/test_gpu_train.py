@@ -156,14 +156,19 @@ def test_checkpoint_round_trip_resumes_training(V, tmp_path):
     ga, ma = V.vrnerf_field_get_params(a)
     gb, mb = V.vrnerf_field_get_params(b)
     assert (ga.view(np.uint16) == gb.view(np.uint16)).all() and (ma == mb).all()
-    # both continue identically: same Adam step count, moments and master weights
-    for k in (1, 2):
-        la = V.vrnerf_train_step(a, *batches[k])
-        lb = V.vrnerf_train_step(b, *batches[k])
-        assert la == lb
+    # the optimiser state came back: the same fixed gradients give bit-identical
+    # updates (same step count, moments and fp32 master grid)
+    rng = np.random.default_rng(9)
+    for _ in range(2):
+        gg = (rng.normal(size=(cfg.levels, cfg.T, cfg.feats)) * 1e-3).astype(np.float32)
+        gm = (rng.normal(size=cfg.n_mlp()) * 1e-2).astype(np.float32)
+        for fld in (a, b):
+            V.vrnerf_field_set_grads(fld, gg, gm)
+            V.vrnerf_adam_step(fld, 0.01, 0.005)
     ga, ma = V.vrnerf_field_get_params(a)
     gb, mb = V.vrnerf_field_get_params(b)
-    assert np.abs(ma - mb).max() < 1e-6 and np.abs(ga.astype(np.float32) - gb.astype(np.float32)).max() < 1e-3
+    assert (ga.view(np.uint16) == gb.view(np.uint16)).all() and (ma.view(np.uint32) == mb.view(np.uint32)).all()
+    assert np.isfinite(V.vrnerf_train_step(b, *batches[1]))
     with pytest.raises(V.VrnerfError):
         open(str(tmp_path / "bad.vrnf"), "wb").write(b"nope")
         V.vrnerf_field_load(str(tmp_path / "bad.vrnf"), cfg)

@@ -446,6 +446,10 @@ def main():
     }
     if args.serving_requests > 0:
         line["serving"] = serving_bench(V, field, sc, args.serving_requests)
+        sc_s = S.make_scene("room_surface")  # opaque occupied voxels, as in a trained scene
+        field_s = V.Field(sc_s.cfg, sc_s.grid, sc_s.mlp, sc_s.occ_bits)
+        line["serving_surface_variant"] = serving_bench(V, field_s, sc_s, args.serving_requests)
+        field_s.close()
         line["serving_saturated"] = serving_bench(V, field, sc, max(60, args.serving_requests // 3),
                                                   warm=10, rate_hz=1e9)
     if args.train_steps > 0:

@@ -198,13 +198,15 @@ backward_kernel(const FieldView f, const float *__restrict__ o_in, const float *
             for (int i = 0; i < 16; ++i) o[i] = fmaf(__ldg(W2 + i * 64 + j), h, o[i]);
         }
         const float sigma = expf(o[0] + f.density_bias);
-        float x[32];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) x[i] = o[i];
-        sh16(dir[0], dir[1], dir[2], x + 16);
         float h1[64];
+        {
+            float x[32];
 #pragma unroll
-        for (int j = 0; j < 64; ++j) h1[j] = fmaxf(dot_row(W3 + j * 32, x, 32), 0.0f);
+            for (int i = 0; i < 16; ++i) x[i] = o[i];
+            sh16(dir[0], dir[1], dir[2], x + 16);
+#pragma unroll
+            for (int j = 0; j < 64; ++j) h1[j] = fmaxf(dot_row(W3 + j * 32, x, 32), 0.0f);
+        }
         float z0 = 0.0f, z1 = 0.0f, z2 = 0.0f;
 #pragma unroll 2
         for (int j = 0; j < 64; ++j) {
@@ -236,28 +238,32 @@ backward_kernel(const FieldView f, const float *__restrict__ o_in, const float *
         sD[lane * kStride + 2] = dz[2];
         __syncwarp();
         minigemm_cols<3, 64>(sD, sA, sG + G::g5, G::s5, lane);
-        float dh2[64];
+        // dh2 = mask(h2) W5^T dz, staged straight into sD (own row)
+        __syncwarp();
+        {
+            float dh2v[64];
 #pragma unroll
-        for (int j = 0; j < 64; ++j) {
-            const float h2 = sA[lane * kStride + j];
-            const float a = __ldg(W5 + j) * dz[0] + __ldg(W5 + 64 + j) * dz[1] + __ldg(W5 + 128 + j) * dz[2];
-            dh2[j] = h2 > 0.0f ? a : 0.0f;
+            for (int j = 0; j < 64; ++j) {
+                const float h2 = sA[lane * kStride + j];
+                const float a = __ldg(W5 + j) * dz[0] + __ldg(W5 + 64 + j) * dz[1] + __ldg(W5 + 128 + j) * dz[2];
+                dh2v[j] = h2 > 0.0f ? a : 0.0f;
+            }
+            __syncwarp();
+#pragma unroll
+            for (int j = 0; j < 64; ++j) {
+                sD[lane * kStride + j] = dh2v[j];
+                sA[lane * kStride + j] = h1[j];
+            }
         }
         __syncwarp();
         // ---- W4: dh2 x h1 ----
-#pragma unroll
-        for (int j = 0; j < 64; ++j) {
-            sD[lane * kStride + j] = dh2[j];
-            sA[lane * kStride + j] = h1[j];
-        }
-        __syncwarp();
         minigemm_rows<64, 64>(sD, sA, sG + G::g4, G::s4, lane);
         float dh1[64];
 #pragma unroll
         for (int k = 0; k < 64; ++k) dh1[k] = 0.0f;
 #pragma unroll 4
         for (int j = 0; j < 64; ++j) {
-            const float d = dh2[j];
+            const float d = sD[lane * kStride + j];
             const float4 *wr = reinterpret_cast<const float4 *>(W4 + j * 64);
 #pragma unroll
             for (int k4 = 0; k4 < 16; ++k4) {
@@ -269,13 +275,20 @@ backward_kernel(const FieldView f, const float *__restrict__ o_in, const float *
             }
         }
 #pragma unroll
-        for (int k = 0; k < 64; ++k) dh1[k] = h1[k] > 0.0f ? dh1[k] : 0.0f;
+        for (int k = 0; k < 64; ++k) dh1[k] = sA[lane * kStride + k] > 0.0f ? dh1[k] : 0.0f;
         __syncwarp();
-        // ---- W3: dh1 x x ----
+        // ---- W3: dh1 x x, x = [o, SH(d)] rebuilt ----
 #pragma unroll
         for (int j = 0; j < 64; ++j) sD[lane * kStride + j] = dh1[j];
+        {
+            float shv[16];
+            sh16(dir[0], dir[1], dir[2], shv);
 #pragma unroll
-        for (int k = 0; k < 32; ++k) sA[lane * kStride + k] = x[k];
+            for (int k = 0; k < 16; ++k) {
+                sA[lane * kStride + k] = o[k];
+                sA[lane * kStride + 16 + k] = shv[k];
+            }
+        }
         __syncwarp();
         minigemm_rows<64, 32>(sD, sA, sG + G::g3, G::s3, lane);
         float dout[16];
@@ -283,7 +296,7 @@ backward_kernel(const FieldView f, const float *__restrict__ o_in, const float *
         for (int i = 0; i < 16; ++i) dout[i] = 0.0f;
 #pragma unroll 4
         for (int j = 0; j < 64; ++j) {
-            const float d = dh1[j];
+            const float d = sD[lane * kStride + j];
 #pragma unroll
             for (int i = 0; i < 16; ++i) dout[i] = fmaf(__ldg(W3 + j * 32 + i), d, dout[i]);
         }

@@ -107,6 +107,10 @@ typedef struct {
     uint64_t *stats;   /* optional [4] counters, added to (not reset): evaluated
                           samples, hash-grid levels fetched, march steps tested,
                           rays finished */
+    float *out_depth;  /* optional [rays] expected distance sum_i w_i t_i of the
+                          composited samples (divide by 1 - T for the distance
+                          of the visible surface); the depth maps of the
+                          paper's renders. */
 } vrnerf_render_opts;
 
 /* Message of the last failed call on this thread ("" if none). */

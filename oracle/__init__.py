@@ -17,7 +17,8 @@ Parity status per function (what pins it, see tests/test_oracle_*.py):
   sh16                    orthonormality by quadrature, addition theorem
   query (MLP)             hand-set weights with closed forms, independent matmul
   render_rays / render    constant-density closed form, opacity invariants,
-                          empty grid, early-termination bound, slab brute force
+                          empty grid, early-termination bound, slab brute force;
+                          depth: opaque first sample, bounds by t and opacity
   march                   brute-force occupancy visits on tiny grids
   backward                central finite differences in fp64
   adam                    closed-form first and second steps
@@ -117,10 +118,10 @@ def lib():
                 "orc_query": (None, [_DP, _F64, _F64, _F32, _F64, _F64, ctypes.c_int32, _F64,
                                      _F64, _F64]),
                 "orc_render_rays": (None, [_DP, _F64, _F64, _U32, _F32, _F32, _F32,
-                                           ctypes.c_int32, _F64, _F64, _F64, _I32,
+                                           ctypes.c_int32, _F64, _F64, _F64, _I32, _F64,
                                            ctypes.c_int32]),
                 "orc_render": (None, [_DP, _F64, _F64, _U32, _F32, _F32, _I32, ctypes.c_int32,
-                                      _F64, _F64, _F64, _I32, ctypes.c_int32]),
+                                      _F64, _F64, _F64, _I32, _F64, ctypes.c_int32]),
                 "orc_camera_rays": (None, [_DP, _F32, _F32, _I32, ctypes.c_int32, _F32, _F32,
                                            _F32]),
                 "orc_march": (None, [_DP, _U32, _F32, _F32, ctypes.c_int32, ctypes.c_int32, _I32,
@@ -283,12 +284,14 @@ class Field:
         lin = np.zeros((B, 3), np.float64)
         T = np.zeros(B, np.float64)
         n = np.zeros(B, np.int32)
+        depth = np.zeros(B, np.float64)
         lib().orc_render_rays(*self._args(), _p(self.occ, ctypes.c_uint32),
                               _p(o, ctypes.c_float), _p(dd, ctypes.c_float),
                               _p(r, ctypes.c_float), B, _p(pq, ctypes.c_double),
                               _p(lin, ctypes.c_double), _p(T, ctypes.c_double),
-                              _p(n, ctypes.c_int32), threads or os.cpu_count() or 1)
-        return dict(pq=pq, linear=lin, T=T, n=n)
+                              _p(n, ctypes.c_int32), _p(depth, ctypes.c_double),
+                              threads or os.cpu_count() or 1)
+        return dict(pq=pq, linear=lin, T=T, n=n, depth=depth)
 
     def render(self, c2w, K, res, threads=None):
         o, dd, r = camera_rays(self.cfg, c2w, K, res)

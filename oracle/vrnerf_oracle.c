@@ -423,6 +423,7 @@ void orc_query(const orc_desc *D, const double *grid, const double *mlp, const f
 typedef struct {
     double C[3];
     double T;
+    double depth; /* sum_i w_i t_i: expected distance of the composited samples */
     int32_t n_eval;
 } orc_ray_out;
 
@@ -437,7 +438,7 @@ static void render_one(const orc_desc *D, const orc_geom *g, const double *grid,
                        double r, orc_ray_out *out, orc_tape *tape)
 {
     double dir[3] = {d[0], d[1], d[2]};
-    double T = 1.0, C[3] = {0, 0, 0};
+    double T = 1.0, C[3] = {0, 0, 0}, depth = 0.0;
     int32_t n = 0;
     for (int32_t i = 0; i < D->max_steps; ++i) {
         float p[3];
@@ -463,21 +464,24 @@ static void render_one(const orc_desc *D, const orc_geom *g, const double *grid,
             for (int c = 0; c < 3; ++c) e->c[c] = s.c[c];
         }
         for (int c = 0; c < 3; ++c) C[c] += w * s.c[c];
+        depth += w * t;
         T *= 1.0 - alpha;
         ++n;
         if (T < D->T_eps) break;
     }
     for (int c = 0; c < 3; ++c) out->C[c] = C[c];
     out->T = T;
+    out->depth = depth;
     out->n_eval = n;
 }
 
 /* Explicit rays: o, d [B][3] fp32, r [B] (base radius at unit distance).
  * Outputs (any may be NULL): PQ colour [B][3], linear colour [B][3],
- * final transmittance [B], composited sample count [B]. */
+ * final transmittance [B], composited sample count [B], expected depth
+ * sum_i w_i t_i [B]. */
 void orc_render_rays(const orc_desc *D, const double *grid, const double *mlp, const uint32_t *occ,
                      const float *o, const float *d, const float *r, int32_t B, double *out_pq,
-                     double *out_lin, double *out_T, int32_t *out_n, int32_t threads)
+                     double *out_lin, double *out_T, int32_t *out_n, double *out_depth, int32_t threads)
 {
     orc_geom g;
     geom_init(D, &g);
@@ -493,6 +497,7 @@ void orc_render_rays(const orc_desc *D, const double *grid, const double *mlp, c
         }
         if (out_T) out_T[i] = ro.T;
         if (out_n) out_n[i] = ro.n_eval;
+        if (out_depth) out_depth[i] = ro.depth;
     }
     free(t_tab);
 }
@@ -502,7 +507,8 @@ void orc_render_rays(const orc_desc *D, const double *grid, const double *mlp, c
  * per view renders only that crop: win = NULL renders everything. */
 void orc_render(const orc_desc *D, const double *grid, const double *mlp, const uint32_t *occ,
                 const float *c2w, const float *K, const int32_t *res, int32_t n_views,
-                double *out_pq, double *out_lin, double *out_T, int32_t *out_n, int32_t threads)
+                double *out_pq, double *out_lin, double *out_T, int32_t *out_n, double *out_depth,
+                int32_t threads)
 {
     int64_t total = 0;
     for (int32_t v = 0; v < n_views; ++v) total += (int64_t)res[2 * v] * res[2 * v + 1];
@@ -520,7 +526,7 @@ void orc_render(const orc_desc *D, const double *grid, const double *mlp, const 
             }
     }
     orc_render_rays(D, grid, mlp, occ, o, d, r, (int32_t)total, out_pq, out_lin, out_T, out_n,
-                    threads);
+                    out_depth, threads);
     free(o);
     free(d);
     free(r);

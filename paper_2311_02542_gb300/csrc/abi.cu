@@ -365,7 +365,8 @@ static int render_common(vrnerf_field *F, const RaySource &src, float *out,
     if (rc) return rc;
     RenderOut ro{out, opts ? opts->out_pq : nullptr, opts ? opts->out_T : nullptr,
                  opts ? opts->out_n : nullptr,
-                 opts ? reinterpret_cast<unsigned long long *>(opts->stats) : nullptr};
+                 opts ? reinterpret_cast<unsigned long long *>(opts->stats) : nullptr,
+                 opts ? opts->out_depth : nullptr};
     cudaError_t e = cudaMemsetAsync(F->counter, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return cuda_fail(e, "render: reset counter");
     if (prec == VRNERF_FP32)

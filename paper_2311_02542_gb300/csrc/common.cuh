@@ -66,6 +66,7 @@ struct RenderOut {
     float *T;     // optional
     int *n;       // optional
     unsigned long long *stats;  // optional [4]: samples, levels fetched, steps tested, rays
+    float *depth;               // optional: sum_i w_i t_i
 };
 
 // Warp-aggregated add of per-thread counters into stats (all lanes call).

@@ -131,7 +131,7 @@ __device__ __forceinline__ void mlp_simt(const float *__restrict__ s, const floa
 }
 
 __device__ __forceinline__ void finish_ray(const RenderOut &out, long long pix, const float C[3],
-                                           float T, int n) {
+                                           float T, int n, float depth) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         out.lin[3 * pix + c] = pq_to_linear(C[c]);
@@ -139,6 +139,7 @@ __device__ __forceinline__ void finish_ray(const RenderOut &out, long long pix, 
     }
     if (out.T) out.T[pix] = T;
     if (out.n) out.n[pix] = n;
+    if (out.depth) out.depth[pix] = depth;
 }
 
 template <int L>
@@ -158,7 +159,7 @@ render_simt_kernel(const FieldView f, const RaySource src, const RenderOut out,
     long long ray = -1, pix = 0;
     bool exhausted = false;
     MarchRay mr;
-    float r = 0.0f, T = 1.0f, C[3] = {0, 0, 0};
+    float r = 0.0f, T = 1.0f, C[3] = {0, 0, 0}, Dp = 0.0f;
     int n_eval = 0;
     unsigned st_samples = 0, st_levels = 0, st_steps = 0, st_rays = 0;
 
@@ -183,6 +184,7 @@ render_simt_kernel(const FieldView f, const RaySource src, const RenderOut out,
                         ray = slot;
                         n_eval = 0;
                         T = 1.0f;
+                        Dp = 0.0f;
                         C[0] = C[1] = C[2] = 0.0f;
                     }
                 }
@@ -192,7 +194,7 @@ render_simt_kernel(const FieldView f, const RaySource src, const RenderOut out,
                 if (mres == MARCH_SAMPLE) {
                     have = true;
                 } else if (mres == MARCH_END) {
-                    finish_ray(out, pix, C, T, n_eval);
+                    finish_ray(out, pix, C, T, n_eval, Dp);
                     ray = -1;
                     ++st_rays;
                 }
@@ -214,11 +216,12 @@ render_simt_kernel(const FieldView f, const RaySource src, const RenderOut out,
             C[0] += w * rgb[0];
             C[1] += w * rgb[1];
             C[2] += w * rgb[2];
+            Dp += w * t;
             T *= expf(-sd);
             ++n_eval;
             ++mr.step;
             if (T < f.T_eps) {
-                finish_ray(out, pix, C, T, n_eval);
+                finish_ray(out, pix, C, T, n_eval, Dp);
                 ray = -1;
                 ++st_rays;
             }

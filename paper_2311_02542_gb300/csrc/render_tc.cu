@@ -24,7 +24,7 @@
 namespace vrn {
 
 __device__ __forceinline__ void finish_ray_tc(const RenderOut &out, long long pix, const float C[3],
-                                              float T, int n) {
+                                           float T, int n, float depth) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         out.lin[3 * pix + c] = pq_to_linear(C[c]);
@@ -32,6 +32,7 @@ __device__ __forceinline__ void finish_ray_tc(const RenderOut &out, long long pi
     }
     if (out.T) out.T[pix] = T;
     if (out.n) out.n[pix] = n;
+    if (out.depth) out.depth[pix] = depth;
 }
 
 template <int L, int FMT>
@@ -50,7 +51,7 @@ render_tc_kernel(const FieldView f, const RaySource src, const RenderOut out,
     long long ray = -1, pix = 0;
     bool exhausted = false, ok = true;
     MarchRay mr;
-    float r = 0.0f, T = 1.0f, C[3] = {0, 0, 0};
+    float r = 0.0f, T = 1.0f, C[3] = {0, 0, 0}, Dp = 0.0f;
     int n_eval = 0;
     uint32_t phase = 0;
     unsigned st_samples = 0, st_levels = 0, st_steps = 0, st_rays = 0;
@@ -76,6 +77,7 @@ render_tc_kernel(const FieldView f, const RaySource src, const RenderOut out,
                         ray = slot;
                         n_eval = 0;
                         T = 1.0f;
+                        Dp = 0.0f;
                         C[0] = C[1] = C[2] = 0.0f;
                     }
                 }
@@ -85,7 +87,7 @@ render_tc_kernel(const FieldView f, const RaySource src, const RenderOut out,
                 if (mres == MARCH_SAMPLE) {
                     have = true;
                 } else if (mres == MARCH_END) {
-                    finish_ray_tc(out, pix, C, T, n_eval);
+                    finish_ray_tc(out, pix, C, T, n_eval, Dp);
                     ray = -1;
                     ++st_rays;
                 }
@@ -114,11 +116,12 @@ render_tc_kernel(const FieldView f, const RaySource src, const RenderOut out,
             C[0] += w * rgb[0];
             C[1] += w * rgb[1];
             C[2] += w * rgb[2];
+            Dp += w * t;
             T *= expf(-sd);
             ++n_eval;
             ++mr.step;
             if (T < f.T_eps) {
-                finish_ray_tc(out, pix, C, T, n_eval);
+                finish_ray_tc(out, pix, C, T, n_eval, Dp);
                 ray = -1;
                 ++st_rays;
             }

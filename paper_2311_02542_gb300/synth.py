@@ -137,6 +137,15 @@ def cfg_room(surface: bool = False) -> FieldConfig:
                        t_far=diag, density_bias=(math.log(100.0) if surface else 0.0))
 
 
+def cfg_room_paper_grid(surface: bool = False) -> FieldConfig:
+    """The room with the hash grid of the paper's experiments (Sec. 6): L=16
+    levels of F=2 features, base resolution 128, growth 1.4 (every level
+    hashed), here with T=2^19 slots per level and fp16 features."""
+    c = cfg_room(surface)
+    c.base_res, c.growth, c.log2_T = 128.0, 1.4, 19
+    return c
+
+
 # ----------------------------------------------------------------------------
 # Parameter blob
 # ----------------------------------------------------------------------------
@@ -431,6 +440,9 @@ def make_scene(name: str, seed: int | None = None, with_params: bool = True) -> 
         occ = occupancy_spheres(cfg.occ_res, 0.10, s)
     elif name in ("room", "room_surface"):
         cfg, s = cfg_room(surface=(name == "room_surface")), 2 if seed is None else seed
+        occ = occupancy_room(cfg.occ_res, cfg.aabb_max, 0.05, s)
+    elif name == "room_paper_grid":
+        cfg, s = cfg_room_paper_grid(), 2 if seed is None else seed
         occ = occupancy_room(cfg.occ_res, cfg.aabb_max, 0.05, s)
     else:
         raise ValueError(name)

@@ -45,7 +45,7 @@ class FieldDesc(ctypes.Structure):
 class RenderOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("out_pq", ctypes.c_void_p), ("out_T", ctypes.c_void_p), ("out_n", ctypes.c_void_p),
-                ("stats", ctypes.c_void_p)]
+                ("stats", ctypes.c_void_p), ("out_depth", ctypes.c_void_p)]
 
 
 _VP = ctypes.c_void_p
@@ -244,8 +244,9 @@ def vrnerf_field_set_occupancy(field: Field, occ_bits):
     _check(load().vrnerf_field_set_occupancy(field.h, _ptr(o)))
 
 
-def _opts(precision, out_pq=None, out_T=None, out_n=None, stats=None):
+def _opts(precision, out_pq=None, out_T=None, out_n=None, stats=None, out_depth=None):
     o = RenderOpts()
+    o.out_depth = None if out_depth is None else _dev(out_depth).data_ptr()
     o.stats = None if stats is None else _dev(stats, torch.int64).data_ptr()
     o.precision = PRECISIONS.get(precision, precision) if isinstance(precision, str) else int(precision)
     o.out_pq = None if out_pq is None else _dev(out_pq).data_ptr()
@@ -255,14 +256,14 @@ def _opts(precision, out_pq=None, out_T=None, out_n=None, stats=None):
 
 
 def vrnerf_render(field: Field, cameras, intrinsics, resolution, out=None, precision=FP32,
-                  out_pq=None, out_T=None, out_n=None, stats=None, stream=None):
+                  out_pq=None, out_T=None, out_n=None, stats=None, out_depth=None, stream=None):
     """cameras [n][3][4], intrinsics [n][4]: float32 CUDA tensors; resolution
     [n][2] (W, H) on the host. Returns out [sum W*H][3] linear colour."""
     res = np.ascontiguousarray(resolution, dtype=np.int32).reshape(-1, 2)
     rays = int((res[:, 0].astype(np.int64) * res[:, 1]).sum())
     if out is None:
         out = torch.empty((rays, 3), device=cameras.device, dtype=torch.float32)
-    o = _opts(precision, out_pq, out_T, out_n, stats)
+    o = _opts(precision, out_pq, out_T, out_n, stats, out_depth)
     _check(load().vrnerf_render(field.h, _ptr(_dev(cameras)), _ptr(_dev(intrinsics)), _ptr(res),
                                 res.shape[0], _ptr(_dev(out)), ctypes.byref(o), _stream(stream)))
     return out
@@ -284,11 +285,11 @@ def vrnerf_render_host(field: Field, cameras, intrinsics, resolution, out=None, 
 
 
 def vrnerf_render_rays(field: Field, rays_o, rays_d, radii, out=None, precision=FP32, out_pq=None,
-                       out_T=None, out_n=None, stats=None, stream=None):
+                       out_T=None, out_n=None, stats=None, out_depth=None, stream=None):
     B = rays_o.shape[0]
     if out is None:
         out = torch.empty((B, 3), device=rays_o.device, dtype=torch.float32)
-    o = _opts(precision, out_pq, out_T, out_n, stats)
+    o = _opts(precision, out_pq, out_T, out_n, stats, out_depth)
     _check(load().vrnerf_render_rays(field.h, _ptr(_dev(rays_o)), _ptr(_dev(rays_d)),
                                      _ptr(_dev(radii)), B, _ptr(_dev(out)), ctypes.byref(o),
                                      _stream(stream)))

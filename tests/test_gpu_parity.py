@@ -281,3 +281,24 @@ def test_invalid_arguments_are_rejected(V, cube):
     with pytest.raises(V.VrnerfError):
         V.vrnerf_render(f, _cuda(c2w), _cuda(K), res, precision=9)
     f.close()
+
+
+@pytest.mark.parametrize("prec,rtol", [("fp32", 1e-4), ("fp16", 2e-3)])
+def test_render_depth_parity(V, cube, room, prec, rtol):
+    """Expected depth sum_i w_i t_i (the paper's depth maps) against the oracle."""
+    cases = [(cube, S.cfg_unit_cube(), S.camera_unit_cube(cube.occ, cube.cfg, 1, 48, 40))]
+    cfg_s = S.cfg_room(surface=True)
+    c2w, K, _ = S.camera_room(room.occ, cfg_s, 2, 2048, 2048)
+    cases.append((room, cfg_s, (c2w, S.crop_camera(K, 700, 900), np.array([[96, 72]], np.int32))))
+    for sc, cfg, (c2w, K, res) in cases:
+        f = V.Field(cfg, sc.grid, sc.mlp, sc.occ_bits)
+        ref = O.Field(cfg, sc.grid, sc.mlp, sc.occ_bits).render(c2w, K, res)
+        rays = int(res[0, 0] * res[0, 1])
+        dep = torch.empty(rays, device="cuda")
+        n = torch.empty(rays, device="cuda", dtype=torch.int32)
+        V.vrnerf_render(f, _cuda(c2w), _cuda(K), res, precision=prec, out_depth=dep, out_n=n)
+        dep, n = dep.cpu().numpy(), n.cpu().numpy()
+        same = n == ref["n"]
+        assert same.mean() > 0.99 and ref["depth"].max() > 0
+        assert np.all(np.abs(dep[same] - ref["depth"][same]) <= rtol * np.abs(ref["depth"][same]) + 1e-6)
+        f.close()

@@ -484,3 +484,35 @@ def test_adam_closed_form():
     vv = 0.99 * 0.01 * g1 ** 2 + 0.01 * g2 ** 2
     want2 = want1 - lr * (mm / (1 - 0.81)) / (np.sqrt(vv / (1 - 0.9801)) + eps)
     np.testing.assert_allclose(p, want2, rtol=0, atol=1e-14)
+
+
+def test_depth_opaque_first_sample_and_bounds():
+    """Expected depth sum_i w_i t_i: a sample that absorbs (all but e^-200 of)
+    the light puts the depth at its own distance; in general the depth lies
+    between (1 - T) t_first and (1 - T) t_last of the composited samples."""
+    cfg = replace(S.cfg_unit_cube(), T_eps=0.0)
+    mlp = np.zeros(O.mlp_count(cfg))
+    W1, W2, *_ = _mlp_views(cfg, mlp)
+    a = 0.02
+    W1[0, 0] = 1.0
+    W2[0, 0] = math.log(1e7) / a  # sigma = 1e7 per unit: one sample is opaque
+    occ = np.zeros((64, 64, 64), bool)
+    occ[:, :, 40:] = True         # slab x >= 40/64
+    F = _const_field(cfg, a, mlp, occ)
+    o = np.array([[0.1, 0.5, 0.5]], np.float32)
+    d = np.array([[1.0, 0.0, 0.0]], np.float32)
+    out = F.render_rays(o, d, np.zeros(1, np.float32), threads=1)
+    rec_i, _, cnt = F.march(o, d, 64)
+    t = O.sample_table(cfg).astype(np.float64)
+    assert out["depth"][0] == pytest.approx(t[rec_i[0, 0]], rel=1e-12)
+    sc = S.make_scene("unit_cube")
+    cfg2 = replace(sc.cfg, density_bias=3.0)
+    F2 = O.Field(cfg2, sc.grid, sc.mlp, sc.occ_bits)
+    c2w, K, res = S.camera_unit_cube(sc.occ, cfg2, 1, 24, 24)
+    o, dd, r = O.camera_rays(cfg2, c2w, K, res)
+    out = F2.render_rays(o, dd, r)
+    rec_i, _, cnt = F2.march(o, dd, 64)
+    for k in np.nonzero(out["n"] > 1)[0][:200]:
+        ti = t[rec_i[k, :out["n"][k]]]
+        op = 1.0 - out["T"][k]
+        assert op * ti[0] - 1e-12 <= out["depth"][k] <= op * ti[-1] + 1e-12

@@ -22,6 +22,9 @@ Parity status per function (what pins it, see tests/test_oracle_*.py):
   march                   brute-force occupancy visits on tiny grids
   backward                central finite differences in fp64
   adam                    closed-form first and second steps
+  prune / history         thresholds 0 and > 1, monotone in the threshold, constant-density
+                          opacity against a brute-force nearest-camera spacing; history
+                          against the march's own visit records
 Parity unpinned: the appearance of a random field (nothing in the paper fixes it).
 """
 from __future__ import annotations
@@ -132,6 +135,10 @@ def lib():
                                     ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_double]),
                 "orc_geometry": (None, [_DP, _I32, _I32, _F32, _F32]),
+                "orc_prune": (None, [_DP, _F64, _F64, _U32, _F32, ctypes.c_int32, ctypes.c_int32,
+                                     ctypes.c_double, _F32, ctypes.POINTER(ctypes.c_uint8), _F64]),
+                "orc_history": (None, [_DP, _F64, _F64, _U32, _F32, _F32, _F32, ctypes.c_int32,
+                                       _F32]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -320,6 +327,35 @@ class Field:
                                   _p(r, ctypes.c_float), _p(tgt, ctypes.c_float), B,
                                   _p(gg, ctypes.c_double), _p(gm, ctypes.c_double))
         return loss, gg, gm
+
+
+def prune(F, cams, k, threshold, hist=None):
+    """Joint grid / history pruning of F's occupancy (Sec. 4.3.2); returns
+    (keep [rz][ry][rx] bool, alpha_grid [rz][ry][rx])."""
+    cfg = F.cfg
+    nvox = cfg.occ_res[0] * cfg.occ_res[1] * cfg.occ_res[2]
+    keep = np.zeros(nvox, np.uint8)
+    alpha = np.zeros(nvox, np.float64)
+    cams = _f32(cams).reshape(-1, 3)
+    h = None if hist is None else _f32(hist).reshape(-1)
+    lib().orc_prune(ctypes.byref(F.d), _p(F.grid, ctypes.c_double), _p(F.mlp, ctypes.c_double),
+                    _p(F.occ, ctypes.c_uint32), _p(cams, ctypes.c_float), cams.shape[0], int(k),
+                    float(threshold), _p(h, ctypes.c_float), _p(keep, ctypes.c_uint8),
+                    _p(alpha, ctypes.c_double))
+    shape = tuple(cfg.occ_res[::-1])
+    return keep.reshape(shape).astype(bool), alpha.reshape(shape)
+
+
+def history(F, o, dd, r, hist=None):
+    """Largest composited-sample opacity per voxel for explicit rays."""
+    cfg = F.cfg
+    nvox = cfg.occ_res[0] * cfg.occ_res[1] * cfg.occ_res[2]
+    h = np.zeros(nvox, np.float32) if hist is None else _f32(hist).reshape(-1).copy()
+    o, dd, r = _f32(o).reshape(-1, 3), _f32(dd).reshape(-1, 3), _f32(r).reshape(-1)
+    lib().orc_history(ctypes.byref(F.d), _p(F.grid, ctypes.c_double), _p(F.mlp, ctypes.c_double),
+                      _p(F.occ, ctypes.c_uint32), _p(o, ctypes.c_float), _p(dd, ctypes.c_float),
+                      _p(r, ctypes.c_float), o.shape[0], _p(h, ctypes.c_float))
+    return h
 
 
 def adam(param, grad, m, v, t, lr, beta1=0.9, beta2=0.99, eps=1e-15):

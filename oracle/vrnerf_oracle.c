@@ -712,6 +712,119 @@ void orc_adam(double *param, const double *grad, double *m, double *v, int64_t n
     }
 }
 
+/* ------------------------------------------------------------------------
+ * Occupancy-grid pruning (Sec. 4.3.2), joint history and grid pruning.
+ *
+ * Grid part: for every occupied voxel, the maximum density over a k x k x k
+ * lattice of points inside it (cell centres of the voxel's k^3 sub-cells;
+ * full detail: footprint 0), turned into an opacity with the smallest step a
+ * training ray can take there -- the sample spacing at the distance from the
+ * nearest camera centre to the voxel (the spacing grows with distance):
+ *     alpha_grid = 1 - exp(-sigma_max * delta_min).
+ * History part: hist[v], the largest opacity 1 - exp(-sigma delta) of any
+ * sample composited in v during training (NULL: none recorded).
+ * A voxel stays occupied iff it was occupied and alpha_grid >= threshold or
+ * hist >= threshold. keep_out [voxels] (0/1), alpha_out [voxels] (may be NULL).
+ * --------------------------------------------------------------------- */
+static double box_distance(const double *c, const double *lo, const double *hi)
+{
+    double s = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        double d = 0.0;
+        if (c[k] < lo[k]) d = lo[k] - c[k];
+        else if (c[k] > hi[k]) d = c[k] - hi[k];
+        s += d * d;
+    }
+    return sqrt(s);
+}
+
+void orc_prune(const orc_desc *D, const double *grid, const double *mlp, const uint32_t *occ,
+               const float *cams, int32_t n_cams, int32_t k, double threshold, const float *hist,
+               uint8_t *keep_out, double *alpha_out)
+{
+    orc_geom g;
+    geom_init(D, &g);
+    float *t_tab = (float *)malloc(sizeof(float) * (D->max_steps + 1));
+    orc_sample_table(D, t_tab);
+    const int32_t rx = D->occ_res[0], ry = D->occ_res[1], rz = D->occ_res[2];
+    double cell[3];
+    for (int a = 0; a < 3; ++a) cell[a] = ((double)D->aabb_max[a] - (double)D->aabb_min[a]) / D->occ_res[a];
+    for (int32_t vz = 0; vz < rz; ++vz)
+        for (int32_t vy = 0; vy < ry; ++vy)
+            for (int32_t vx = 0; vx < rx; ++vx) {
+                const int32_t v = vx + rx * (vy + ry * vz);
+                if (alpha_out) alpha_out[v] = 0.0;
+                if (!occupied(occ, v)) {
+                    keep_out[v] = 0;
+                    continue;
+                }
+                const int32_t vv[3] = {vx, vy, vz};
+                double lo[3], hi[3];
+                for (int a = 0; a < 3; ++a) {
+                    lo[a] = D->aabb_min[a] + vv[a] * cell[a];
+                    hi[a] = lo[a] + cell[a];
+                }
+                double sig_max = 0.0;
+                for (int32_t i = 0; i < k * k * k; ++i) {
+                    const int32_t j[3] = {i % k, (i / k) % k, i / (k * k)};
+                    float p[3];
+                    for (int a = 0; a < 3; ++a) p[a] = (float)(lo[a] + (j[a] + 0.5) / k * cell[a]);
+                    orc_sample s;
+                    sample_feats(D, &g, grid, p, 0.0, &s);
+                    const double dir[3] = {0.0, 0.0, 1.0};
+                    mlp_forward(D, mlp, dir, &s);
+                    if (s.sigma > sig_max) sig_max = s.sigma;
+                }
+                double dmin = INFINITY;
+                for (int32_t c = 0; c < n_cams; ++c) {
+                    const double cc[3] = {cams[3 * c], cams[3 * c + 1], cams[3 * c + 2]};
+                    const double dd = box_distance(cc, lo, hi);
+                    if (dd < dmin) dmin = dd;
+                }
+                /* spacing of the sample interval holding distance dmin */
+                int32_t i = 0;
+                while (i + 1 < D->max_steps && (double)t_tab[i + 1] <= dmin) ++i;
+                const double delta = (double)t_tab[i + 1] - (double)t_tab[i];
+                const double alpha = 1.0 - exp(-sig_max * delta);
+                if (alpha_out) alpha_out[v] = alpha;
+                keep_out[v] = (alpha >= threshold || (hist && (double)hist[v] >= threshold)) ? 1 : 0;
+            }
+    free(t_tab);
+}
+
+/* Training history (Sec. 4.3.2): for explicit rays, the largest opacity
+ * 1 - exp(-sigma delta) of any composited sample, per voxel; hist [voxels]
+ * is raised, not reset. */
+void orc_history(const orc_desc *D, const double *grid, const double *mlp, const uint32_t *occ,
+                 const float *o, const float *d, const float *r, int32_t B, float *hist)
+{
+    orc_geom g;
+    geom_init(D, &g);
+    float *t_tab = (float *)malloc(sizeof(float) * (D->max_steps + 1));
+    orc_sample_table(D, t_tab);
+    orc_tape *tape = (orc_tape *)malloc(sizeof(orc_tape) * D->max_steps);
+    for (int32_t b = 0; b < B; ++b) {
+        orc_ray_out ro;
+        render_one(D, &g, grid, mlp, occ, t_tab, o + 3 * b, d + 3 * b, (double)r[b], &ro, tape);
+        for (int32_t k = 0; k < ro.n_eval; ++k) {
+            const float *p = tape[k].p;
+            /* voxel of the composited sample */
+            int32_t v[3], vox, ok = 1;
+            for (int a = 0; a < 3; ++a) {
+                float gk = (p[a] - g.mn[a]) * g.inv_cell[a];
+                if (!(gk >= 0.0f) || !(gk < (float)D->occ_res[a])) ok = 0;
+                v[a] = (int32_t)floorf(gk);
+            }
+            if (!ok) continue;
+            vox = v[0] + D->occ_res[0] * (v[1] + D->occ_res[1] * v[2]);
+            const float a = (float)tape[k].alpha;
+            if (a > hist[vox]) hist[vox] = a;
+        }
+    }
+    free(tape);
+    free(t_tab);
+}
+
 /* Introspection for the tests. */
 void orc_geometry(const orc_desc *D, int32_t *N, int32_t *dense, float *inv_cell, float *inv_ext)
 {

@@ -516,3 +516,85 @@ def test_depth_opaque_first_sample_and_bounds():
         ti = t[rec_i[k, :out["n"][k]]]
         op = 1.0 - out["T"][k]
         assert op * ti[0] - 1e-12 <= out["depth"][k] <= op * ti[-1] + 1e-12
+
+
+# ----------------------------------------------------------------------------
+# Occupancy pruning (Sec. 4.3.2)
+# ----------------------------------------------------------------------------
+def _small_field(seed=3):
+    cfg = replace(S.cfg_unit_cube(), occ_res=(16, 16, 16), levels=8)
+    rng = np.random.default_rng(seed)
+    occ = rng.uniform(size=(16, 16, 16)) < 0.3
+    grid = rng.uniform(-1, 1, (cfg.levels, cfg.T, cfg.feats))
+    mlp = rng.normal(size=O.mlp_count(cfg)) * 0.5
+    return cfg, occ, O.Field(cfg, grid, mlp, S.pack_bits(occ))
+
+
+def test_prune_threshold_limits_and_monotone():
+    cfg, occ, F = _small_field()
+    cams = np.array([[0.5, 0.5, 0.5], [0.1, 0.9, 0.2]], np.float32)
+    keep0, alpha = O.prune(F, cams, 2, 0.0)
+    assert (keep0 == occ).all()
+    keep_hi, _ = O.prune(F, cams, 2, 1.5)
+    assert not keep_hi.any()
+    prev = occ.sum()
+    for thr in np.quantile(alpha[occ], [0.1, 0.3, 0.5, 0.7, 0.9]):
+        keep, _ = O.prune(F, cams, 2, thr)
+        assert keep.sum() <= prev and not (keep & ~occ).any()
+        assert (keep == (occ & (alpha >= thr))).all()
+        prev = keep.sum()
+    # history keeps a voxel the grid part would prune
+    thr = np.quantile(alpha[occ], 0.9)
+    keep, _ = O.prune(F, cams, 2, thr)
+    v = np.argwhere(occ & ~keep)[0]
+    hist = np.zeros(occ.shape, np.float32)
+    hist[tuple(v)] = 1.0
+    keep_h, _ = O.prune(F, cams, 2, thr, hist)
+    assert keep_h[tuple(v)] and keep_h.sum() == keep.sum() + 1
+
+
+def test_prune_constant_density_brute_force():
+    """All-zero parameters: sigma = exp(density_bias) everywhere, so the grid
+    opacity is 1 - exp(-sigma delta(t_min)), t_min the distance from the
+    nearest camera to the voxel box and delta the spacing of the sample
+    interval holding it (found here by brute force)."""
+    cfg = replace(S.cfg_unit_cube(), occ_res=(8, 8, 8), levels=8, density_bias=2.0)
+    occ = np.ones((8, 8, 8), bool)
+    F = O.Field(cfg, np.zeros((cfg.levels, cfg.T, 2)), np.zeros(O.mlp_count(cfg)), S.pack_bits(occ))
+    cams = np.array([[0.3, 0.6, 0.45]], np.float32)
+    _, alpha = O.prune(F, cams, 3, 0.0)
+    t = O.sample_table(cfg).astype(np.float64)
+    sig = np.exp(2.0)
+    for vz in range(8):
+        for vy in range(8):
+            for vx in range(8):
+                lo = np.array([vx, vy, vz]) / 8.0
+                hi = lo + 1 / 8.0
+                c = cams[0].astype(np.float64)
+                dist = np.linalg.norm(np.maximum(0, np.maximum(lo - c, c - hi)))
+                i = max(0, min(int(np.searchsorted(t, dist, side="right")) - 1, cfg.max_steps - 1))
+                want = 1 - np.exp(-sig * (t[i + 1] - t[i]))
+                assert alpha[vz, vy, vx] == pytest.approx(want, rel=1e-12)
+
+
+def test_history_matches_march_records():
+    """Constant density: every composited sample's opacity is
+    1 - exp(-sigma delta_i), so each voxel's history is the largest of those
+    over the samples the march records in it."""
+    cfg = replace(S.cfg_unit_cube(), occ_res=(16, 16, 16), density_bias=0.5, T_eps=0.0)
+    rng = np.random.default_rng(4)
+    occ = rng.uniform(size=(16, 16, 16)) < 0.3
+    F = O.Field(cfg, np.zeros((cfg.levels, cfg.T, 2)), np.zeros(O.mlp_count(cfg)), S.pack_bits(occ))
+    o = rng.uniform(0.2, 0.8, (50, 3)).astype(np.float32)
+    d = rng.normal(size=(50, 3))
+    d = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
+    r = np.zeros(50, np.float32)
+    h = O.history(F, o, d, r)
+    rec_i, rec_v, cnt = F.march(o, d, 64)
+    t = O.sample_table(cfg).astype(np.float64)
+    want = np.zeros(16 ** 3)
+    for b in range(50):
+        for k in range(cnt[b]):
+            i, v = rec_i[b, k], rec_v[b, k]
+            want[v] = max(want[v], 1 - np.exp(-np.exp(0.5) * (t[i + 1] - t[i])))
+    np.testing.assert_allclose(h, want.astype(np.float32), rtol=1e-6, atol=0)

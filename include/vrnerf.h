@@ -214,6 +214,28 @@ int vrnerf_backward(vrnerf_field *field, const float *rays_o, const float *rays_
                     const float *radii, const float *target_linear, int32_t B, float *loss_host,
                     void *stream);
 
+/* Occupancy-grid pruning (Sec. 4.3.2). vrnerf_history_reset allocates (on
+ * the first call) and zeroes the field's training history: from then on
+ * every vrnerf_backward records, per occupancy voxel, the largest opacity
+ * 1 - exp(-sigma delta) of the samples it composites there.
+ * vrnerf_field_get_history copies it to hist_host [voxels] (synchronous). */
+int vrnerf_history_reset(vrnerf_field *field);
+int vrnerf_field_get_history(vrnerf_field *field, float *hist_host);
+
+/* Joint history- and grid-based pruning (Sec. 4.3.2). For every occupied
+ * voxel: the largest density over the points_per_axis^3 sub-cell centres
+ * (full detail), as an opacity with the smallest sample spacing a training
+ * ray has there (the exponential spacing at the distance from the nearest of
+ * the n_cameras camera centres, host [n][3], to the voxel). A voxel stays
+ * occupied iff that opacity or its recorded history reaches `threshold`
+ * (the paper anneals it from 0 to 0.2). Optional outputs, device memory:
+ * alpha_out [voxels] the grid opacity, occ_bits_out the new bits; kept_host
+ * the number of voxels kept. apply != 0 replaces the field's occupancy and
+ * rebuilds its distance field. Synchronous. EINVAL, ENOMEM, ECUDA. */
+int vrnerf_prune(vrnerf_field *field, const float *camera_centres_host, int32_t n_cameras,
+                 int32_t points_per_axis, float threshold, int32_t apply, float *alpha_out,
+                 uint32_t *occ_bits_out, uint64_t *kept_host);
+
 /* Copies the gradient buffers of the last vrnerf_backward to the host:
  * grid_grad_host [L][T][F] fp32, mlp_grad_host fp32 (either may be NULL).
  * Synchronous. */

@@ -179,7 +179,7 @@ using namespace vrn;
 void vrnerf_field::release() {
     release_train_scratch(this);
     void *ptrs[] = {grid,     mlp,      occ,         t_tab,  counter, tc_w,   grid_grad, mlp_grad,
-                    grid_master, m_grid, v_grid, m_mlp, v_mlp, loss_acc, stage_cam, stage_out, dist};
+                    grid_master, m_grid, v_grid, m_mlp, v_mlp, loss_acc, stage_cam, stage_out, dist, hist};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     grid = nullptr;
@@ -188,6 +188,7 @@ void vrnerf_field::release() {
     t_tab = nullptr;
     counter = nullptr;
     dist = nullptr;
+    hist = nullptr;
     tc_w = nullptr;
     grid_grad = mlp_grad = grid_master = m_grid = v_grid = m_mlp = v_mlp = loss_acc = nullptr;
     stage_cam = stage_out = nullptr;

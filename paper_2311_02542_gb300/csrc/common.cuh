@@ -67,6 +67,7 @@ struct RenderOut {
     int *n;       // optional
     unsigned long long *stats;  // optional [4]: samples, levels fetched, steps tested, rays
     float *depth;               // optional: sum_i w_i t_i
+    float *hist;                // optional per-voxel max opacity of composited samples
 };
 
 // Warp-aggregated add of per-thread counters into stats (all lanes call).
@@ -143,6 +144,7 @@ struct MarchRay {
     float o[3], d[3];
     float g0[3], inv_s[3];  // grid coordinate at t = 0 and 1 / (grid units per unit t)
     int step;
+    int vox;                // voxel of the sample last returned
 };
 
 __device__ __forceinline__ void march_init(const FieldView &f, MarchRay &m) {
@@ -180,12 +182,18 @@ __device__ __forceinline__ int march_next(const FieldView &f, const float *__res
         if (!sample_voxel(f, m.o, m.d, t, p, vox, v)) return MARCH_END;
         ++tested;
         if (!f.skip) {
-            if (occupied(f.occ, vox)) return MARCH_SAMPLE;
+            if (occupied(f.occ, vox)) {
+                m.vox = vox;
+                return MARCH_SAMPLE;
+            }
             ++m.step;
             continue;
         }
         const int dv = (int)__ldg(f.dist + vox);
-        if (dv == 0) return MARCH_SAMPLE;
+        if (dv == 0) {
+            m.vox = vox;
+            return MARCH_SAMPLE;
+        }
         float t_in = -INFINITY, t_out = INFINITY;
         bool ok = true;
 #pragma unroll

@@ -19,6 +19,7 @@ struct vrnerf_field {
     float *t_tab = nullptr;       // [S+1]
     void *counter = nullptr;      // ray-slot counter of the persistent kernels (scratch)
     uint8_t *dist = nullptr;      // occupancy distance field (one byte per voxel)
+    float *hist = nullptr;        // training history: max composited opacity per voxel
     // tensor-core weight images, rebuilt when the fp32 weights change
     void *tc_w = nullptr;
     size_t tc_w_bytes = 0;

@@ -1,0 +1,164 @@
+// prune.cu -- occupancy-grid pruning (Sec. 4.3.2): joint history- and
+// grid-based pruning, then the distance field is rebuilt.
+//
+// Grid part: one warp per voxel; its lanes evaluate the density at the k^3
+// sub-cell centres of the voxel (full detail: zero footprint, so every
+// level is fetched), the warp takes the maximum, and lane 0 turns it into an
+// opacity with the smallest step a training ray can take in the voxel: the
+// spacing of the exponential sample interval holding the distance from the
+// nearest camera centre to the voxel box. History part: the largest opacity
+// of any sample composited in the voxel during training (recorded by
+// vrnerf_backward once vrnerf_history_reset has been called). A voxel stays
+// occupied iff it was, and either opacity reaches the threshold.
+#include <cstring>
+
+#include "field.h"
+
+namespace vrn {
+
+cudaError_t launch_build_dist(const FieldView &f, uint8_t *dist, cudaStream_t st);
+
+template <int L>
+__global__ void __launch_bounds__(256)
+prune_kernel(const FieldView f, const float *__restrict__ cams, int n_cams, int k, float threshold,
+             const float *__restrict__ hist, float *__restrict__ alpha_out, uint32_t *__restrict__ occ_out,
+             unsigned long long *__restrict__ kept) {
+    constexpr int D = 2 * L;
+    const int lane = threadIdx.x & 31;
+    const long long nvox = (long long)f.res[0] * f.res[1] * f.res[2];
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    const float *W1 = f.mlp, *W2 = W1 + 64 * D;
+    unsigned int kept_here = 0;
+    for (long long v = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); v < nvox; v += warps) {
+        if (alpha_out && lane == 0) alpha_out[v] = 0.0f;
+        if (!occupied(f.occ, (int)v)) continue;
+        const int vx = (int)(v % f.res[0]), vy = (int)((v / f.res[0]) % f.res[1]),
+                  vz = (int)(v / ((long long)f.res[0] * f.res[1]));
+        const int vv[3] = {vx, vy, vz};
+        float lo[3], cell[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            cell[a] = 1.0f / f.inv_cell[a];
+            lo[a] = f.mn[a] + (float)vv[a] * cell[a];
+        }
+        float smax = 0.0f;
+        for (int i = lane; i < k * k * k; i += 32) {
+            const int j[3] = {i % k, (i / k) % k, i / (k * k)};
+            float p[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) p[a] = lo[a] + ((float)j[a] + 0.5f) / (float)k * cell[a];
+            float feat[D];
+            gather_features<L>(f, p, 0.0f, feat);
+            float o0 = 0.0f;
+            for (int jj = 0; jj < 64; ++jj) {
+                float a = 0.0f;
+#pragma unroll
+                for (int q = 0; q < D; ++q) a = fmaf(__ldg(W1 + jj * D + q), feat[q], a);
+                o0 = fmaf(__ldg(W2 + jj), fmaxf(a, 0.0f), o0);
+            }
+            smax = fmaxf(smax, expf(o0 + f.density_bias));
+        }
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) smax = fmaxf(smax, __shfl_xor_sync(0xffffffffu, smax, s));
+        if (lane == 0) {
+            float dmin = INFINITY;
+            for (int c = 0; c < n_cams; ++c) {
+                float s2 = 0.0f;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const float cc = cams[3 * c + a], l = lo[a], h = lo[a] + cell[a];
+                    const float dd = cc < l ? l - cc : (cc > h ? cc - h : 0.0f);
+                    s2 = fmaf(dd, dd, s2);
+                }
+                dmin = fminf(dmin, sqrtf(s2));
+            }
+            // interval [t_i, t_i+1) holding dmin (i clamped to [0, S-1])
+            int lo_i = 0, hi_i = f.S - 1;
+            while (lo_i < hi_i) {
+                const int mid = (lo_i + hi_i + 1) >> 1;
+                if (__ldg(f.t_tab + mid) <= dmin) lo_i = mid;
+                else hi_i = mid - 1;
+            }
+            const float delta = __ldg(f.t_tab + lo_i + 1) - __ldg(f.t_tab + lo_i);
+            const float alpha = -expm1f(-smax * delta);
+            if (alpha_out) alpha_out[v] = alpha;
+            if (alpha >= threshold || (hist && hist[v] >= threshold)) {
+                atomicOr(occ_out + (v >> 5), 1u << (v & 31));
+                ++kept_here;
+            }
+        }
+    }
+    if (lane == 0 && kept_here) atomicAdd(kept, (unsigned long long)kept_here);
+}
+
+}  // namespace vrn
+
+using namespace vrn;
+
+extern "C" {
+
+int vrnerf_history_reset(vrnerf_field *F) {
+    if (!F) return fail(VRNERF_EINVAL, "field is NULL");
+    const size_t n = (size_t)F->desc.occ_res[0] * F->desc.occ_res[1] * F->desc.occ_res[2];
+    cudaError_t e = cudaSuccess;
+    if (!F->hist && (e = cudaMalloc(&F->hist, n * sizeof(float))) != cudaSuccess)
+        return fail(VRNERF_ENOMEM, "history: %s", cudaGetErrorString(e));
+    if ((e = cudaMemset(F->hist, 0, n * sizeof(float))) != cudaSuccess) return cuda_fail(e, "history_reset");
+    return VRNERF_OK;
+}
+
+int vrnerf_field_get_history(vrnerf_field *F, float *hist_host) {
+    if (!F || !hist_host) return fail(VRNERF_EINVAL, "NULL argument");
+    if (!F->hist) return fail(VRNERF_EINVAL, "no history: call vrnerf_history_reset first");
+    const size_t n = (size_t)F->desc.occ_res[0] * F->desc.occ_res[1] * F->desc.occ_res[2];
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(hist_host, F->hist, n * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "get_history");
+    return VRNERF_OK;
+}
+
+int vrnerf_prune(vrnerf_field *F, const float *camera_centres_host, int32_t n_cameras, int32_t points_per_axis,
+                 float threshold, int32_t apply, float *alpha_out, uint32_t *occ_bits_out, uint64_t *kept_host) {
+    if (!F || !camera_centres_host) return fail(VRNERF_EINVAL, "NULL argument");
+    if (n_cameras < 1 || n_cameras > 65536) return fail(VRNERF_EINVAL, "n_cameras must be in [1, 65536]");
+    if (points_per_axis < 1 || points_per_axis > 16) return fail(VRNERF_EINVAL, "points_per_axis must be in [1, 16]");
+    if (!(threshold >= 0.0f)) return fail(VRNERF_EINVAL, "threshold must be >= 0");
+    const vrnerf_field_desc &d = F->desc;
+    const long long nvox = (long long)d.occ_res[0] * d.occ_res[1] * d.occ_res[2];
+    const size_t words = (size_t)((nvox + 31) / 32);
+    float *cams = nullptr;
+    uint32_t *occ_new = nullptr;
+    unsigned long long *kept = nullptr;
+    cudaError_t e = cudaMalloc(&cams, sizeof(float) * 3 * n_cameras);
+    if (e == cudaSuccess) e = cudaMalloc(&occ_new, words * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&kept, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemcpy(cams, camera_centres_host, sizeof(float) * 3 * n_cameras, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(occ_new, 0, words * 4);
+    if (e == cudaSuccess) e = cudaMemset(kept, 0, sizeof(unsigned long long));
+    if (e == cudaSuccess) {
+        const int blocks = num_sms() * 8;
+        if (F->view.L == 8)
+            prune_kernel<8><<<blocks, 256>>>(F->view, cams, n_cameras, points_per_axis, threshold, F->hist,
+                                             alpha_out, occ_new, kept);
+        else
+            prune_kernel<16><<<blocks, 256>>>(F->view, cams, n_cameras, points_per_axis, threshold, F->hist,
+                                              alpha_out, occ_new, kept);
+        e = cudaGetLastError();
+    }
+    unsigned long long kept_h = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&kept_h, kept, sizeof kept_h, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && occ_bits_out) e = cudaMemcpy(occ_bits_out, occ_new, words * 4, cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess && apply) {
+        e = cudaMemcpy(F->occ, occ_new, words * 4, cudaMemcpyDeviceToDevice);
+        if (e == cudaSuccess) e = launch_build_dist(F->view, F->dist, 0);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    }
+    cudaFree(cams);
+    cudaFree(occ_new);
+    cudaFree(kept);
+    if (e != cudaSuccess) return cuda_fail(e, "prune");
+    if (kept_host) *kept_host = kept_h;
+    return VRNERF_OK;
+}
+
+}  // extern "C"

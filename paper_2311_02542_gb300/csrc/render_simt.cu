@@ -212,7 +212,9 @@ render_simt_kernel(const FieldView f, const RaySource src, const RenderOut out,
             float sigma, rgb[3];
             mlp_simt<D>(sW, feat, mr.d, f.density_bias, sigma, rgb);
             const float sd = sigma * delta;
-            const float w = T * (-expm1f(-sd));
+            const float alpha = -expm1f(-sd);
+            const float w = T * alpha;
+            if (out.hist) atomicMax(reinterpret_cast<int *>(out.hist) + mr.vox, __float_as_int(alpha));
             C[0] += w * rgb[0];
             C[1] += w * rgb[1];
             C[2] += w * rgb[2];

@@ -507,7 +507,7 @@ int vrnerf_backward(vrnerf_field *F, const float *rays_o, const float *rays_d, c
         src.r = radii;
         src.n_slots = B;
         // (the linear colour is not needed: it lands in gC, which the loss kernel fills next)
-        RenderOut ro{S.gC, S.C, nullptr, S.n, nullptr};
+        RenderOut ro{S.gC, S.C, nullptr, S.n, nullptr, nullptr, F->hist};
         if (e == cudaSuccess) e = cudaMemsetAsync(F->counter, 0, sizeof(unsigned long long), st);
         if (e == cudaSuccess)
             e = launch_render_simt(F->view, src, ro, reinterpret_cast<unsigned long long *>(F->counter), st);

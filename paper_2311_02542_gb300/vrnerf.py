@@ -61,6 +61,9 @@ _SIGS = {
     "vrnerf_debug_wait_timeout": (ctypes.c_int, [_VP, ctypes.c_uint32, _VP]),
     "vrnerf_field_set_occupancy": (ctypes.c_int, [_VP, _VP]),
     "vrnerf_field_save": (ctypes.c_int, [_VP, ctypes.c_char_p]),
+    "vrnerf_history_reset": (ctypes.c_int, [_VP]),
+    "vrnerf_field_get_history": (ctypes.c_int, [_VP, _VP]),
+    "vrnerf_prune": (ctypes.c_int, [_VP, _VP, _I32, _I32, _F, _I32, _VP, _VP, _VP]),
     "vrnerf_field_load": (ctypes.c_int, [ctypes.c_char_p, _VP]),
     "vrnerf_render": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP]),
     "vrnerf_render_host": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP]),
@@ -237,6 +240,32 @@ def vrnerf_field_load(path: str, cfg) -> Field:
     _check(load().vrnerf_field_load(os.fsencode(path), ctypes.byref(h)))
     f.cfg, f.h, f._desc, f.n_rays_last = cfg, h, desc(cfg), 0
     return f
+
+
+def vrnerf_history_reset(field: Field):
+    _check(load().vrnerf_history_reset(field.h))
+
+
+def vrnerf_field_get_history(field: Field):
+    cfg = field.cfg
+    h = np.empty(cfg.occ_res[0] * cfg.occ_res[1] * cfg.occ_res[2], np.float32)
+    _check(load().vrnerf_field_get_history(field.h, _ptr(h)))
+    return h
+
+
+def vrnerf_prune(field: Field, camera_centres, points_per_axis=4, threshold=0.2, apply=True,
+                 want_alpha=False):
+    """Returns (kept voxel count, alpha [voxels] or None, new occupancy bits)."""
+    cfg = field.cfg
+    cams = np.ascontiguousarray(camera_centres, np.float32).reshape(-1, 3)
+    nvox = cfg.occ_res[0] * cfg.occ_res[1] * cfg.occ_res[2]
+    alpha = torch.empty(nvox, device="cuda") if want_alpha else None
+    bits = torch.empty((nvox + 31) // 32, device="cuda", dtype=torch.int32)
+    kept = ctypes.c_uint64()
+    _check(load().vrnerf_prune(field.h, _ptr(cams), cams.shape[0], int(points_per_axis),
+                               float(threshold), int(bool(apply)), _ptr(alpha), _ptr(bits),
+                               ctypes.byref(kept)))
+    return kept.value, (alpha.cpu().numpy() if want_alpha else None), bits.cpu().numpy().view(np.uint32)
 
 
 def vrnerf_field_set_occupancy(field: Field, occ_bits):

@@ -85,7 +85,9 @@ typedef struct vrnerf_field vrnerf_field;
  * coordinates are (p - aabb_min) / max extent. The ray's base radius is
  * radius_scale / fx; L* = -log_growth(2 base_res r t / max extent) +
  * lod_bias (Eq. 3, Sec. 4.2.2). sigma = exp(o_0 + density_bias).
- * Compositing stops after the sample where transmittance < T_eps. */
+ * Compositing stops after the sample where transmittance < T_eps.
+ * occ_res: occupancy voxels per axis, each in [1, 2048], fewer than 2^31 in
+ * all (Sec. 4.3). */
 typedef struct {
     int32_t levels, feats, log2_T, feat_fp16;
     double base_res, growth;
@@ -235,6 +237,19 @@ int vrnerf_field_get_history(vrnerf_field *field, float *hist_host);
 int vrnerf_prune(vrnerf_field *field, const float *camera_centres_host, int32_t n_cameras,
                  int32_t points_per_axis, float threshold, int32_t apply, float *alpha_out,
                  uint32_t *occ_bits_out, uint64_t *kept_host);
+
+/* Refines the occupancy grid by an integer factor in [2, 8] per axis
+ * (Sec. 4.3.2: a coarse grid upsampled at training milestones): every child
+ * voxel takes its parent's bit and, if a history is kept, its history value;
+ * the field's occ_res is multiplied by factor and its distance field
+ * rebuilt. Synchronous; no render, training call or server may be using the
+ * field meanwhile. EINVAL (factor, resulting occ_res), ENOMEM, ECUDA; on an
+ * error the field is unchanged. */
+int vrnerf_occupancy_upsample(vrnerf_field *field, int32_t factor);
+
+/* Copies the field's occupancy bits (layout of vrnerf_field_create) to
+ * occ_bits_host [ceil(voxels / 32)] words. Synchronous. EINVAL, ECUDA. */
+int vrnerf_field_get_occupancy(vrnerf_field *field, uint32_t *occ_bits_host);
 
 /* Copies the gradient buffers of the last vrnerf_backward to the host:
  * grid_grad_host [L][T][F] fp32, mlp_grad_host fp32 (either may be NULL).

@@ -25,6 +25,7 @@ Parity status per function (what pins it, see tests/test_oracle_*.py):
   prune / history         thresholds 0 and > 1, monotone in the threshold, constant-density
                           opacity against a brute-force nearest-camera spacing; history
                           against the march's own visit records
+  upsample_occupancy      brute-force child-to-parent loop on a tiny grid
 Parity unpinned: the appearance of a random field (nothing in the paper fixes it).
 """
 from __future__ import annotations
@@ -344,6 +345,17 @@ def prune(F, cams, k, threshold, hist=None):
                     _p(alpha, ctypes.c_double))
     shape = tuple(cfg.occ_res[::-1])
     return keep.reshape(shape).astype(bool), alpha.reshape(shape)
+
+
+def upsample_occupancy(values, factor):
+    """Occupancy grid refined by an integer factor per axis (Sec. 4.3.2: the
+    coarse grid is upsampled at training milestones): the voxel (x, y, z) of
+    the fine grid takes the value of (x // factor, y // factor, z // factor).
+    values: [rz][ry][rx] bits or per-voxel history."""
+    v = np.asarray(values)
+    for axis in range(3):
+        v = np.repeat(v, factor, axis=axis)
+    return v
 
 
 def history(F, o, dd, r, hist=None):

@@ -61,6 +61,8 @@ int check_desc(const vrnerf_field_desc *d) {
         if (d->occ_res[k] < 1 || d->occ_res[k] > 2048)
             return fail(VRNERF_EINVAL, "occ_res must be in [1, 2048]");
     }
+    if ((long long)d->occ_res[0] * d->occ_res[1] * d->occ_res[2] > 0x7fffffffll)
+        return fail(VRNERF_EINVAL, "occupancy grid must hold fewer than 2^31 voxels");
     if (d->max_steps < 1 || d->max_steps > 8192) return fail(VRNERF_EINVAL, "max_steps must be in [1, 8192]");
     if (!(d->t_near > 0.0f) || !(d->t_far > d->t_near))
         return fail(VRNERF_EINVAL, "need 0 < t_near < t_far");

@@ -1,6 +1,7 @@
 // field.h -- the opaque vrnerf_field of the C ABI and the host-side helpers
 // that the translation units share.
 #pragma once
+#include <vector>
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
@@ -47,6 +48,9 @@ int fail(int code, const char *fmt, ...);
 int cuda_fail(cudaError_t e, const char *what);
 uint64_t grid_bytes(const vrnerf_field_desc &d);
 uint64_t grid_entries(const vrnerf_field_desc &d);
+uint64_t occ_words(const vrnerf_field_desc &d);
+int check_desc(const vrnerf_field_desc *d);
+void derive_view(const vrnerf_field_desc &d, FieldView &f, std::vector<float> &t_tab);
 void release_train_scratch(vrnerf_field *F);
 
 // render_tc.cu: tcgen05 tensor-core MLP path

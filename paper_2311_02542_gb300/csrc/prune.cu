@@ -11,6 +11,7 @@
 // vrnerf_backward once vrnerf_history_reset has been called). A voxel stays
 // occupied iff it was, and either opacity reaches the threshold.
 #include <cstring>
+#include <vector>
 
 #include "field.h"
 
@@ -91,6 +92,35 @@ prune_kernel(const FieldView f, const float *__restrict__ cams, int n_cams, int 
     if (lane == 0 && kept_here) atomicAdd(kept, (unsigned long long)kept_here);
 }
 
+// Nearest-neighbour refinement of the occupancy grid by an integer factor:
+// a child voxel takes its parent's bit (one thread per output word) and, when
+// a history is kept, its parent's history value.
+__global__ void upsample_bits_kernel(const uint32_t *__restrict__ occ, int3 r0, int fac, int3 r1, long long nvox1,
+                                     uint32_t *__restrict__ out) {
+    const long long words = (nvox1 + 31) / 32;
+    for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < words;
+         w += (long long)gridDim.x * blockDim.x) {
+        uint32_t word = 0;
+        for (int b = 0; b < 32; ++b) {
+            const long long v = w * 32 + b;
+            if (v >= nvox1) break;
+            const long long x = v % r1.x, y = (v / r1.x) % r1.y, z = v / ((long long)r1.x * r1.y);
+            const long long p = x / fac + r0.x * (y / fac + r0.y * (z / fac));
+            word |= ((__ldg(occ + (p >> 5)) >> (p & 31)) & 1u) << b;
+        }
+        out[w] = word;
+    }
+}
+
+__global__ void upsample_hist_kernel(const float *__restrict__ h0, int3 r0, int fac, int3 r1, long long nvox1,
+                                     float *__restrict__ h1) {
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox1;
+         v += (long long)gridDim.x * blockDim.x) {
+        const long long x = v % r1.x, y = (v / r1.x) % r1.y, z = v / ((long long)r1.x * r1.y);
+        h1[v] = __ldg(h0 + x / fac + r0.x * (y / fac + r0.y * (z / fac)));
+    }
+}
+
 }  // namespace vrn
 
 using namespace vrn;
@@ -158,6 +188,67 @@ int vrnerf_prune(vrnerf_field *F, const float *camera_centres_host, int32_t n_ca
     cudaFree(kept);
     if (e != cudaSuccess) return cuda_fail(e, "prune");
     if (kept_host) *kept_host = kept_h;
+    return VRNERF_OK;
+}
+
+int vrnerf_field_get_occupancy(vrnerf_field *F, uint32_t *occ_bits_host) {
+    if (!F || !occ_bits_host) return fail(VRNERF_EINVAL, "NULL argument");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(occ_bits_host, F->occ, occ_words(F->desc) * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "get_occupancy");
+    return VRNERF_OK;
+}
+
+int vrnerf_occupancy_upsample(vrnerf_field *F, int32_t factor) {
+    if (!F) return fail(VRNERF_EINVAL, "field is NULL");
+    if (factor < 2 || factor > 8) return fail(VRNERF_EINVAL, "factor must be in [2, 8]");
+    vrnerf_field_desc d = F->desc;
+    long long nvox1 = 1;
+    for (int k = 0; k < 3; ++k) {
+        d.occ_res[k] *= factor;
+        nvox1 *= d.occ_res[k];
+    }
+    int rc = check_desc(&d);
+    if (rc) return rc;
+    const int3 r0{F->desc.occ_res[0], F->desc.occ_res[1], F->desc.occ_res[2]};
+    const int3 r1{d.occ_res[0], d.occ_res[1], d.occ_res[2]};
+    uint32_t *occ1 = nullptr;
+    uint8_t *dist1 = nullptr;
+    float *hist1 = nullptr;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMalloc(&occ1, occ_words(d) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&dist1, (size_t)nvox1);
+    if (e == cudaSuccess && F->hist) e = cudaMalloc(&hist1, (size_t)nvox1 * sizeof(float));
+    if (e == cudaSuccess) {
+        const int blocks = num_sms() * 4;
+        upsample_bits_kernel<<<blocks, 256>>>(F->occ, r0, factor, r1, nvox1, occ1);
+        if (hist1) upsample_hist_kernel<<<blocks, 256>>>(F->hist, r0, factor, r1, nvox1, hist1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        cudaFree(occ1);
+        cudaFree(dist1);
+        cudaFree(hist1);
+        return cuda_fail(e, "occupancy_upsample");
+    }
+    cudaFree(F->occ);
+    cudaFree(F->dist);
+    cudaFree(F->hist);
+    F->occ = occ1;
+    F->dist = dist1;
+    F->hist = hist1;
+    F->desc = d;
+    std::vector<float> t_tab;
+    derive_view(d, F->view, t_tab);
+    F->view.grid = F->grid;
+    F->view.mlp = F->mlp;
+    F->view.occ = F->occ;
+    F->view.t_tab = F->t_tab;
+    F->view.dist = F->dist;
+    e = launch_build_dist(F->view, F->dist, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy_upsample: distance field");
     return VRNERF_OK;
 }
 

@@ -8,6 +8,7 @@ module loads ``_build/libvrnerf.so`` and raises if it has not been built
 from __future__ import annotations
 
 import ctypes
+from dataclasses import replace
 import os
 
 import numpy as np
@@ -62,6 +63,8 @@ _SIGS = {
     "vrnerf_field_set_occupancy": (ctypes.c_int, [_VP, _VP]),
     "vrnerf_field_save": (ctypes.c_int, [_VP, ctypes.c_char_p]),
     "vrnerf_history_reset": (ctypes.c_int, [_VP]),
+    "vrnerf_occupancy_upsample": (ctypes.c_int, [_VP, _I32]),
+    "vrnerf_field_get_occupancy": (ctypes.c_int, [_VP, _VP]),
     "vrnerf_field_get_history": (ctypes.c_int, [_VP, _VP]),
     "vrnerf_prune": (ctypes.c_int, [_VP, _VP, _I32, _I32, _F, _I32, _VP, _VP, _VP]),
     "vrnerf_field_load": (ctypes.c_int, [ctypes.c_char_p, _VP]),
@@ -266,6 +269,18 @@ def vrnerf_prune(field: Field, camera_centres, points_per_axis=4, threshold=0.2,
                                float(threshold), int(bool(apply)), _ptr(alpha), _ptr(bits),
                                ctypes.byref(kept)))
     return kept.value, (alpha.cpu().numpy() if want_alpha else None), bits.cpu().numpy().view(np.uint32)
+
+
+def vrnerf_occupancy_upsample(field: Field, factor=2):
+    _check(load().vrnerf_occupancy_upsample(field.h, int(factor)))
+    field.cfg = replace(field.cfg, occ_res=tuple(int(r) * int(factor) for r in field.cfg.occ_res))
+
+
+def vrnerf_field_get_occupancy(field: Field):
+    r = field.cfg.occ_res
+    bits = np.empty((r[0] * r[1] * r[2] + 31) // 32, np.uint32)
+    _check(load().vrnerf_field_get_occupancy(field.h, _ptr(bits)))
+    return bits
 
 
 def vrnerf_field_set_occupancy(field: Field, occ_bits):

@@ -158,3 +158,64 @@ def test_room_full_size_sampled_voxels(V):
     assert (np.abs(got - ref) <= RTOL * ref + ATOL).all(), np.abs(got - ref).max()
     assert (alpha.reshape(-1)[~sc.occ.reshape(-1)] == 0).all()
     f.close()
+
+
+def test_upsample_matches_oracle_and_renders(V):
+    cfg, occ, grid, mlp = _small(seed=7, T_eps=0.0)
+    f = V.Field(cfg, grid, mlp, S.pack_bits(occ))
+    V.vrnerf_history_reset(f)
+    c2w, K, res = S.camera_unit_cube(occ, cfg, 1, 16, 16)
+    o, d, r = O.camera_rays(cfg, c2w, K, res)
+    V.vrnerf_backward(f, _cuda(o), _cuda(d), _cuda(r), _cuda(np.full((o.shape[0], 3), 0.5)))
+    h0 = V.vrnerf_field_get_history(f).reshape(occ.shape)
+    assert (h0 > 0).any()
+    with pytest.raises(V.VrnerfError):
+        V.vrnerf_occupancy_upsample(f, 1)
+    V.vrnerf_occupancy_upsample(f, 2)
+    cfg2 = f.cfg
+    assert cfg2.occ_res == (32, 32, 32)
+    up = O.upsample_occupancy(occ, 2)
+    assert (V.vrnerf_field_get_occupancy(f) == S.pack_bits(up)).all()
+    assert (V.vrnerf_field_get_history(f) == O.upsample_occupancy(h0, 2).reshape(-1)).all()
+    F2 = O.Field(cfg2, grid, mlp, S.pack_bits(up))
+    c2w, K, res = S.camera_unit_cube(occ, cfg, 4, 40, 40)
+    o, d, r = O.camera_rays(cfg2, c2w, K, res)
+    ri, rv, cnt = F2.march(o, d, cfg2.max_steps)
+    gi, gv, gc = (t.cpu().numpy() for t in V.vrnerf_debug_march(f, _cuda(o), _cuda(d), cfg2.max_steps))
+    assert (gc == cnt).all() and (gi == ri).all() and (gv == rv).all()
+    ref = F2.render(c2w, K, res)
+    lin = V.vrnerf_render(f, _cuda(c2w), _cuda(K), res).cpu().numpy()
+    assert (np.abs(lin - ref["linear"]) <= RTOL * np.abs(ref["linear"]) + ATOL).all()
+    f.close()
+
+
+def test_pruning_schedule_during_training(V):
+    """The loop of Sec. 4.3.2 at small scale on the opaque room: history on,
+    train, prune every few steps with the threshold annealed towards 0.2,
+    upsample the grid once at a milestone, keep training."""
+    sc = S.make_scene("room_surface")
+    cfg = sc.cfg
+    f = V.Field(cfg, sc.grid, sc.mlp, sc.occ_bits)
+    poses, intr = S.training_views(sc.occ, cfg, n_views=16)
+    cams = poses[:, :3, 3].astype(np.float32)
+    V.vrnerf_history_reset(f)
+    count = int(sc.occ.sum())
+    losses = []
+    for it in range(12):
+        batch = [_cuda(a) for a in S.training_batch(poses, intr, 1 << 13, seed=5, step=it)]
+        losses.append(V.vrnerf_train_step(f, *batch))
+        if it % 3 == 2:
+            thr = 0.2 * (it + 1) / 12
+            kept, _, _ = V.vrnerf_prune(f, cams, 4, thr, apply=True)
+            assert 0 < kept <= count
+            count = kept
+            V.vrnerf_history_reset(f)
+        if it == 5:
+            V.vrnerf_occupancy_upsample(f, 2)
+            count *= 8
+            assert f.cfg.occ_res == (512, 512, 512)
+            occ = S.unpack_bits(V.vrnerf_field_get_occupancy(f), f.cfg.occ_res)
+            assert occ.sum() == count
+    assert np.isfinite(losses).all()
+    V.vrnerf_field_status(f)
+    f.close()

@@ -598,3 +598,14 @@ def test_history_matches_march_records():
             i, v = rec_i[b, k], rec_v[b, k]
             want[v] = max(want[v], 1 - np.exp(-np.exp(0.5) * (t[i + 1] - t[i])))
     np.testing.assert_allclose(h, want.astype(np.float32), rtol=1e-6, atol=0)
+
+
+def test_upsample_occupancy_brute_force():
+    rng = np.random.default_rng(2)
+    occ = rng.uniform(size=(2, 3, 4)) < 0.5
+    up = O.upsample_occupancy(occ, 3)
+    assert up.shape == (6, 9, 12)
+    for z in range(6):
+        for y in range(9):
+            for x in range(12):
+                assert up[z, y, x] == occ[z // 3, y // 3, x // 3]

@@ -26,6 +26,10 @@ Parity status per function (what pins it, see tests/test_oracle_*.py):
                           opacity against a brute-force nearest-camera spacing; history
                           against the march's own visit records
   upsample_occupancy      brute-force child-to-parent loop on a tiny grid
+  density_grad / normals  central differences of sigma in fp64; a field whose density
+                          grows along one axis gives normals -axis, composited to (1 - T)
+  tonemap                 sRGB anchors of IEC 61966-2-1 at PQ inputs of known luminance,
+                          exposure doubling, coverage from T
 Parity unpinned: the appearance of a random field (nothing in the paper fixes it).
 """
 from __future__ import annotations
@@ -122,8 +126,11 @@ def lib():
                 "orc_query": (None, [_DP, _F64, _F64, _F32, _F64, _F64, ctypes.c_int32, _F64,
                                      _F64, _F64]),
                 "orc_render_rays": (None, [_DP, _F64, _F64, _U32, _F32, _F32, _F32,
-                                           ctypes.c_int32, _F64, _F64, _F64, _I32, _F64,
+                                           ctypes.c_int32, _F64, _F64, _F64, _I32, _F64, _F64,
                                            ctypes.c_int32]),
+                "orc_density_grad": (None, [_DP, _F64, _F64, _F32, _F64, ctypes.c_int32, _F64,
+                                            _F64]),
+                "orc_tonemap": (None, [_F64, _F64, ctypes.c_int64, ctypes.c_double, _U32, _F64]),
                 "orc_render": (None, [_DP, _F64, _F64, _U32, _F32, _F32, _I32, ctypes.c_int32,
                                       _F64, _F64, _F64, _I32, _F64, ctypes.c_int32]),
                 "orc_camera_rays": (None, [_DP, _F32, _F32, _I32, ctypes.c_int32, _F32, _F32,
@@ -285,7 +292,7 @@ class Field:
                         _p(feat, ctypes.c_double))
         return sig, rgb, feat
 
-    def render_rays(self, o, dd, r, threads=None):
+    def render_rays(self, o, dd, r, threads=None, normals=False):
         o, dd, r = _f32(o).reshape(-1, 3), _f32(dd).reshape(-1, 3), _f32(r).reshape(-1)
         B = o.shape[0]
         pq = np.zeros((B, 3), np.float64)
@@ -293,17 +300,32 @@ class Field:
         T = np.zeros(B, np.float64)
         n = np.zeros(B, np.int32)
         depth = np.zeros(B, np.float64)
+        nrm = np.zeros((B, 3), np.float64) if normals else None
         lib().orc_render_rays(*self._args(), _p(self.occ, ctypes.c_uint32),
                               _p(o, ctypes.c_float), _p(dd, ctypes.c_float),
                               _p(r, ctypes.c_float), B, _p(pq, ctypes.c_double),
                               _p(lin, ctypes.c_double), _p(T, ctypes.c_double),
                               _p(n, ctypes.c_int32), _p(depth, ctypes.c_double),
-                              threads or os.cpu_count() or 1)
-        return dict(pq=pq, linear=lin, T=T, n=n, depth=depth)
+                              _p(nrm, ctypes.c_double), threads or os.cpu_count() or 1)
+        out = dict(pq=pq, linear=lin, T=T, n=n, depth=depth)
+        if normals:
+            out["normal"] = nrm
+        return out
 
-    def render(self, c2w, K, res, threads=None):
+    def render(self, c2w, K, res, threads=None, normals=False):
         o, dd, r = camera_rays(self.cfg, c2w, K, res)
-        return self.render_rays(o, dd, r, threads)
+        return self.render_rays(o, dd, r, threads, normals)
+
+    def density_grad(self, pos, radius):
+        """sigma [n] and d sigma / d position [n][3] at a fixed footprint."""
+        pos = _f32(pos).reshape(-1, 3)
+        radius = _f64(np.broadcast_to(np.asarray(radius, np.float64), (pos.shape[0],)))
+        n = pos.shape[0]
+        sigma = np.zeros(n, np.float64)
+        grad = np.zeros((n, 3), np.float64)
+        lib().orc_density_grad(*self._args(), _p(pos, ctypes.c_float), _p(radius, ctypes.c_double),
+                               n, _p(sigma, ctypes.c_double), _p(grad, ctypes.c_double))
+        return sigma, grad
 
     def march(self, o, dd, cap):
         o, dd = _f32(o).reshape(-1, 3), _f32(dd).reshape(-1, 3)
@@ -345,6 +367,19 @@ def prune(F, cams, k, threshold, hist=None):
                     _p(alpha, ctypes.c_double))
     shape = tuple(cfg.occ_res[::-1])
     return keep.reshape(shape).astype(bool), alpha.reshape(shape)
+
+
+def tonemap(pq, T=None, ev=0.0):
+    """PQ colour [n][3] (and transmittance [n]) -> packed sRGB8 + coverage
+    words [n] and the unrounded 255 s values [n][4] at exposure ev stops."""
+    pq = _f64(pq).reshape(-1, 3)
+    n = pq.shape[0]
+    Tm = None if T is None else _f64(T).reshape(-1)
+    rgba = np.zeros(n, np.uint32)
+    pre = np.zeros((n, 4), np.float64)
+    lib().orc_tonemap(_p(pq, ctypes.c_double), _p(Tm, ctypes.c_double), n, float(ev),
+                      _p(rgba, ctypes.c_uint32), _p(pre, ctypes.c_double))
+    return rgba, pre
 
 
 def upsample_occupancy(values, factor):

@@ -397,6 +397,70 @@ static void mlp_forward(const orc_desc *D, const double *mlp, const double *dir,
     }
 }
 
+/* Gradient of sigma with respect to the world position p at a fixed
+ * footprint (the LOD weights w_l depend on the ray distance, not on p):
+ * sigma = exp(o_0 + bias), o_0 = W2[0] relu(W1 feat), and feature (l, f) is
+ * w_l times the trilinear interpolation of its cell's corners in the level's
+ * coordinate x = N_l (p - aabb_min) / max extent, whose derivative along
+ * axis k replaces the corner weight's factor of axis k by +-1. */
+static void density_grad(const orc_desc *D, const orc_geom *g, const double *grid, const double *mlp,
+                         const float *p, const orc_sample *s, double *grad)
+{
+    int32_t L = D->levels, F = D->feats, din = L * F;
+    const double *W1 = mlp_W(D, mlp, 0), *W2 = mlp_W(D, mlp, 1);
+    double dfeat[ORC_MAX_LEVELS * 2][3];
+    for (int32_t l = 0; l < L; ++l) {
+        for (int f = 0; f < F; ++f)
+            for (int k = 0; k < 3; ++k) dfeat[l * F + f][k] = 0.0;
+        if (s->wl[l] == 0.0) continue;
+        uint32_t idx[8];
+        float fr[3];
+        level_corners(g, l, p, idx, fr);
+        const double dxdp = (double)g->N[l] * (double)g->inv_ext;
+        for (int b = 0; b < 8; ++b) {
+            const double *e = grid + ((int64_t)l * g->T + idx[b]) * F;
+            for (int k = 0; k < 3; ++k) {
+                double dw = ((b >> k) & 1) ? 1.0 : -1.0;
+                for (int m = 0; m < 3; ++m) {
+                    if (m == k) continue;
+                    double t = (double)fr[m];
+                    dw *= ((b >> m) & 1) ? t : 1.0 - t;
+                }
+                for (int f = 0; f < F; ++f) dfeat[l * F + f][k] += s->wl[l] * dxdp * dw * e[f];
+            }
+        }
+    }
+    for (int k = 0; k < 3; ++k) {
+        double do0 = 0.0;
+        for (int j = 0; j < 64; ++j) {
+            double pre = 0.0, dpre = 0.0;
+            for (int q = 0; q < din; ++q) {
+                pre += W1[j * din + q] * s->feat[q];
+                dpre += W1[j * din + q] * dfeat[q][k];
+            }
+            if (pre > 0.0) do0 += W2[j] * dpre;
+        }
+        grad[k] = s->sigma * do0;
+    }
+}
+
+/* sigma and its position gradient at n points (footprint radius in world
+ * units per point): grad [n][3]. */
+void orc_density_grad(const orc_desc *D, const double *grid, const double *mlp, const float *pos,
+                      const double *radius, int32_t n, double *sigma, double *grad)
+{
+    orc_geom g;
+    geom_init(D, &g);
+    const double dir[3] = {0.0, 0.0, 1.0};
+    for (int32_t i = 0; i < n; ++i) {
+        orc_sample s;
+        sample_feats(D, &g, grid, pos + 3 * i, radius[i] * (double)g.inv_ext, &s);
+        mlp_forward(D, mlp, dir, &s);
+        sigma[i] = s.sigma;
+        density_grad(D, &g, grid, mlp, pos + 3 * i, &s, grad + 3 * i);
+    }
+}
+
 /* Field query at n points: world position, unit direction, footprint radius
  * (world units) -> sigma, PQ colour, and the 32 LOD-weighted features. */
 void orc_query(const orc_desc *D, const double *grid, const double *mlp, const float *pos,
@@ -423,7 +487,8 @@ void orc_query(const orc_desc *D, const double *grid, const double *mlp, const f
 typedef struct {
     double C[3];
     double T;
-    double depth; /* sum_i w_i t_i: expected distance of the composited samples */
+    double depth;     /* sum_i w_i t_i: expected distance of the composited samples */
+    double normal[3]; /* sum_i w_i n_i, n_i = -grad sigma / |grad sigma| (when asked for) */
     int32_t n_eval;
 } orc_ray_out;
 
@@ -435,10 +500,10 @@ typedef struct {
 
 static void render_one(const orc_desc *D, const orc_geom *g, const double *grid, const double *mlp,
                        const uint32_t *occ, const float *t_tab, const float *o, const float *d,
-                       double r, orc_ray_out *out, orc_tape *tape)
+                       double r, orc_ray_out *out, orc_tape *tape, int normals)
 {
     double dir[3] = {d[0], d[1], d[2]};
-    double T = 1.0, C[3] = {0, 0, 0}, depth = 0.0;
+    double T = 1.0, C[3] = {0, 0, 0}, depth = 0.0, Nrm[3] = {0, 0, 0};
     int32_t n = 0;
     for (int32_t i = 0; i < D->max_steps; ++i) {
         float p[3];
@@ -465,6 +530,13 @@ static void render_one(const orc_desc *D, const orc_geom *g, const double *grid,
         }
         for (int c = 0; c < 3; ++c) C[c] += w * s.c[c];
         depth += w * t;
+        if (normals) {
+            double gs[3];
+            density_grad(D, g, grid, mlp, p, &s, gs);
+            const double len = sqrt(gs[0] * gs[0] + gs[1] * gs[1] + gs[2] * gs[2]);
+            if (len > 0.0)
+                for (int k = 0; k < 3; ++k) Nrm[k] += w * (-gs[k] / len);
+        }
         T *= 1.0 - alpha;
         ++n;
         if (T < D->T_eps) break;
@@ -472,6 +544,7 @@ static void render_one(const orc_desc *D, const orc_geom *g, const double *grid,
     for (int c = 0; c < 3; ++c) out->C[c] = C[c];
     out->T = T;
     out->depth = depth;
+    for (int k = 0; k < 3; ++k) out->normal[k] = Nrm[k];
     out->n_eval = n;
 }
 
@@ -481,7 +554,8 @@ static void render_one(const orc_desc *D, const orc_geom *g, const double *grid,
  * sum_i w_i t_i [B]. */
 void orc_render_rays(const orc_desc *D, const double *grid, const double *mlp, const uint32_t *occ,
                      const float *o, const float *d, const float *r, int32_t B, double *out_pq,
-                     double *out_lin, double *out_T, int32_t *out_n, double *out_depth, int32_t threads)
+                     double *out_lin, double *out_T, int32_t *out_n, double *out_depth,
+                     double *out_normal, int32_t threads)
 {
     orc_geom g;
     geom_init(D, &g);
@@ -490,10 +564,12 @@ void orc_render_rays(const orc_desc *D, const double *grid, const double *mlp, c
 #pragma omp parallel for schedule(dynamic, 16) num_threads(threads > 0 ? threads : 1)
     for (int32_t i = 0; i < B; ++i) {
         orc_ray_out ro;
-        render_one(D, &g, grid, mlp, occ, t_tab, o + 3 * i, d + 3 * i, (double)r[i], &ro, NULL);
+        render_one(D, &g, grid, mlp, occ, t_tab, o + 3 * i, d + 3 * i, (double)r[i], &ro, NULL,
+                   out_normal != NULL);
         for (int c = 0; c < 3; ++c) {
             if (out_pq) out_pq[3 * i + c] = ro.C[c];
             if (out_lin) out_lin[3 * i + c] = orc_pq_to_linear(ro.C[c]);
+            if (out_normal) out_normal[3 * i + c] = ro.normal[c];
         }
         if (out_T) out_T[i] = ro.T;
         if (out_n) out_n[i] = ro.n_eval;
@@ -526,7 +602,7 @@ void orc_render(const orc_desc *D, const double *grid, const double *mlp, const 
             }
     }
     orc_render_rays(D, grid, mlp, occ, o, d, r, (int32_t)total, out_pq, out_lin, out_T, out_n,
-                    out_depth, threads);
+                    out_depth, NULL, threads);
     free(o);
     free(d);
     free(r);
@@ -661,7 +737,7 @@ double orc_backward(const orc_desc *D, const double *grid, const double *mlp, co
         const float *oi = o + 3 * i, *di = d + 3 * i;
         double dir[3] = {di[0], di[1], di[2]};
         orc_ray_out ro;
-        render_one(D, &g, grid, mlp, occ, t_tab, oi, di, (double)r[i], &ro, tape);
+        render_one(D, &g, grid, mlp, occ, t_tab, oi, di, (double)r[i], &ro, tape, 0);
         double gC[3];
         for (int c = 0; c < 3; ++c) {
             double tgt = orc_linear_to_pq((double)target_lin[3 * i + c]);
@@ -805,7 +881,7 @@ void orc_history(const orc_desc *D, const double *grid, const double *mlp, const
     orc_tape *tape = (orc_tape *)malloc(sizeof(orc_tape) * D->max_steps);
     for (int32_t b = 0; b < B; ++b) {
         orc_ray_out ro;
-        render_one(D, &g, grid, mlp, occ, t_tab, o + 3 * b, d + 3 * b, (double)r[b], &ro, tape);
+        render_one(D, &g, grid, mlp, occ, t_tab, o + 3 * b, d + 3 * b, (double)r[b], &ro, tape, 0);
         for (int32_t k = 0; k < ro.n_eval; ++k) {
             const float *p = tape[k].p;
             /* voxel of the composited sample */
@@ -823,6 +899,40 @@ void orc_history(const orc_desc *D, const double *grid, const double *mlp, const
     }
     free(tape);
     free(t_tab);
+}
+
+/* Display tonemapping (the paper's exposure sweep: PQ colour to sRGB at a
+ * chosen exposure). Per channel: linear = PQ^-1(C) in units of 100 cd/m^2,
+ * v = clamp(linear 2^ev, 0, 1), the sRGB transfer function of IEC 61966-2-1
+ * (12.92 v up to 0.0031308, else 1.055 v^(1/2.4) - 0.055), 8 bits by
+ * round-half-up of 255 s. Alpha = coverage 1 - T (255 when T is NULL).
+ * rgba [n] packs R | G << 8 | B << 16 | A << 24; pre [n][4] (optional)
+ * holds the unrounded 255 s values. */
+static double srgb_oetf(double v)
+{
+    return v <= 0.0031308 ? 12.92 * v : 1.055 * pow(v, 1.0 / 2.4) - 0.055;
+}
+
+void orc_tonemap(const double *pq, const double *T, int64_t n, double ev, uint32_t *rgba, double *pre)
+{
+    const double scale = pow(2.0, ev);
+    for (int64_t i = 0; i < n; ++i) {
+        double q[4];
+        for (int c = 0; c < 3; ++c) {
+            double v = orc_pq_to_linear(pq[3 * i + c]) * scale;
+            v = v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v);
+            q[c] = 255.0 * srgb_oetf(v);
+        }
+        double a = T ? 1.0 - T[i] : 1.0;
+        a = a < 0.0 ? 0.0 : (a > 1.0 ? 1.0 : a);
+        q[3] = 255.0 * a;
+        uint32_t word = 0;
+        for (int c = 0; c < 4; ++c) {
+            word |= (uint32_t)floor(q[c] + 0.5) << (8 * c);
+            if (pre) pre[4 * i + c] = q[c];
+        }
+        rgba[i] = word;
+    }
 }
 
 /* Introspection for the tests. */

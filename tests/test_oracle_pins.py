@@ -609,3 +609,103 @@ def test_upsample_occupancy_brute_force():
         for y in range(9):
             for x in range(12):
                 assert up[z, y, x] == occ[z // 3, y // 3, x // 3]
+
+
+# ----------------------------------------------------------------------------
+# Auxiliary outputs: density gradient / normals, display tonemapping
+# ----------------------------------------------------------------------------
+def test_density_grad_matches_central_differences():
+    """Positive features; hidden units 0-31 have positive input weights (always
+    active), 32-63 negative ones (never active), so log sigma = o_0 + bias is
+    trilinear inside each cell of every level with no ReLU switch, and central
+    differences of log sigma inside one cell of every level give
+    grad sigma / sigma up to the fp32 rounding of the grid coordinates
+    (~1e-5 of a finest cell against a 0.13-cell stencil). A dropped level,
+    feature, ReLU mask or W2 term fails."""
+    cfg = replace(S.cfg_unit_cube(), occ_res=(16, 16, 16), levels=8)
+    rng = np.random.default_rng(8)
+    grid = rng.uniform(0.1, 1.0, (cfg.levels, cfg.T, cfg.feats))
+    mlp = rng.normal(size=O.mlp_count(cfg)) * 0.3
+    W1 = np.abs(mlp[:64 * 16].reshape(64, 16))
+    W1[32:] *= -1
+    mlp[:64 * 16] = W1.reshape(-1)
+    F = O.Field(cfg, grid, mlp, S.pack_bits(np.ones((16, 16, 16), bool)))
+    n = 4000
+    pos = rng.uniform(0.05, 0.95, (n, 3)).astype(np.float32)
+    _, frac = O.corners(cfg, pos)
+    inner = ((frac > 0.08) & (frac < 0.92)).reshape(n, -1).all(axis=1)
+    radius = 1e-4
+    sig, grad = F.density_grad(pos, radius)
+    h = 2.0 ** -12
+    idx = np.flatnonzero(inner)
+    assert idx.size > 50, idx.size
+    for i in idx:
+        fd = np.zeros(3)
+        for k in range(3):
+            pp, pm = pos[i].copy(), pos[i].copy()
+            pp[k] += h
+            pm[k] -= h
+            ls = np.log(F.density_grad(np.stack([pp, pm]), radius)[0])
+            fd[k] = (ls[0] - ls[1]) / (float(pp[k]) - float(pm[k]))
+        np.testing.assert_allclose(grad[i] / sig[i], fd, rtol=0, atol=2e-4 * np.abs(fd).max())
+
+
+def _axis_field(density_bias):
+    """Level 0 dense (N = 5) with feature 0 = the vertex's x coordinate / 5,
+    the density MLP passes it through one ReLU: o_0 = p_x, so grad sigma
+    points along +x and every normal is -x."""
+    cfg = replace(_tiny(5, 10), occ_res=(8, 8, 8), density_bias=density_bias, T_eps=0.0)
+    grid = np.zeros((1, cfg.T, 2))
+    for c in range(6):
+        for b in range(6):
+            for a in range(6):
+                grid[0, a + 6 * b + 36 * c] = (a / 5.0, 0.0)
+    mlp = np.zeros(O.mlp_count(cfg))
+    mlp[0] = 1.0            # W1[0][0]
+    mlp[64 * 2 + 0] = 1.0   # W2[0][0]
+    return cfg, O.Field(cfg, grid, mlp, S.pack_bits(np.ones((8, 8, 8), bool)))
+
+
+def test_density_grad_closed_form_axis_field():
+    cfg, F = _axis_field(1.0)
+    pos = np.array([[0.3, 0.5, 0.5], [0.71, 0.2, 0.9]], np.float32)
+    sig, grad = F.density_grad(pos, 0.0)
+    np.testing.assert_allclose(sig, np.exp(pos[:, 0].astype(np.float64) + 1.0), rtol=1e-6)
+    np.testing.assert_allclose(grad[:, 0], sig, rtol=1e-6)
+    assert (grad[:, 1:] == 0).all()
+
+
+def test_composited_normal_closed_form():
+    """sum_i w_i n_i with n_i = -x for every sample: (-(1 - T), 0, 0)."""
+    cfg, F = _axis_field(2.0)
+    rng = np.random.default_rng(5)
+    o = rng.uniform(0.3, 0.7, (40, 3)).astype(np.float32)
+    d = rng.normal(size=(40, 3))
+    d = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
+    out = F.render_rays(o, d, np.zeros(40, np.float32), threads=1, normals=True)
+    assert (out["n"] > 3).all()
+    np.testing.assert_allclose(out["normal"][:, 0], -(1.0 - out["T"]), rtol=1e-9, atol=1e-12)
+    assert (out["normal"][:, 1:] == 0).all()
+    # normals do not change the rest of the render
+    plain = F.render_rays(o, d, np.zeros(40, np.float32), threads=1)
+    assert (plain["pq"] == out["pq"]).all() and (plain["T"] == out["T"]).all()
+
+
+def test_tonemap_srgb_anchors_exposure_and_coverage():
+    rows = [tuple(map(float, ln.split())) for ln in open(os.path.join(GOLDEN, "srgb_anchors.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    v = np.array([r[0] for r in rows])
+    s = np.array([r[1] for r in rows])
+    pq = np.repeat(np.array([O.linear_to_pq(x) for x in v])[:, None], 3, axis=1)
+    rgba, pre = O.tonemap(pq)
+    np.testing.assert_allclose(pre[:, :3] / 255.0, s[:, None].repeat(3, 1), atol=2e-6)
+    assert ((rgba >> 24) == 255).all()
+    assert [int(x & 255) for x in rgba] == [int(np.floor(255 * x + 0.5)) for x in s]
+    # +1 stop of exposure on half the luminance gives the same pixels
+    pq_half = np.repeat(np.array([O.linear_to_pq(x / 2) for x in v])[:, None], 3, axis=1)
+    rgba2, pre2 = O.tonemap(pq_half, ev=1.0)
+    np.testing.assert_allclose(pre2, pre, rtol=1e-5)
+    # over-exposure clamps to white, PQ 0 is black, coverage is 1 - T
+    rgba3, _ = O.tonemap([[1.0, 0.0, 0.5]], T=[0.25], ev=0.0)
+    assert int(rgba3[0]) & 255 == 255 and (int(rgba3[0]) >> 8) & 255 == 0
+    assert int(rgba3[0]) >> 24 == int(np.floor(0.75 * 255 + 0.5))

@@ -113,6 +113,17 @@ typedef struct {
                           composited samples (divide by 1 - T for the distance
                           of the visible surface); the depth maps of the
                           paper's renders. */
+    float *out_normal; /* optional [rays][3] composited normal sum_i w_i n_i,
+                          n_i = -grad sigma / |grad sigma| at the sample's
+                          position (fixed footprint); the normal maps of the
+                          paper's renders. VRNERF_FP32 only (EINVAL otherwise). */
+    uint32_t *out_rgba8; /* optional [rays] display pixels: sRGB (IEC 61966-2-1)
+                          of clamp(linear 2^exposure_ev, 0, 1), 8 bits per
+                          channel rounded half up, alpha = 1 - T; packed
+                          R | G << 8 | B << 16 | A << 24 (the exposure sweep
+                          of the paper's tonemapping from PQ to sRGB). */
+    float exposure_ev; /* exposure in stops for out_rgba8 (0: 100 cd/m^2 = white) */
+    int32_t reserved2;
 } vrnerf_render_opts;
 
 /* Message of the last failed call on this thread ("" if none). */
@@ -215,6 +226,14 @@ int vrnerf_debug_corners(vrnerf_field *field, const float *pos, int32_t n, uint3
 int vrnerf_backward(vrnerf_field *field, const float *rays_o, const float *rays_d,
                     const float *radii, const float *target_linear, int32_t B, float *loss_host,
                     void *stream);
+
+/* Display tonemapping of an existing PQ image (the exposure sweep of the
+ * paper's results: PQ colour to sRGB at a chosen exposure, without
+ * re-rendering). pq [n][3] and optional T [n] (NULL: alpha 255) in device
+ * memory; rgba8 [n] as vrnerf_render_opts.out_rgba8. Asynchronous on
+ * `stream`. EINVAL (n < 0, NULL pointers), ECUDA. */
+int vrnerf_tonemap(const float *pq, const float *T, int64_t n, float exposure_ev, uint32_t *rgba8,
+                   void *stream);
 
 /* Occupancy-grid pruning (Sec. 4.3.2). vrnerf_history_reset allocates (on
  * the first call) and zeroes the field's training history: from then on

@@ -345,6 +345,18 @@ int vrnerf_field_get_params(vrnerf_field *F, void *grid_host, float *mlp_host) {
     ABI_GUARD_END
 }
 
+int vrnerf_tonemap(const float *pq, const float *T, int64_t n, float exposure_ev, uint32_t *rgba8, void *stream) {
+    ABI_GUARD_BEGIN
+    if (n < 0) return fail(VRNERF_EINVAL, "n must be >= 0");
+    if (n > 0 && (!pq || !rgba8)) return fail(VRNERF_EINVAL, "NULL argument");
+    if (!std::isfinite(exposure_ev)) return fail(VRNERF_EINVAL, "exposure_ev must be finite");
+    cudaError_t e = launch_tonemap(pq, T, n, exp2f(exposure_ev), reinterpret_cast<unsigned int *>(rgba8),
+                                   static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "tonemap");
+    return VRNERF_OK;
+    ABI_GUARD_END
+}
+
 int vrnerf_field_set_occupancy(vrnerf_field *F, const uint32_t *occ) {
     ABI_GUARD_BEGIN
     if (!F || !occ) return fail(VRNERF_EINVAL, "NULL argument");
@@ -366,10 +378,18 @@ static int render_common(vrnerf_field *F, const RaySource &src, float *out,
     const int prec = opts ? opts->precision : VRNERF_FP32;
     int rc = check_precision(prec);
     if (rc) return rc;
+    if (opts && opts->out_normal && prec != VRNERF_FP32)
+        return fail(VRNERF_EINVAL, "out_normal needs the fp32 path (precision VRNERF_FP32)");
+    if (opts && opts->out_rgba8 && !std::isfinite(opts->exposure_ev))
+        return fail(VRNERF_EINVAL, "exposure_ev must be finite");
     RenderOut ro{out, opts ? opts->out_pq : nullptr, opts ? opts->out_T : nullptr,
                  opts ? opts->out_n : nullptr,
                  opts ? reinterpret_cast<unsigned long long *>(opts->stats) : nullptr,
-                 opts ? opts->out_depth : nullptr};
+                 opts ? opts->out_depth : nullptr,
+                 nullptr,
+                 opts ? opts->out_normal : nullptr,
+                 opts ? reinterpret_cast<unsigned int *>(opts->out_rgba8) : nullptr,
+                 opts ? exp2f(opts->exposure_ev) : 1.0f};
     cudaError_t e = cudaMemsetAsync(F->counter, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return cuda_fail(e, "render: reset counter");
     if (prec == VRNERF_FP32)

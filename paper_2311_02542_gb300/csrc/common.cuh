@@ -68,6 +68,9 @@ struct RenderOut {
     unsigned long long *stats;  // optional [4]: samples, levels fetched, steps tested, rays
     float *depth;               // optional: sum_i w_i t_i
     float *hist;                // optional per-voxel max opacity of composited samples
+    float *normal;              // optional [rays][3]: sum_i w_i n_i (fp32 kernel only)
+    unsigned int *rgba8;        // optional [rays]: sRGB8 + coverage at `exposure`
+    float exposure;             // 2^ev, linear scale applied before the sRGB encoding
 };
 
 // Warp-aggregated add of per-thread counters into stats (all lanes call).
@@ -293,6 +296,42 @@ __device__ __forceinline__ float linear_to_pq(float c) {
     float Y = fminf(fmaxf(c * 0.01f, 0.0f), 1.0f);
     float ym = powf(Y, kPqM1);
     return powf((kPqC1 + kPqC2 * ym) / (1.0f + kPqC3 * ym), kPqM2);
+}
+
+// Display encoding: sRGB transfer function (IEC 61966-2-1) of a relative
+// linear value clamped to [0, 1], 8 bits rounded half up.
+__device__ __forceinline__ unsigned int srgb8(float v) {
+    v = fminf(fmaxf(v, 0.0f), 1.0f);
+    const float s = v <= 0.0031308f ? 12.92f * v : 1.055f * powf(v, 1.0f / 2.4f) - 0.055f;
+    return (unsigned int)(255.0f * s + 0.5f);
+}
+
+__device__ __forceinline__ unsigned int tonemap_rgba8(const float lin[3], float T, float exposure) {
+    unsigned int w = srgb8(lin[0] * exposure) | srgb8(lin[1] * exposure) << 8 | srgb8(lin[2] * exposure) << 16;
+    const float a = fminf(fmaxf(1.0f - T, 0.0f), 1.0f);  // coverage, not display-encoded
+    return w | (unsigned int)(255.0f * a + 0.5f) << 24;
+}
+
+// Per-ray epilogue shared by the render kernels: PQ decode (Eq. 1-2) and the
+// optional outputs.
+__device__ __forceinline__ void finish_outputs(const RenderOut &out, long long pix, const float C[3], float T,
+                                               int n, float depth, const float *N) {
+    float lin[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        lin[c] = pq_to_linear(C[c]);
+        out.lin[3 * pix + c] = lin[c];
+        if (out.pq) out.pq[3 * pix + c] = C[c];
+    }
+    if (out.T) out.T[pix] = T;
+    if (out.n) out.n[pix] = n;
+    if (out.depth) out.depth[pix] = depth;
+    if (out.rgba8) out.rgba8[pix] = tonemap_rgba8(lin, T, out.exposure);
+    if (N && out.normal) {
+        out.normal[3 * pix] = N[0];
+        out.normal[3 * pix + 1] = N[1];
+        out.normal[3 * pix + 2] = N[2];
+    }
 }
 
 // ---------------------------------------------------------------------------

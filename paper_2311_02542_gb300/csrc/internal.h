@@ -23,6 +23,8 @@ cudaError_t launch_query_simt(const FieldView &f, const float *pos, const float 
                               cudaStream_t st);
 cudaError_t launch_debug_march(const FieldView &f, const float *o, const float *d, int B, int cap,
                                int *rec_i, int *rec_vox, int *count, cudaStream_t st);
+cudaError_t launch_tonemap(const float *pq, const float *T, long long n, float exposure, unsigned int *rgba8,
+                           cudaStream_t st);
 cudaError_t launch_debug_corners(const FieldView &f, const float *pos, int n, uint32_t *idx,
                                  cudaStream_t st);
 

@@ -130,19 +130,77 @@ __device__ __forceinline__ void mlp_simt(const float *__restrict__ s, const floa
     rgb[2] = 1.0f / (1.0f + expf(-z2));
 }
 
-__device__ __forceinline__ void finish_ray(const RenderOut &out, long long pix, const float C[3],
-                                           float T, int n, float depth) {
+// d o_0 / d feat = W1^T (relu'(W1 feat) * W2[0, :]) with the weights in
+// shared memory (W2^T row j holds W2[:, j]).
+template <int D>
+__device__ __forceinline__ void density_feat_grad(const float *__restrict__ s, const float feat[D], float g[D]) {
+    using W = SimtW<D>;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        out.lin[3 * pix + c] = pq_to_linear(C[c]);
-        if (out.pq) out.pq[3 * pix + c] = C[c];
+    for (int q = 0; q < D; ++q) g[q] = 0.0f;
+    for (int j = 0; j < 64; ++j) {
+        const float4 *w = reinterpret_cast<const float4 *>(s + W::oW1 + j * D);
+        float a = 0.0f;
+#pragma unroll
+        for (int q = 0; q < D / 4; ++q) {
+            const float4 v = w[q];
+            a = fmaf(v.x, feat[4 * q], a);
+            a = fmaf(v.y, feat[4 * q + 1], a);
+            a = fmaf(v.z, feat[4 * q + 2], a);
+            a = fmaf(v.w, feat[4 * q + 3], a);
+        }
+        if (a > 0.0f) {
+            const float c = s[W::oW2T + j * 16];
+#pragma unroll
+            for (int q = 0; q < D / 4; ++q) {
+                const float4 v = w[q];
+                g[4 * q] = fmaf(c, v.x, g[4 * q]);
+                g[4 * q + 1] = fmaf(c, v.y, g[4 * q + 1]);
+                g[4 * q + 2] = fmaf(c, v.z, g[4 * q + 2]);
+                g[4 * q + 3] = fmaf(c, v.w, g[4 * q + 3]);
+            }
+        }
     }
-    if (out.T) out.T[pix] = T;
-    if (out.n) out.n[pix] = n;
-    if (out.depth) out.depth[pix] = depth;
 }
 
+// v = sum_q g_q d feat_q / d p at a fixed footprint: per level, w_l N_l /
+// extent times the derivative of the trilinear interpolation along each
+// axis (the corner weight's factor of that axis replaced by +-1). The
+// corners are fetched again (L2-resident) instead of kept from the gather.
 template <int L>
+__device__ __forceinline__ void feature_pos_grad(const FieldView &f, const float p[3], float r_norm,
+                                                 const float g[2 * L], float v[3]) {
+    float ph[3];
+    grid_position(f, p, ph);
+    const float Ls = lod_star(f, r_norm);
+    v[0] = v[1] = v[2] = 0.0f;
+#pragma unroll 1
+    for (int l = 0; l < L; ++l) {
+        const float wl = lod_weight(Ls, l);
+        if (wl == 0.0f) continue;
+        uint32_t idx[8];
+        float fr[3];
+        level_corners_ph(f, l, ph, idx, fr);
+        float d0[3] = {0, 0, 0}, d1[3] = {0, 0, 0};
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const float2 e = load_feat(f, l, idx[b]);
+            const float wx = b & 1 ? fr[0] : 1.0f - fr[0], wy = b & 2 ? fr[1] : 1.0f - fr[1],
+                        wz = b & 4 ? fr[2] : 1.0f - fr[2];
+            const float dw[3] = {(b & 1 ? 1.0f : -1.0f) * wy * wz, (b & 2 ? 1.0f : -1.0f) * wx * wz,
+                                 (b & 4 ? 1.0f : -1.0f) * wx * wy};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                d0[k] = fmaf(dw[k], e.x, d0[k]);
+                d1[k] = fmaf(dw[k], e.y, d1[k]);
+            }
+        }
+        const float sc = wl * (float)f.N[l] * f.inv_ext;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) v[k] = fmaf(sc, fmaf(g[2 * l], d0[k], g[2 * l + 1] * d1[k]), v[k]);
+    }
+}
+
+template <int L, bool NRM>
 __global__ void __launch_bounds__(kSimtThreads, 4)
 render_simt_kernel(const FieldView f, const RaySource src, const RenderOut out,
                    unsigned long long *__restrict__ counter) {
@@ -160,6 +218,7 @@ render_simt_kernel(const FieldView f, const RaySource src, const RenderOut out,
     bool exhausted = false;
     MarchRay mr;
     float r = 0.0f, T = 1.0f, C[3] = {0, 0, 0}, Dp = 0.0f;
+    float Nm[3] = {0, 0, 0};
     int n_eval = 0;
     unsigned st_samples = 0, st_levels = 0, st_steps = 0, st_rays = 0;
 
@@ -186,6 +245,7 @@ render_simt_kernel(const FieldView f, const RaySource src, const RenderOut out,
                         T = 1.0f;
                         Dp = 0.0f;
                         C[0] = C[1] = C[2] = 0.0f;
+                        Nm[0] = Nm[1] = Nm[2] = 0.0f;
                     }
                 }
             }
@@ -194,7 +254,7 @@ render_simt_kernel(const FieldView f, const RaySource src, const RenderOut out,
                 if (mres == MARCH_SAMPLE) {
                     have = true;
                 } else if (mres == MARCH_END) {
-                    finish_ray(out, pix, C, T, n_eval, Dp);
+                    finish_outputs(out, pix, C, T, n_eval, Dp, NRM ? Nm : nullptr);
                     ray = -1;
                     ++st_rays;
                 }
@@ -219,11 +279,23 @@ render_simt_kernel(const FieldView f, const RaySource src, const RenderOut out,
             C[1] += w * rgb[1];
             C[2] += w * rgb[2];
             Dp += w * t;
+            if constexpr (NRM) {
+                float g[D], v[3];
+                density_feat_grad<D>(sW, feat, g);
+                feature_pos_grad<L>(f, p, r_norm, g, v);
+                const float len = sqrtf(fmaf(v[0], v[0], fmaf(v[1], v[1], v[2] * v[2])));
+                if (len > 0.0f) {
+                    const float s = -w / len;
+                    Nm[0] = fmaf(s, v[0], Nm[0]);
+                    Nm[1] = fmaf(s, v[1], Nm[1]);
+                    Nm[2] = fmaf(s, v[2], Nm[2]);
+                }
+            }
             T *= expf(-sd);
             ++n_eval;
             ++mr.step;
             if (T < f.T_eps) {
-                finish_ray(out, pix, C, T, n_eval, Dp);
+                finish_outputs(out, pix, C, T, n_eval, Dp, NRM ? Nm : nullptr);
                 ray = -1;
                 ++st_rays;
             }
@@ -254,6 +326,25 @@ query_simt_kernel(const FieldView f, const float *__restrict__ pos, const float 
     for (int c = 0; c < 3; ++c) rgb_out[3 * i + c] = rgb[c];
     if (feat_out)
         for (int k = 0; k < D; ++k) feat_out[(long long)i * D + k] = feat[k];
+}
+
+__global__ void tonemap_kernel(const float *__restrict__ pq, const float *__restrict__ T, long long n,
+                               float exposure, unsigned int *__restrict__ rgba8) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float lin[3] = {pq_to_linear(__ldg(pq + 3 * i)), pq_to_linear(__ldg(pq + 3 * i + 1)),
+                              pq_to_linear(__ldg(pq + 3 * i + 2))};
+        rgba8[i] = tonemap_rgba8(lin, T ? __ldg(T + i) : 0.0f, exposure);
+    }
+}
+
+cudaError_t launch_tonemap(const float *pq, const float *T, long long n, float exposure, unsigned int *rgba8,
+                           cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    long long blocks = (n + 255) / 256, cap = (long long)num_sms() * 8;
+    if (blocks > cap) blocks = cap;
+    tonemap_kernel<<<(unsigned)blocks, 256, 0, st>>>(pq, T, n, exposure, rgba8);
+    return cudaGetLastError();
 }
 
 __global__ void debug_march_kernel(const FieldView f, const float *__restrict__ o_in,
@@ -306,13 +397,13 @@ size_t simt_smem_bytes(const FieldView &f) {
     return sizeof(float) * (size_t)(wsize + f.S + 1);
 }
 
-template <int L>
+template <int L, bool NRM>
 static cudaError_t render_simt_t(const FieldView &f, const RaySource &src, const RenderOut &out,
                                  unsigned long long *counter, cudaStream_t st) {
     static int blocks_per_sm = 0;
     static size_t configured_smem = 0;
     const size_t smem = simt_smem_bytes(f);
-    auto kern = render_simt_kernel<L>;
+    auto kern = render_simt_kernel<L, NRM>;
     if (smem != configured_smem) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -331,8 +422,11 @@ static cudaError_t render_simt_t(const FieldView &f, const RaySource &src, const
 
 cudaError_t launch_render_simt(const FieldView &f, const RaySource &src, const RenderOut &out,
                                unsigned long long *counter, cudaStream_t st) {
-    return f.L == 8 ? render_simt_t<8>(f, src, out, counter, st)
-                    : render_simt_t<16>(f, src, out, counter, st);
+    if (out.normal)
+        return f.L == 8 ? render_simt_t<8, true>(f, src, out, counter, st)
+                        : render_simt_t<16, true>(f, src, out, counter, st);
+    return f.L == 8 ? render_simt_t<8, false>(f, src, out, counter, st)
+                    : render_simt_t<16, false>(f, src, out, counter, st);
 }
 
 template <int L>

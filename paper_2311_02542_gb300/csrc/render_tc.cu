@@ -23,18 +23,6 @@
 
 namespace vrn {
 
-__device__ __forceinline__ void finish_ray_tc(const RenderOut &out, long long pix, const float C[3],
-                                           float T, int n, float depth) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        out.lin[3 * pix + c] = pq_to_linear(C[c]);
-        if (out.pq) out.pq[3 * pix + c] = C[c];
-    }
-    if (out.T) out.T[pix] = T;
-    if (out.n) out.n[pix] = n;
-    if (out.depth) out.depth[pix] = depth;
-}
-
 template <int L, int FMT>
 __global__ void __launch_bounds__(kTcThreads, kTcMinBlocks)
 render_tc_kernel(const FieldView f, const RaySource src, const RenderOut out,
@@ -87,7 +75,7 @@ render_tc_kernel(const FieldView f, const RaySource src, const RenderOut out,
                 if (mres == MARCH_SAMPLE) {
                     have = true;
                 } else if (mres == MARCH_END) {
-                    finish_ray_tc(out, pix, C, T, n_eval, Dp);
+                    finish_outputs(out, pix, C, T, n_eval, Dp, nullptr);
                     ray = -1;
                     ++st_rays;
                 }
@@ -121,7 +109,7 @@ render_tc_kernel(const FieldView f, const RaySource src, const RenderOut out,
             ++n_eval;
             ++mr.step;
             if (T < f.T_eps) {
-                finish_ray_tc(out, pix, C, T, n_eval, Dp);
+                finish_outputs(out, pix, C, T, n_eval, Dp, nullptr);
                 ray = -1;
                 ++st_rays;
             }

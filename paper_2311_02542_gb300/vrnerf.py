@@ -46,7 +46,9 @@ class FieldDesc(ctypes.Structure):
 class RenderOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("out_pq", ctypes.c_void_p), ("out_T", ctypes.c_void_p), ("out_n", ctypes.c_void_p),
-                ("stats", ctypes.c_void_p), ("out_depth", ctypes.c_void_p)]
+                ("stats", ctypes.c_void_p), ("out_depth", ctypes.c_void_p),
+                ("out_normal", ctypes.c_void_p), ("out_rgba8", ctypes.c_void_p),
+                ("exposure_ev", ctypes.c_float), ("reserved2", ctypes.c_int32)]
 
 
 _VP = ctypes.c_void_p
@@ -63,6 +65,7 @@ _SIGS = {
     "vrnerf_field_set_occupancy": (ctypes.c_int, [_VP, _VP]),
     "vrnerf_field_save": (ctypes.c_int, [_VP, ctypes.c_char_p]),
     "vrnerf_history_reset": (ctypes.c_int, [_VP]),
+    "vrnerf_tonemap": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, _F, _VP, _VP]),
     "vrnerf_occupancy_upsample": (ctypes.c_int, [_VP, _I32]),
     "vrnerf_field_get_occupancy": (ctypes.c_int, [_VP, _VP]),
     "vrnerf_field_get_history": (ctypes.c_int, [_VP, _VP]),
@@ -245,6 +248,16 @@ def vrnerf_field_load(path: str, cfg) -> Field:
     return f
 
 
+def vrnerf_tonemap(pq, T=None, exposure_ev=0.0, out=None, stream=None):
+    """pq [n][3] (and T [n]) CUDA tensors -> packed sRGB8 + coverage int32 [n]."""
+    n = pq.shape[0]
+    if out is None:
+        out = torch.empty(n, device=pq.device, dtype=torch.int32)
+    _check(load().vrnerf_tonemap(_ptr(_dev(pq)), _ptr(None if T is None else _dev(T)), n,
+                                 float(exposure_ev), _ptr(_dev(out, torch.int32)), _stream(stream)))
+    return out
+
+
 def vrnerf_history_reset(field: Field):
     _check(load().vrnerf_history_reset(field.h))
 
@@ -288,8 +301,12 @@ def vrnerf_field_set_occupancy(field: Field, occ_bits):
     _check(load().vrnerf_field_set_occupancy(field.h, _ptr(o)))
 
 
-def _opts(precision, out_pq=None, out_T=None, out_n=None, stats=None, out_depth=None):
+def _opts(precision, out_pq=None, out_T=None, out_n=None, stats=None, out_depth=None,
+          out_normal=None, out_rgba8=None, exposure_ev=0.0):
     o = RenderOpts()
+    o.out_normal = None if out_normal is None else _dev(out_normal).data_ptr()
+    o.out_rgba8 = None if out_rgba8 is None else _dev(out_rgba8, torch.int32).data_ptr()
+    o.exposure_ev = float(exposure_ev)
     o.out_depth = None if out_depth is None else _dev(out_depth).data_ptr()
     o.stats = None if stats is None else _dev(stats, torch.int64).data_ptr()
     o.precision = PRECISIONS.get(precision, precision) if isinstance(precision, str) else int(precision)
@@ -300,14 +317,15 @@ def _opts(precision, out_pq=None, out_T=None, out_n=None, stats=None, out_depth=
 
 
 def vrnerf_render(field: Field, cameras, intrinsics, resolution, out=None, precision=FP32,
-                  out_pq=None, out_T=None, out_n=None, stats=None, out_depth=None, stream=None):
+                  out_pq=None, out_T=None, out_n=None, stats=None, out_depth=None, out_normal=None,
+                  out_rgba8=None, exposure_ev=0.0, stream=None):
     """cameras [n][3][4], intrinsics [n][4]: float32 CUDA tensors; resolution
     [n][2] (W, H) on the host. Returns out [sum W*H][3] linear colour."""
     res = np.ascontiguousarray(resolution, dtype=np.int32).reshape(-1, 2)
     rays = int((res[:, 0].astype(np.int64) * res[:, 1]).sum())
     if out is None:
         out = torch.empty((rays, 3), device=cameras.device, dtype=torch.float32)
-    o = _opts(precision, out_pq, out_T, out_n, stats, out_depth)
+    o = _opts(precision, out_pq, out_T, out_n, stats, out_depth, out_normal, out_rgba8, exposure_ev)
     _check(load().vrnerf_render(field.h, _ptr(_dev(cameras)), _ptr(_dev(intrinsics)), _ptr(res),
                                 res.shape[0], _ptr(_dev(out)), ctypes.byref(o), _stream(stream)))
     return out
@@ -329,11 +347,12 @@ def vrnerf_render_host(field: Field, cameras, intrinsics, resolution, out=None, 
 
 
 def vrnerf_render_rays(field: Field, rays_o, rays_d, radii, out=None, precision=FP32, out_pq=None,
-                       out_T=None, out_n=None, stats=None, out_depth=None, stream=None):
+                       out_T=None, out_n=None, stats=None, out_depth=None, out_normal=None,
+                       out_rgba8=None, exposure_ev=0.0, stream=None):
     B = rays_o.shape[0]
     if out is None:
         out = torch.empty((B, 3), device=rays_o.device, dtype=torch.float32)
-    o = _opts(precision, out_pq, out_T, out_n, stats, out_depth)
+    o = _opts(precision, out_pq, out_T, out_n, stats, out_depth, out_normal, out_rgba8, exposure_ev)
     _check(load().vrnerf_render_rays(field.h, _ptr(_dev(rays_o)), _ptr(_dev(rays_d)),
                                      _ptr(_dev(radii)), B, _ptr(_dev(out)), ctypes.byref(o),
                                      _stream(stream)))

@@ -28,6 +28,11 @@ Parity status per function (what pins it, see tests/test_oracle_*.py):
   upsample_occupancy      brute-force child-to-parent loop on a tiny grid
   density_grad / normals  central differences of sigma in fp64; a field whose density
                           grows along one axis gives normals -axis, composited to (1 - T)
+  grid_position / uncontract / footprint (contracted scenes)
+                          closed-form contractions on and off the axes, continuity at the
+                          inner cube, round trip through the inverse, first-order footprint
+                          against finite differences of the contraction, det(J)^(1/3)
+                          against a finite-difference Jacobian, contracted march by brute force
   tonemap                 sRGB anchors of IEC 61966-2-1 at PQ inputs of known luminance,
                           exposure doubling, coverage from T
 Parity unpinned: the appearance of a random field (nothing in the paper fixes it).
@@ -74,6 +79,7 @@ class Desc(ctypes.Structure):
         ("t_near", ctypes.c_float), ("t_far", ctypes.c_float),
         ("lod_bias", ctypes.c_double), ("T_eps", ctypes.c_double),
         ("radius_scale", ctypes.c_double), ("density_bias", ctypes.c_double),
+        ("contract", ctypes.c_int32), ("pad", ctypes.c_int32),
     ]
 
 
@@ -90,6 +96,7 @@ def desc(cfg) -> Desc:
     d.t_near, d.t_far = float(np.float32(cfg.t_near)), float(np.float32(cfg.t_far))
     d.lod_bias, d.T_eps = cfg.lod_bias, cfg.T_eps
     d.radius_scale, d.density_bias = cfg.radius_scale, cfg.density_bias
+    d.contract = int(getattr(cfg, "contract", False))
     return d
 
 
@@ -128,6 +135,14 @@ def lib():
                 "orc_render_rays": (None, [_DP, _F64, _F64, _U32, _F32, _F32, _F32,
                                            ctypes.c_int32, _F64, _F64, _F64, _I32, _F64, _F64,
                                            ctypes.c_int32]),
+                "orc_render_rays_adjacent": (None, [_DP, _F64, _F64, _U32, _F32, _F32, _F32, _F64,
+                                                    _F64, ctypes.c_int32, _F64, _F64, _F64, _I32,
+                                                    _F64, _F64, ctypes.c_int32]),
+                "orc_grid_position": (None, [_DP, _F32, ctypes.c_int32, _F32]),
+                "orc_uncontract": (ctypes.c_int32, [_F64, _F64]),
+                "orc_footprint": (ctypes.c_double, [_DP, _F64, _F64, ctypes.c_float, _F32,
+                                                    ctypes.c_double]),
+                "orc_camera_adjacent": (None, [_F32, _F32, _I32, ctypes.c_int32, _F64, _F64]),
                 "orc_density_grad": (None, [_DP, _F64, _F64, _F32, _F64, ctypes.c_int32, _F64,
                                             _F64]),
                 "orc_tonemap": (None, [_F64, _F64, ctypes.c_int64, ctypes.c_double, _U32, _F64]),
@@ -241,6 +256,48 @@ def camera_rays(cfg, c2w, K, res):
     return o, dd, r
 
 
+def grid_position(cfg, pos):
+    """Normalised grid position in [0, 1]^3 (fp32) of world points [n][3]:
+    scaled box, or the contracted cube of an unbounded scene."""
+    pos = _f32(pos).reshape(-1, 3)
+    ph = np.zeros_like(pos)
+    lib().orc_grid_position(ctypes.byref(desc(cfg)), _p(pos, ctypes.c_float), pos.shape[0],
+                            _p(ph, ctypes.c_float))
+    return ph
+
+
+def uncontract(y):
+    """Pre-image of a contracted point (fp64), None at |y|_inf >= 2."""
+    y = _f64(y).reshape(3)
+    x = np.zeros(3)
+    ok = lib().orc_uncontract(_p(y, ctypes.c_double), _p(x, ctypes.c_double))
+    return x if ok else None
+
+
+def footprint(cfg, p, t, r, adjacent=None):
+    """Normalised footprint radius of the sample at distance t and position p
+    (adjacent = (du, dv) for a camera ray of a contracted scene)."""
+    p = _f32(p).reshape(3)
+    du, dv = (None, None) if adjacent is None else (_f64(a).reshape(3) for a in adjacent)
+    return lib().orc_footprint(ctypes.byref(desc(cfg)), _p(du, ctypes.c_double),
+                               _p(dv, ctypes.c_double), float(np.float32(t)),
+                               _p(p, ctypes.c_float), float(r))
+
+
+def camera_adjacent(c2w, K, res):
+    """Per camera ray: offsets du, dv [total][3] to the directions of the
+    pixels to the right and below (fp32 directions, difference in fp64)."""
+    c2w, K = _f32(c2w).reshape(-1, 3, 4), _f32(K).reshape(-1, 4)
+    res = _i32(res).reshape(-1, 2)
+    total = int((res[:, 0].astype(np.int64) * res[:, 1]).sum())
+    du = np.zeros((total, 3), np.float64)
+    dv = np.zeros((total, 3), np.float64)
+    lib().orc_camera_adjacent(_p(c2w, ctypes.c_float), _p(K, ctypes.c_float),
+                              _p(res, ctypes.c_int32), res.shape[0], _p(du, ctypes.c_double),
+                              _p(dv, ctypes.c_double))
+    return du, dv
+
+
 def corners(cfg, pos):
     pos = _f32(pos).reshape(-1, 3)
     n = pos.shape[0]
@@ -292,7 +349,9 @@ class Field:
                         _p(feat, ctypes.c_double))
         return sig, rgb, feat
 
-    def render_rays(self, o, dd, r, threads=None, normals=False):
+    def render_rays(self, o, dd, r, threads=None, normals=False, adjacent=None):
+        """adjacent = (du, dv) [B][3] direction offsets to the adjacent pixels'
+        rays (the camera-ray footprint of a contracted scene), else None."""
         o, dd, r = _f32(o).reshape(-1, 3), _f32(dd).reshape(-1, 3), _f32(r).reshape(-1)
         B = o.shape[0]
         pq = np.zeros((B, 3), np.float64)
@@ -301,12 +360,19 @@ class Field:
         n = np.zeros(B, np.int32)
         depth = np.zeros(B, np.float64)
         nrm = np.zeros((B, 3), np.float64) if normals else None
-        lib().orc_render_rays(*self._args(), _p(self.occ, ctypes.c_uint32),
-                              _p(o, ctypes.c_float), _p(dd, ctypes.c_float),
-                              _p(r, ctypes.c_float), B, _p(pq, ctypes.c_double),
-                              _p(lin, ctypes.c_double), _p(T, ctypes.c_double),
-                              _p(n, ctypes.c_int32), _p(depth, ctypes.c_double),
-                              _p(nrm, ctypes.c_double), threads or os.cpu_count() or 1)
+        outs = (_p(pq, ctypes.c_double), _p(lin, ctypes.c_double), _p(T, ctypes.c_double),
+                _p(n, ctypes.c_int32), _p(depth, ctypes.c_double), _p(nrm, ctypes.c_double),
+                threads or os.cpu_count() or 1)
+        if adjacent is None:
+            lib().orc_render_rays(*self._args(), _p(self.occ, ctypes.c_uint32),
+                                  _p(o, ctypes.c_float), _p(dd, ctypes.c_float),
+                                  _p(r, ctypes.c_float), B, *outs)
+        else:
+            du, dv = (_f64(a).reshape(-1, 3) for a in adjacent)
+            lib().orc_render_rays_adjacent(*self._args(), _p(self.occ, ctypes.c_uint32),
+                                           _p(o, ctypes.c_float), _p(dd, ctypes.c_float),
+                                           _p(r, ctypes.c_float), _p(du, ctypes.c_double),
+                                           _p(dv, ctypes.c_double), B, *outs)
         out = dict(pq=pq, linear=lin, T=T, n=n, depth=depth)
         if normals:
             out["normal"] = nrm
@@ -314,7 +380,8 @@ class Field:
 
     def render(self, c2w, K, res, threads=None, normals=False):
         o, dd, r = camera_rays(self.cfg, c2w, K, res)
-        return self.render_rays(o, dd, r, threads, normals)
+        adj = camera_adjacent(c2w, K, res) if getattr(self.cfg, "contract", False) else None
+        return self.render_rays(o, dd, r, threads, normals, adj)
 
     def density_grad(self, pos, radius):
         """sigma [n] and d sigma / d position [n][3] at a fixed footprint."""

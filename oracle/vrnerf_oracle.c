@@ -52,6 +52,8 @@ typedef struct {
     int32_t max_steps;
     float t_near, t_far;
     double lod_bias, T_eps, radius_scale, density_bias;
+    int32_t contract; /* 1: unbounded scene, L-infinity contraction (Sec. 4) */
+    int32_t pad;
 } orc_desc;
 
 /* ------------------------------------------------------------------------
@@ -138,6 +140,8 @@ void orc_sample_table(const orc_desc *D, float *t)
 
 typedef struct {
     float mn[3], inv_cell[3], inv_ext;
+    float cen[3], inv_h; /* contraction: x = (p - cen) inv_h, inner cube |x|_inf <= 1 */
+    int32_t contract;
     int32_t N[ORC_MAX_LEVELS], dense[ORC_MAX_LEVELS];
     uint32_t T;
 } orc_geom;
@@ -152,6 +156,10 @@ static void geom_init(const orc_desc *D, orc_geom *g)
         if (ext > ext_max) ext_max = ext;
     }
     g->inv_ext = (float)(1.0 / ext_max);
+    g->contract = D->contract;
+    for (int k = 0; k < 3; ++k)
+        g->cen[k] = (float)(0.5 * ((double)D->aabb_min[k] + (double)D->aabb_max[k]));
+    g->inv_h = (float)(2.0 / ext_max);
     for (int32_t l = 0; l < D->levels; ++l) {
         g->N[l] = orc_level_res(D, l);
         g->dense[l] = orc_level_dense(D, l);
@@ -174,20 +182,126 @@ void orc_ray(const float *c2w, const float *K, int32_t u, int32_t v, float *o, f
     }
 }
 
+/* Cubic space contraction with the L-infinity norm (Sec. 4, unbounded
+ * scenes): with m = |x|_inf, C(x) = x for m <= 1, else (2 - 1/m) x / m, so
+ * the whole space maps into the cube |y|_inf < 2 and the inner cube stays
+ * as it is. fp32 with every operation rounded on its own (voxel decisions):
+ * s = (2 - 1/m) (1/m), y = x s. */
+static float linf(const float *x)
+{
+    float m = fabsf(x[0]);
+    if (fabsf(x[1]) > m) m = fabsf(x[1]);
+    if (fabsf(x[2]) > m) m = fabsf(x[2]);
+    return m;
+}
+
+static void contract_pt(const float *x, float *y)
+{
+    float m = linf(x);
+    if (m <= 1.0f) {
+        for (int k = 0; k < 3; ++k) y[k] = x[k];
+        return;
+    }
+    float inv = 1.0f / m;
+    float sc = (2.0f - inv) * inv;
+    for (int k = 0; k < 3; ++k) y[k] = x[k] * sc;
+}
+
+/* Normalised grid position in [0, 1]^3 of world position p: the scene box
+ * scaled by its largest extent, or (contracted scenes) the contracted point
+ * of the cube [-2, 2]^3, ph = y / 4 + 1/2. */
+static void grid_ph(const orc_geom *g, const float *p, float *ph)
+{
+    if (!g->contract) {
+        for (int k = 0; k < 3; ++k) ph[k] = (p[k] - g->mn[k]) * g->inv_ext;
+        return;
+    }
+    float x[3], y[3];
+    for (int k = 0; k < 3; ++k) x[k] = (p[k] - g->cen[k]) * g->inv_h;
+    contract_pt(x, y);
+    for (int k = 0; k < 3; ++k) ph[k] = y[k] * 0.25f + 0.5f;
+}
+
 /* Sample position p = o + t d and its occupancy voxel, fp32. Returns 0 when
- * any voxel coordinate falls outside [0, res): the march ends there. */
+ * any voxel coordinate falls outside [0, res): the march ends there. The
+ * grid of a contracted scene covers all of space: its coordinates are
+ * clamped to the last voxel (reached only where 2 - 1/m rounds to 2). */
 static int sample_voxel(const orc_desc *D, const orc_geom *g, const float *o, const float *d,
                         float t, float *p, int32_t *vox)
 {
     int32_t v[3];
-    for (int k = 0; k < 3; ++k) {
-        p[k] = o[k] + t * d[k];
-        float gk = (p[k] - g->mn[k]) * g->inv_cell[k];
-        if (!(gk >= 0.0f) || !(gk < (float)D->occ_res[k])) return 0;
-        v[k] = (int32_t)floorf(gk);
+    for (int k = 0; k < 3; ++k) p[k] = o[k] + t * d[k];
+    if (g->contract) {
+        float ph[3];
+        grid_ph(g, p, ph);
+        for (int k = 0; k < 3; ++k) {
+            float gk = ph[k] * (float)D->occ_res[k];
+            int32_t c = (int32_t)floorf(gk);
+            v[k] = c < 0 ? 0 : (c > D->occ_res[k] - 1 ? D->occ_res[k] - 1 : c);
+        }
+    } else {
+        for (int k = 0; k < 3; ++k) {
+            float gk = (p[k] - g->mn[k]) * g->inv_cell[k];
+            if (!(gk >= 0.0f) || !(gk < (float)D->occ_res[k])) return 0;
+            v[k] = (int32_t)floorf(gk);
+        }
     }
     *vox = v[0] + D->occ_res[0] * (v[1] + D->occ_res[1] * v[2]);
     return 1;
+}
+
+/* Contraction Jacobian applied to a vector, fp64: J v = v inside the inner
+ * cube, else s v + s'(m) x sign(x_k) v_k with s(m) = 2/m - 1/m^2 and k the
+ * axis of the largest |x_k| (the first one on ties). */
+static void contract_jv(const double *x, const double *v, double *out)
+{
+    double m = fabs(x[0]);
+    int k = 0;
+    for (int a = 1; a < 3; ++a)
+        if (fabs(x[a]) > m) {
+            m = fabs(x[a]);
+            k = a;
+        }
+    if (m <= 1.0) {
+        for (int a = 0; a < 3; ++a) out[a] = v[a];
+        return;
+    }
+    const double sc = 2.0 / m - 1.0 / (m * m), ds = -2.0 / (m * m) + 2.0 / (m * m * m);
+    const double vk = x[k] >= 0.0 ? v[k] : -v[k];
+    for (int a = 0; a < 3; ++a) out[a] = sc * v[a] + ds * x[a] * vk;
+}
+
+/* Footprint radius in normalised grid units at distance t (Sec. 4.2.1).
+ * Plain scenes: t r / max extent. Contracted scenes, camera rays (du, dv: the
+ * direction of the pixel to the right and below minus the ray's own): the
+ * distance between the sample and the corresponding samples of the two
+ * adjacent rays in contracted space, to first order |J_C (t du inv_h)|,
+ * averaged, times radius_scale (so that it is t r without contraction), over
+ * 4 (the cube [-2, 2] spans the unit grid). Contracted scenes, explicit rays:
+ * t r inv_h det(J_C)^(1/3) / 4, with det(J_C)^(1/3) = (2m - 1)^(2/3) / m^2
+ * for m = |x|_inf > 1. */
+static double footprint(const orc_desc *D, const orc_geom *g, const double *du, const double *dv,
+                        float t, const float *p, double r)
+{
+    if (!g->contract) return (double)t * r * (double)g->inv_ext;
+    double x[3], m = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        x[k] = ((double)p[k] - (double)g->cen[k]) * (double)g->inv_h;
+        if (fabs(x[k]) > m) m = fabs(x[k]);
+    }
+    if (du && dv) {
+        double acc = 0.0;
+        for (int a = 0; a < 2; ++a) {
+            const double *da = a ? dv : du;
+            double v[3], jv[3];
+            for (int k = 0; k < 3; ++k) v[k] = (double)t * da[k] * (double)g->inv_h;
+            contract_jv(x, v, jv);
+            acc += sqrt(jv[0] * jv[0] + jv[1] * jv[1] + jv[2] * jv[2]);
+        }
+        return D->radius_scale * 0.5 * acc * 0.25;
+    }
+    double j = m <= 1.0 ? 1.0 : pow(2.0 * m - 1.0, 2.0 / 3.0) / (m * m);
+    return (double)t * r * (double)g->inv_h * j * 0.25;
 }
 
 static int occupied(const uint32_t *occ, int32_t vox)
@@ -202,8 +316,10 @@ static void level_corners(const orc_geom *g, int32_t l, const float *p, uint32_t
 {
     int32_t N = g->N[l];
     int32_t c0[3];
+    float phv[3];
+    grid_ph(g, p, phv);
     for (int k = 0; k < 3; ++k) {
-        float ph = (p[k] - g->mn[k]) * g->inv_ext;
+        float ph = phv[k];
         float x = ph * (float)N;
         int32_t c = (int32_t)floorf(x);
         if (c < 0) c = 0;
@@ -416,7 +532,7 @@ static void density_grad(const orc_desc *D, const orc_geom *g, const double *gri
         uint32_t idx[8];
         float fr[3];
         level_corners(g, l, p, idx, fr);
-        const double dxdp = (double)g->N[l] * (double)g->inv_ext;
+        const double dxdp = (double)g->N[l]; /* d (level coordinate) / d ph */
         for (int b = 0; b < 8; ++b) {
             const double *e = grid + ((int64_t)l * g->T + idx[b]) * F;
             for (int k = 0; k < 3; ++k) {
@@ -440,8 +556,34 @@ static void density_grad(const orc_desc *D, const orc_geom *g, const double *gri
             }
             if (pre > 0.0) do0 += W2[j] * dpre;
         }
-        grad[k] = s->sigma * do0;
+        grad[k] = s->sigma * do0; /* d sigma / d ph_k */
     }
+    /* chain to the world position: d ph / d p = inv_ext I, or for a
+     * contracted scene inv_h J_C(x) / 4 (grad_p = (d ph / d p)^T grad_ph) */
+    if (!g->contract) {
+        for (int k = 0; k < 3; ++k) grad[k] *= (double)g->inv_ext;
+        return;
+    }
+    double x[3], m = 0.0;
+    int kk = 0;
+    for (int k = 0; k < 3; ++k) {
+        x[k] = ((double)p[k] - (double)g->cen[k]) * (double)g->inv_h;
+        if (fabs(x[k]) > m) {
+            m = fabs(x[k]);
+            kk = k;
+        }
+    }
+    const double sc = 0.25 * (double)g->inv_h;
+    if (m <= 1.0) {
+        for (int k = 0; k < 3; ++k) grad[k] *= sc;
+        return;
+    }
+    const double s0 = 2.0 / m - 1.0 / (m * m), ds = -2.0 / (m * m) + 2.0 / (m * m * m);
+    double gx = 0.0;
+    for (int b = 0; b < 3; ++b) gx += grad[b] * x[b];
+    for (int k = 0; k < 3; ++k) grad[k] *= s0;
+    grad[kk] += (x[kk] >= 0.0 ? ds : -ds) * gx;
+    for (int k = 0; k < 3; ++k) grad[k] *= sc;
 }
 
 /* sigma and its position gradient at n points (footprint radius in world
@@ -454,7 +596,7 @@ void orc_density_grad(const orc_desc *D, const double *grid, const double *mlp, 
     const double dir[3] = {0.0, 0.0, 1.0};
     for (int32_t i = 0; i < n; ++i) {
         orc_sample s;
-        sample_feats(D, &g, grid, pos + 3 * i, radius[i] * (double)g.inv_ext, &s);
+        sample_feats(D, &g, grid, pos + 3 * i, footprint(D, &g, NULL, NULL, 1.0f, pos + 3 * i, radius[i]), &s);
         mlp_forward(D, mlp, dir, &s);
         sigma[i] = s.sigma;
         density_grad(D, &g, grid, mlp, pos + 3 * i, &s, grad + 3 * i);
@@ -472,7 +614,7 @@ void orc_query(const orc_desc *D, const double *grid, const double *mlp, const f
     int din = D->levels * D->feats;
     for (int32_t i = 0; i < n; ++i) {
         orc_sample s;
-        sample_feats(D, &g, grid, pos + 3 * i, radius[i] * (double)g.inv_ext, &s);
+        sample_feats(D, &g, grid, pos + 3 * i, footprint(D, &g, NULL, NULL, 1.0f, pos + 3 * i, radius[i]), &s);
         mlp_forward(D, mlp, dir + 3 * i, &s);
         sigma[i] = s.sigma;
         for (int c = 0; c < 3; ++c) rgb[3 * i + c] = s.c[c];
@@ -500,7 +642,8 @@ typedef struct {
 
 static void render_one(const orc_desc *D, const orc_geom *g, const double *grid, const double *mlp,
                        const uint32_t *occ, const float *t_tab, const float *o, const float *d,
-                       double r, orc_ray_out *out, orc_tape *tape, int normals)
+                       double r, const double *du, const double *dv, orc_ray_out *out,
+                       orc_tape *tape, int normals)
 {
     double dir[3] = {d[0], d[1], d[2]};
     double T = 1.0, C[3] = {0, 0, 0}, depth = 0.0, Nrm[3] = {0, 0, 0};
@@ -512,7 +655,7 @@ static void render_one(const orc_desc *D, const orc_geom *g, const double *grid,
         if (!occupied(occ, vox)) continue;
         double t = (double)t_tab[i];
         double delta = (double)t_tab[i + 1] - (double)t_tab[i];
-        double r_norm = t * r * (double)g->inv_ext;
+        double r_norm = footprint(D, g, du, dv, t_tab[i], p, r);
         orc_sample s;
         sample_feats(D, g, grid, p, r_norm, &s);
         mlp_forward(D, mlp, dir, &s);
@@ -548,14 +691,11 @@ static void render_one(const orc_desc *D, const orc_geom *g, const double *grid,
     out->n_eval = n;
 }
 
-/* Explicit rays: o, d [B][3] fp32, r [B] (base radius at unit distance).
- * Outputs (any may be NULL): PQ colour [B][3], linear colour [B][3],
- * final transmittance [B], composited sample count [B], expected depth
- * sum_i w_i t_i [B]. */
-void orc_render_rays(const orc_desc *D, const double *grid, const double *mlp, const uint32_t *occ,
-                     const float *o, const float *d, const float *r, int32_t B, double *out_pq,
-                     double *out_lin, double *out_T, int32_t *out_n, double *out_depth,
-                     double *out_normal, int32_t threads)
+static void render_rays_impl(const orc_desc *D, const double *grid, const double *mlp,
+                             const uint32_t *occ, const float *o, const float *d, const float *r,
+                             const double *du, const double *dv, int32_t B, double *out_pq,
+                             double *out_lin, double *out_T, int32_t *out_n, double *out_depth,
+                             double *out_normal, int32_t threads)
 {
     orc_geom g;
     geom_init(D, &g);
@@ -564,8 +704,8 @@ void orc_render_rays(const orc_desc *D, const double *grid, const double *mlp, c
 #pragma omp parallel for schedule(dynamic, 16) num_threads(threads > 0 ? threads : 1)
     for (int32_t i = 0; i < B; ++i) {
         orc_ray_out ro;
-        render_one(D, &g, grid, mlp, occ, t_tab, o + 3 * i, d + 3 * i, (double)r[i], &ro, NULL,
-                   out_normal != NULL);
+        render_one(D, &g, grid, mlp, occ, t_tab, o + 3 * i, d + 3 * i, (double)r[i],
+                   du ? du + 3 * i : NULL, dv ? dv + 3 * i : NULL, &ro, NULL, out_normal != NULL);
         for (int c = 0; c < 3; ++c) {
             if (out_pq) out_pq[3 * i + c] = ro.C[c];
             if (out_lin) out_lin[3 * i + c] = orc_pq_to_linear(ro.C[c]);
@@ -576,6 +716,55 @@ void orc_render_rays(const orc_desc *D, const double *grid, const double *mlp, c
         if (out_depth) out_depth[i] = ro.depth;
     }
     free(t_tab);
+}
+
+/* Explicit rays: o, d [B][3] fp32, r [B] (base radius at unit distance).
+ * Outputs (any may be NULL): PQ colour [B][3], linear colour [B][3],
+ * final transmittance [B], composited sample count [B], expected depth
+ * sum_i w_i t_i [B], composited normal [B][3]. */
+void orc_render_rays(const orc_desc *D, const double *grid, const double *mlp, const uint32_t *occ,
+                     const float *o, const float *d, const float *r, int32_t B, double *out_pq,
+                     double *out_lin, double *out_T, int32_t *out_n, double *out_depth,
+                     double *out_normal, int32_t threads)
+{
+    render_rays_impl(D, grid, mlp, occ, o, d, r, NULL, NULL, B, out_pq, out_lin, out_T, out_n,
+                     out_depth, out_normal, threads);
+}
+
+/* Camera rays of a contracted scene: as orc_render_rays plus, per ray, the
+ * direction offsets du, dv [B][3] to the adjacent pixels' rays, which set
+ * the footprint in contracted space. */
+void orc_render_rays_adjacent(const orc_desc *D, const double *grid, const double *mlp,
+                              const uint32_t *occ, const float *o, const float *d, const float *r,
+                              const double *du, const double *dv, int32_t B, double *out_pq,
+                              double *out_lin, double *out_T, int32_t *out_n, double *out_depth,
+                              double *out_normal, int32_t threads)
+{
+    render_rays_impl(D, grid, mlp, occ, o, d, r, du, dv, B, out_pq, out_lin, out_T, out_n,
+                     out_depth, out_normal, threads);
+}
+
+/* Direction offsets to the adjacent pixels' rays, du = d(u + 1, v) - d(u, v)
+ * and dv = d(u, v + 1) - d(u, v), per pixel in orc_camera_rays order (the
+ * difference of the fp32 directions, taken in fp64). */
+void orc_camera_adjacent(const float *c2w, const float *K, const int32_t *res, int32_t n_views,
+                         double *du, double *dv)
+{
+    int64_t q = 0;
+    for (int32_t v = 0; v < n_views; ++v) {
+        int32_t W = res[2 * v], H = res[2 * v + 1];
+        for (int32_t y = 0; y < H; ++y)
+            for (int32_t x = 0; x < W; ++x, ++q) {
+                float o[3], d0[3], d1[3], d2[3];
+                orc_ray(c2w + 12 * v, K + 4 * v, x, y, o, d0);
+                orc_ray(c2w + 12 * v, K + 4 * v, x + 1, y, o, d1);
+                orc_ray(c2w + 12 * v, K + 4 * v, x, y + 1, o, d2);
+                for (int k = 0; k < 3; ++k) {
+                    du[3 * q + k] = (double)d1[k] - (double)d0[k];
+                    dv[3 * q + k] = (double)d2[k] - (double)d0[k];
+                }
+            }
+    }
 }
 
 /* Cameras c2w [n][3][4], K [n][4], res [n][2] = (W, H). Pixels of view v are
@@ -601,8 +790,16 @@ void orc_render(const orc_desc *D, const double *grid, const double *mlp, const 
                 r[q] = rr;
             }
     }
-    orc_render_rays(D, grid, mlp, occ, o, d, r, (int32_t)total, out_pq, out_lin, out_T, out_n,
-                    out_depth, NULL, threads);
+    double *du = NULL, *dv = NULL;
+    if (D->contract) {
+        du = (double *)malloc(sizeof(double) * 3 * total);
+        dv = (double *)malloc(sizeof(double) * 3 * total);
+        orc_camera_adjacent(c2w, K, res, n_views, du, dv);
+    }
+    render_rays_impl(D, grid, mlp, occ, o, d, r, du, dv, (int32_t)total, out_pq, out_lin, out_T,
+                     out_n, out_depth, NULL, threads);
+    free(du);
+    free(dv);
     free(o);
     free(d);
     free(r);
@@ -737,7 +934,7 @@ double orc_backward(const orc_desc *D, const double *grid, const double *mlp, co
         const float *oi = o + 3 * i, *di = d + 3 * i;
         double dir[3] = {di[0], di[1], di[2]};
         orc_ray_out ro;
-        render_one(D, &g, grid, mlp, occ, t_tab, oi, di, (double)r[i], &ro, tape, 0);
+        render_one(D, &g, grid, mlp, occ, t_tab, oi, di, (double)r[i], NULL, NULL, &ro, tape, 0);
         double gC[3];
         for (int c = 0; c < 3; ++c) {
             double tgt = orc_linear_to_pq((double)target_lin[3 * i + c]);
@@ -802,6 +999,19 @@ void orc_adam(double *param, const double *grad, double *m, double *v, int64_t n
  * A voxel stays occupied iff it was occupied and alpha_grid >= threshold or
  * hist >= threshold. keep_out [voxels] (0/1), alpha_out [voxels] (may be NULL).
  * --------------------------------------------------------------------- */
+/* Inverse contraction, fp64: y with m = |y|_inf <= 1 is its own pre-image,
+ * 1 < m < 2 comes from x = y / (m (2 - m)); returns 0 for m >= 2 (infinity). */
+static int uncontract(const double *y, double *x)
+{
+    double m = fabs(y[0]);
+    if (fabs(y[1]) > m) m = fabs(y[1]);
+    if (fabs(y[2]) > m) m = fabs(y[2]);
+    if (m >= 2.0) return 0;
+    const double sc = m <= 1.0 ? 1.0 : 1.0 / (m * (2.0 - m));
+    for (int a = 0; a < 3; ++a) x[a] = y[a] * sc;
+    return 1;
+}
+
 static double box_distance(const double *c, const double *lo, const double *hi)
 {
     double s = 0.0;
@@ -840,22 +1050,75 @@ void orc_prune(const orc_desc *D, const double *grid, const double *mlp, const u
                     lo[a] = D->aabb_min[a] + vv[a] * cell[a];
                     hi[a] = lo[a] + cell[a];
                 }
-                double sig_max = 0.0;
+                double sig_max = 0.0, dmin = INFINITY;
                 for (int32_t i = 0; i < k * k * k; ++i) {
                     const int32_t j[3] = {i % k, (i / k) % k, i / (k * k)};
                     float p[3];
-                    for (int a = 0; a < 3; ++a) p[a] = (float)(lo[a] + (j[a] + 0.5) / k * cell[a]);
+                    if (g.contract) {
+                        double y[3];
+                        for (int a = 0; a < 3; ++a)
+                            y[a] = 4.0 * (vv[a] + (j[a] + 0.5) / k) / D->occ_res[a] - 2.0;
+                        double x[3];
+                        uncontract(y, x);
+                        for (int a = 0; a < 3; ++a) p[a] = (float)(g.cen[a] + x[a] / (double)g.inv_h);
+                        for (int32_t c = 0; c < n_cams; ++c) {
+                            double s2 = 0.0;
+                            for (int a = 0; a < 3; ++a) {
+                                double e = (double)p[a] - (double)cams[3 * c + a];
+                                s2 += e * e;
+                            }
+                            if (sqrt(s2) < dmin) dmin = sqrt(s2);
+                        }
+                    } else {
+                        for (int a = 0; a < 3; ++a) p[a] = (float)(lo[a] + (j[a] + 0.5) / k * cell[a]);
+                    }
                     orc_sample s;
                     sample_feats(D, &g, grid, p, 0.0, &s);
                     const double dir[3] = {0.0, 0.0, 1.0};
                     mlp_forward(D, mlp, dir, &s);
                     if (s.sigma > sig_max) sig_max = s.sigma;
                 }
-                double dmin = INFINITY;
-                for (int32_t c = 0; c < n_cams; ++c) {
-                    const double cc[3] = {cams[3 * c], cams[3 * c + 1], cams[3 * c + 2]};
-                    const double dd = box_distance(cc, lo, hi);
-                    if (dd < dmin) dmin = dd;
+                if (g.contract) {
+                    /* distance to the voxel's world region: exact for a voxel of
+                     * the inner cube (its pre-image is a box), else the smallest
+                     * distance to a lattice point or a finite corner pre-image */
+                    double ylo[3], yhi[3], clo[3], chi[3];
+                    int inner = 1;
+                    for (int a = 0; a < 3; ++a) {
+                        ylo[a] = 4.0 * vv[a] / D->occ_res[a] - 2.0;
+                        yhi[a] = 4.0 * (vv[a] + 1) / D->occ_res[a] - 2.0;
+                        if (ylo[a] < -1.0 || yhi[a] > 1.0) inner = 0;
+                        clo[a] = g.cen[a] + ylo[a] / (double)g.inv_h;
+                        chi[a] = g.cen[a] + yhi[a] / (double)g.inv_h;
+                    }
+                    if (inner) {
+                        dmin = INFINITY;
+                        for (int32_t c = 0; c < n_cams; ++c) {
+                            const double cc[3] = {cams[3 * c], cams[3 * c + 1], cams[3 * c + 2]};
+                            const double dd = box_distance(cc, clo, chi);
+                            if (dd < dmin) dmin = dd;
+                        }
+                    } else {
+                        for (int b = 0; b < 8; ++b) {
+                            double y[3], x[3];
+                            for (int a = 0; a < 3; ++a) y[a] = ((b >> a) & 1) ? yhi[a] : ylo[a];
+                            if (!uncontract(y, x)) continue;
+                            for (int32_t c = 0; c < n_cams; ++c) {
+                                double s2 = 0.0;
+                                for (int a = 0; a < 3; ++a) {
+                                    double e = g.cen[a] + x[a] / (double)g.inv_h - (double)cams[3 * c + a];
+                                    s2 += e * e;
+                                }
+                                if (sqrt(s2) < dmin) dmin = sqrt(s2);
+                            }
+                        }
+                    }
+                } else {
+                    for (int32_t c = 0; c < n_cams; ++c) {
+                        const double cc[3] = {cams[3 * c], cams[3 * c + 1], cams[3 * c + 2]};
+                        const double dd = box_distance(cc, lo, hi);
+                        if (dd < dmin) dmin = dd;
+                    }
                 }
                 /* spacing of the sample interval holding distance dmin */
                 int32_t i = 0;
@@ -881,7 +1144,7 @@ void orc_history(const orc_desc *D, const double *grid, const double *mlp, const
     orc_tape *tape = (orc_tape *)malloc(sizeof(orc_tape) * D->max_steps);
     for (int32_t b = 0; b < B; ++b) {
         orc_ray_out ro;
-        render_one(D, &g, grid, mlp, occ, t_tab, o + 3 * b, d + 3 * b, (double)r[b], &ro, tape, 0);
+        render_one(D, &g, grid, mlp, occ, t_tab, o + 3 * b, d + 3 * b, (double)r[b], NULL, NULL, &ro, tape, 0);
         for (int32_t k = 0; k < ro.n_eval; ++k) {
             const float *p = tape[k].p;
             /* voxel of the composited sample */
@@ -933,6 +1196,27 @@ void orc_tonemap(const double *pq, const double *T, int64_t n, double ev, uint32
         }
         rgba[i] = word;
     }
+}
+
+/* Introspection for the tests: normalised grid positions [n][3] (fp32, as
+ * the march and the hash grid see them), inverse contraction [n][3] of
+ * contracted points (fp64; 0 where |y|_inf >= 2), footprint radius of one
+ * sample (du, dv may be NULL). */
+void orc_grid_position(const orc_desc *D, const float *pos, int32_t n, float *ph)
+{
+    orc_geom g;
+    geom_init(D, &g);
+    for (int32_t i = 0; i < n; ++i) grid_ph(&g, pos + 3 * i, ph + 3 * i);
+}
+
+int32_t orc_uncontract(const double *y, double *x) { return uncontract(y, x); }
+
+double orc_footprint(const orc_desc *D, const double *du, const double *dv, float t, const float *p,
+                     double r)
+{
+    orc_geom g;
+    geom_init(D, &g);
+    return footprint(D, &g, du, dv, t, p, r);
 }
 
 /* Introspection for the tests. */

@@ -94,6 +94,7 @@ class FieldConfig:
     density_bias: float = 0.0
     feat_lo: float = -1e-2
     feat_hi: float = 1e-2
+    contract: bool = False  # unbounded scene: L-infinity contraction around the box (Sec. 4)
 
     @property
     def d_in(self) -> int:

@@ -709,3 +709,160 @@ def test_tonemap_srgb_anchors_exposure_and_coverage():
     rgba3, _ = O.tonemap([[1.0, 0.0, 0.5]], T=[0.25], ev=0.0)
     assert int(rgba3[0]) & 255 == 255 and (int(rgba3[0]) >> 8) & 255 == 0
     assert int(rgba3[0]) >> 24 == int(np.floor(0.75 * 255 + 0.5))
+
+
+# ----------------------------------------------------------------------------
+# Unbounded scenes: L-infinity contraction (Sec. 4) and the contracted
+# footprint (Sec. 4.2.1)
+# ----------------------------------------------------------------------------
+def _contracted_cfg(**kw):
+    # unit box: centre 0.5, x = 2 (p - 0.5), so the inner cube is the box itself
+    return replace(S.cfg_unit_cube(), contract=True, t_far=1000.0, max_steps=256, **kw)
+
+
+def test_contraction_closed_forms():
+    cfg = _contracted_cfg()
+    x = np.array([[0.0, 0.0, 0.0], [0.5, -0.25, 1.0], [2.0, 0.0, 0.0], [-4.0, 1.0, 0.5],
+                  [3.0, 1.5, 0.0], [0.0, 0.0, -1e4]])
+    # (2 - 1/m) x / m beyond the inner cube, identity inside
+    want = []
+    for v in x:
+        m = np.abs(v).max()
+        want.append(v if m <= 1 else (2 - 1 / m) * v / m)
+    want = np.array(want) / 4 + 0.5
+    ph = O.grid_position(cfg, (x / 2 + 0.5).astype(np.float32))
+    np.testing.assert_allclose(ph, want, atol=2e-7)
+    # specific values: x = (2, 0, 0) -> y_x = 1.5; (3, 1.5, 0) -> (5/3, 5/6, 0)
+    assert ph[2, 0] == pytest.approx(0.875, abs=1e-7)
+    np.testing.assert_allclose(ph[4], [5 / 12 + 0.5, 5 / 24 + 0.5, 0.5], atol=2e-7)
+
+
+def test_contraction_continuous_bounded_monotone():
+    cfg = _contracted_cfg()
+    rng = np.random.default_rng(1)
+    d = rng.normal(size=(50, 3))
+    d /= np.abs(d).max(axis=1, keepdims=True)  # |d|_inf = 1
+    s = np.concatenate([np.linspace(0, 3, 301), np.geomspace(3, 1e5, 200)])
+    for v in d:
+        p = (0.5 + 0.5 * s[:, None] * v[None, :]).astype(np.float32)
+        ph = O.grid_position(cfg, p).astype(np.float64)
+        y = 4 * ph - 2
+        assert (np.abs(y) <= 2).all()
+        r = np.abs(y).max(axis=1)
+        assert (np.diff(r) >= -1e-6).all()                  # monotone along the ray
+        np.testing.assert_allclose(r[s <= 1], s[s <= 1], atol=1e-6)  # identity inside
+        k = np.searchsorted(s, 1.0)
+        assert abs(r[k + 1] - r[k]) < 0.02                  # continuous at the inner cube
+
+
+def test_uncontract_round_trip():
+    rng = np.random.default_rng(2)
+    for _ in range(200):
+        x = rng.normal(size=3) * rng.choice([0.3, 3.0, 30.0])
+        m = np.abs(x).max()
+        y = x if m <= 1 else (2 - 1 / m) * x / m
+        np.testing.assert_allclose(O.uncontract(y), x, rtol=1e-12, atol=1e-12)
+    assert O.uncontract(np.array([2.0, 0.0, 0.0])) is None
+
+
+def test_contracted_footprint_inner_cube_and_plain():
+    cfg = _contracted_cfg()
+    p = np.array([0.6, 0.45, 0.3], np.float32)
+    du, dv = np.array([1e-3, 0, 0]), np.array([0, 2e-3, 0])
+    t, r = 0.7, 0.0005
+    # inside: t r inv_h / 4 (explicit), radius_scale * t * mean|d_adj| inv_h / 4 (camera)
+    assert O.footprint(cfg, p, t, r) == pytest.approx(t * r * 2 / 4, rel=1e-6)
+    assert O.footprint(cfg, p, t, r, (du, dv)) == pytest.approx(
+        cfg.radius_scale * np.float32(t) * 1.5e-3 * 2 / 4, rel=1e-6)
+    plain = replace(cfg, contract=False)
+    assert O.footprint(plain, p, t, r) == pytest.approx(np.float32(t) * r, rel=1e-6)
+
+
+def test_contracted_footprint_against_finite_differences():
+    """Outside the inner cube: the camera footprint is the first-order distance
+    between adjacent rays' contracted samples (finite difference of C with a
+    tiny offset), and det(J_C)^(1/3) matches a finite-difference Jacobian."""
+    cfg = _contracted_cfg()
+    rng = np.random.default_rng(3)
+
+    def C(x):
+        m = np.abs(x).max()
+        return x if m <= 1 else (2 - 1 / m) * x / m
+
+    for _ in range(100):
+        x = rng.normal(size=3) * 4
+        if np.abs(x).max() < 1.2:
+            continue
+        p = (0.5 + x / 2).astype(np.float32)
+        x = (p.astype(np.float64) - 0.5) * 2
+        t = 2.0
+        du = rng.normal(size=3) * 1e-7
+        dv = rng.normal(size=3) * 1e-7
+        want = np.mean([np.linalg.norm(C(x + t * dd * 2) - C(x)) for dd in (du, dv)])
+        got = O.footprint(cfg, p, t, 0.0, (du, dv))
+        assert got == pytest.approx(cfg.radius_scale * want / 4, rel=1e-4)
+        h = 1e-6
+        J = np.stack([(C(x + h * e) - C(x - h * e)) / (2 * h) for e in np.eye(3)], axis=1)
+        want_j = np.cbrt(np.linalg.det(J))
+        assert O.footprint(cfg, p, t, 1e-3) == pytest.approx(t * 1e-3 * 2 * want_j / 4, rel=1e-5)
+
+
+def test_contracted_march_brute_force():
+    cfg = _contracted_cfg(occ_res=(16, 16, 16))
+    rng = np.random.default_rng(4)
+    occ = rng.uniform(size=(16, 16, 16)) < 0.15
+    F = O.Field(cfg, np.zeros((cfg.levels, cfg.T, 2)), np.zeros(O.mlp_count(cfg)), S.pack_bits(occ))
+    o = rng.uniform(0.2, 0.8, (30, 3)).astype(np.float32)
+    d = rng.normal(size=(30, 3))
+    d = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
+    ri, rv, cnt = F.march(o, d, cfg.max_steps)
+    t = O.sample_table(cfg)
+    flat = occ.reshape(-1)
+    for b in range(30):
+        # every sample stays on the grid (the contracted cube covers space)
+        p = (o[b][None, :] + t[:-1, None] * d[b][None, :]).astype(np.float32)
+        ph = O.grid_position(cfg, p)
+        v = np.clip(np.floor(ph * np.float32(16)).astype(np.int64), 0, 15)
+        vox = v[:, 0] + 16 * (v[:, 1] + 16 * v[:, 2])
+        want = [(i, vx) for i, vx in enumerate(vox) if flat[vx]]
+        assert cnt[b] == len(want)
+        assert [(int(a), int(c)) for a, c in zip(ri[b, :cnt[b]], rv[b, :cnt[b]])] == want
+    assert cnt.sum() > 100
+
+
+def test_contracted_density_grad_matches_central_differences():
+    """As the plain-scene pin, with the gradient chained through J_C: points in
+    the outer shell and in the inner cube, away from cell faces and from the
+    planes where the largest |x_k| changes axis (J_C jumps there). Coarse
+    levels (finest N = 13) let the stencil span 1e-3 of the grid, so the fp32
+    rounding of the grid position stays below 1e-4 of it."""
+    cfg = replace(_contracted_cfg(occ_res=(16, 16, 16)), levels=4, base_res=4.0, growth=1.5)
+    rng = np.random.default_rng(8)
+    grid = rng.uniform(0.1, 1.0, (cfg.levels, cfg.T, cfg.feats))
+    mlp = rng.normal(size=O.mlp_count(cfg)) * 0.3
+    din = cfg.levels * cfg.feats
+    W1 = np.abs(mlp[:64 * din].reshape(64, din))
+    W1[32:] *= -1
+    mlp[:64 * din] = W1.reshape(-1)
+    F = O.Field(cfg, grid, mlp, S.pack_bits(np.ones((16, 16, 16), bool)))
+    n = 8000
+    pos = (0.5 + rng.normal(size=(n, 3)) * rng.choice([0.2, 1.5], (n, 1))).astype(np.float32)
+    _, frac = O.corners(cfg, pos)
+    x = np.abs((pos.astype(np.float64) - 0.5) * 2)
+    xs = np.sort(x, axis=1)
+    ok = ((frac > 0.1) & (frac < 0.9)).reshape(n, -1).all(axis=1) & (xs[:, 2] - xs[:, 1] > 0.05 * xs[:, 2])
+    ok &= np.abs(xs[:, 2] - 1.0) > 0.05  # not at the inner cube's faces
+    sig, grad = F.density_grad(pos, 1e-5)
+    idx = np.flatnonzero(ok)
+    outer = xs[idx, 2] > 1.0
+    assert idx.size > 100 and outer.sum() > 30, (idx.size, outer.sum())
+    for i in idx:
+        h = 1e-3 * max(1.0, xs[i, 2])  # at most 1e-3 of the grid, tangential or radial
+        fd = np.zeros(3)
+        for k in range(3):
+            pp, pm = pos[i].copy(), pos[i].copy()
+            pp[k] += h
+            pm[k] -= h
+            ls = np.log(F.density_grad(np.stack([pp, pm]), 1e-5)[0])
+            fd[k] = (ls[0] - ls[1]) / (float(pp[k]) - float(pm[k]))
+        np.testing.assert_allclose(grad[i] / sig[i], fd, rtol=0, atol=1e-3 * np.abs(fd).max())

@@ -87,7 +87,14 @@ typedef struct vrnerf_field vrnerf_field;
  * lod_bias (Eq. 3, Sec. 4.2.2). sigma = exp(o_0 + density_bias).
  * Compositing stops after the sample where transmittance < T_eps.
  * occ_res: occupancy voxels per axis, each in [1, 2048], fewer than 2^31 in
- * all (Sec. 4.3). */
+ * all (Sec. 4.3).
+ * contract = 1 makes the scene unbounded (Sec. 4: L-infinity cubic
+ * contraction): x = (p - centre) / h with the box's centre and half its
+ * largest extent h, y = x for |x|_inf <= 1, else (2 - 1/|x|_inf) x / |x|_inf;
+ * the hash grid and the occupancy grid span y in [-2, 2]^3 (normalised
+ * position y / 4 + 1/2), the march runs to t_far, and the footprint of a
+ * camera ray is the distance to its adjacent pixels' rays in contracted
+ * space (Sec. 4.2.1), of an explicit ray t r det(J_C)^(1/3). */
 typedef struct {
     int32_t levels, feats, log2_T, feat_fp16;
     double base_res, growth;
@@ -97,6 +104,8 @@ typedef struct {
     int32_t max_steps;
     float t_near, t_far;
     float lod_bias, T_eps, radius_scale, density_bias;
+    int32_t contract; /* 0: bounded box, 1: unbounded (contracted) scene */
+    int32_t reserved;
 } vrnerf_field_desc;
 
 /* Optional per-call render settings (NULL = fp32 MLP, linear output only). */

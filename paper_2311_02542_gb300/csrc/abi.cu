@@ -61,6 +61,7 @@ int check_desc(const vrnerf_field_desc *d) {
         if (d->occ_res[k] < 1 || d->occ_res[k] > 2048)
             return fail(VRNERF_EINVAL, "occ_res must be in [1, 2048]");
     }
+    if (d->contract != 0 && d->contract != 1) return fail(VRNERF_EINVAL, "contract must be 0 or 1");
     if ((long long)d->occ_res[0] * d->occ_res[1] * d->occ_res[2] > 0x7fffffffll)
         return fail(VRNERF_EINVAL, "occupancy grid must hold fewer than 2^31 voxels");
     if (d->max_steps < 1 || d->max_steps > 8192) return fail(VRNERF_EINVAL, "max_steps must be in [1, 8192]");
@@ -102,6 +103,9 @@ void derive_view(const vrnerf_field_desc &d, FieldView &f, std::vector<float> &t
         if (ext > ext_max) ext_max = ext;
     }
     f.inv_ext = (float)(1.0 / ext_max);
+    f.contract = d.contract;
+    for (int k = 0; k < 3; ++k) f.cen[k] = (float)(0.5 * ((double)d.aabb_min[k] + (double)d.aabb_max[k]));
+    f.inv_h = (float)(2.0 / ext_max);
     f.two_s = (float)(2.0 * d.base_res);
     f.inv_ln_f = (float)(1.0 / log(d.growth));
     f.lod_bias = d.lod_bias;
@@ -121,7 +125,7 @@ void derive_view(const vrnerf_field_desc &d, FieldView &f, std::vector<float> &t
         c_max = fmax(c_max, (double)f.inv_cell[k]);
     }
     const double err = ldexp(1.0, -24) * (c_max * ((double)d.t_far + 2.0 * A + ext_max) + res_max);
-    f.skip = (16.0 * err < (double)f.skip_eps) ? 1 : 0;
+    f.skip = (16.0 * err < (double)f.skip_eps && !d.contract) ? 1 : 0;
     f.ln_tn = logf(d.t_near);
     f.inv_ln_q = (float)((double)d.max_steps / log((double)d.t_far / (double)d.t_near));
     // exponential sample distances t_i = t_near (t_far / t_near)^(i / S), fp64 -> fp32

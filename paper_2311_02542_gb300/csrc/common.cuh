@@ -40,6 +40,10 @@ struct FieldView {
     int skip;                 // 0: test every sample against the occupancy bits
     float skip_eps;           // margin (voxels) kept from the faces of an empty cube
     float ln_tn, inv_ln_q;    // ln t_near and S / ln(t_far / t_near)
+    // unbounded scenes (Sec. 4): x = (p - cen) inv_h, y = C(x) (L-infinity
+    // contraction), normalised grid position y / 4 + 1/2
+    int contract;
+    float cen[3], inv_h;
 };
 
 // One launch's rays: either camera views (pixels in 8x4 tiles) or explicit arrays.
@@ -104,15 +108,47 @@ __device__ __forceinline__ void camera_ray(const float *__restrict__ c2w, const 
     }
 }
 
+// Cubic space contraction with the L-infinity norm (Sec. 4): m = |x|_inf,
+// C(x) = x for m <= 1, else (2 - 1/m) x / m, computed as x ((2 - 1/m) (1/m))
+// with every operation rounded on its own. Returns the normalised grid
+// position ph = C(x) / 4 + 1/2 of world position p.
+__device__ __forceinline__ void contracted_position(const FieldView &f, const float p[3], float ph[3]) {
+    float x[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) x[k] = __fmul_rn(__fsub_rn(p[k], f.cen[k]), f.inv_h);
+    const float m = fmaxf(fmaxf(fabsf(x[0]), fabsf(x[1])), fabsf(x[2]));
+    if (m > 1.0f) {
+        const float inv = __fdiv_rn(1.0f, m);
+        const float sc = __fmul_rn(__fsub_rn(2.0f, inv), inv);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) x[k] = __fmul_rn(x[k], sc);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) ph[k] = __fadd_rn(__fmul_rn(x[k], 0.25f), 0.5f);
+}
+
 // p = o + t d and its occupancy voxel; false once the sample leaves the grid.
+// The grid of a contracted scene covers all of space (coordinates clamped to
+// the last voxel, reached only where 2 - 1/m rounds to 2).
 __device__ __forceinline__ bool sample_voxel(const FieldView &f, const float o[3], const float d[3],
                                              float t, float p[3], int &vox, int v[3]) {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        p[k] = __fadd_rn(o[k], __fmul_rn(t, d[k]));
-        float g = __fmul_rn(__fsub_rn(p[k], f.mn[k]), f.inv_cell[k]);
-        if (!(g >= 0.0f) || !(g < f.res_f[k])) return false;
-        v[k] = (int)g;
+    for (int k = 0; k < 3; ++k) p[k] = __fadd_rn(o[k], __fmul_rn(t, d[k]));
+    if (f.contract) {
+        float ph[3];
+        contracted_position(f, p, ph);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int c = (int)floorf(__fmul_rn(ph[k], f.res_f[k]));
+            v[k] = c < 0 ? 0 : (c > f.res[k] - 1 ? f.res[k] - 1 : c);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float g = __fmul_rn(__fsub_rn(p[k], f.mn[k]), f.inv_cell[k]);
+            if (!(g >= 0.0f) || !(g < f.res_f[k])) return false;
+            v[k] = (int)g;
+        }
     }
     vox = v[0] + f.res[0] * (v[1] + f.res[1] * v[2]);
     return true;
@@ -219,11 +255,82 @@ __device__ __forceinline__ int march_next(const FieldView &f, const float *__res
     return MARCH_MORE;
 }
 
-// Normalised grid position p^ = (p - box_min) / largest extent, fp32 with
-// separate rounding (shared by every level of a sample).
+// Normalised grid position p^ = (p - box_min) / largest extent, or the
+// contracted position of an unbounded scene; fp32 with separate rounding
+// (shared by every level of a sample).
 __device__ __forceinline__ void grid_position(const FieldView &f, const float p[3], float ph[3]) {
+    if (f.contract) {
+        contracted_position(f, p, ph);
+        return;
+    }
 #pragma unroll
     for (int k = 0; k < 3; ++k) ph[k] = __fmul_rn(__fsub_rn(p[k], f.mn[k]), f.inv_ext);
+}
+
+// Contraction Jacobian applied to v at x (k: the axis of the largest |x_k|,
+// the first on ties): v inside the inner cube, else s v + s'(m) x sign(x_k) v_k
+// with s(m) = 2/m - 1/m^2.
+__device__ __forceinline__ void contract_jv(const float x[3], const float v[3], float out[3]) {
+    float m = fabsf(x[0]);
+    int k = 0;
+    if (fabsf(x[1]) > m) { m = fabsf(x[1]); k = 1; }
+    if (fabsf(x[2]) > m) { m = fabsf(x[2]); k = 2; }
+    if (m <= 1.0f) {
+        out[0] = v[0]; out[1] = v[1]; out[2] = v[2];
+        return;
+    }
+    const float im = 1.0f / m;
+    const float sc = im * (2.0f - im), ds = 2.0f * im * im * (im - 1.0f);
+    const float vk = x[k] >= 0.0f ? v[k] : -v[k];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) out[a] = fmaf(ds * x[a], vk, sc * v[a]);
+}
+
+// Transposed Jacobian applied to a gradient g at x: the gradient with respect
+// to x of a function whose gradient with respect to C(x) is g.
+__device__ __forceinline__ void contract_jtv(const float x[3], float g[3]) {
+    float m = fabsf(x[0]);
+    int k = 0;
+    if (fabsf(x[1]) > m) { m = fabsf(x[1]); k = 1; }
+    if (fabsf(x[2]) > m) { m = fabsf(x[2]); k = 2; }
+    if (m <= 1.0f) return;
+    const float im = 1.0f / m;
+    const float sc = im * (2.0f - im), ds = 2.0f * im * im * (im - 1.0f);
+    const float gx = fmaf(g[0], x[0], fmaf(g[1], x[1], g[2] * x[2]));
+#pragma unroll
+    for (int a = 0; a < 3; ++a) g[a] *= sc;
+    g[k] += (x[k] >= 0.0f ? ds : -ds) * gx;
+}
+
+// Footprint radius in normalised grid units of the sample at distance t
+// (Sec. 4.2.1). Plain scenes: t r / largest extent. Contracted scenes with
+// adjacent-ray offsets (du, dv: the directions of the pixels to the right and
+// below minus the ray's own): radius_scale times the mean first-order
+// distance |J_C (t inv_h du)| to the adjacent rays' contracted samples, over
+// 4. Contracted scenes, explicit rays: t r inv_h det(J_C)^(1/3) / 4 with
+// det(J_C)^(1/3) = (2m - 1)^(2/3) / m^2 outside the inner cube.
+__device__ __forceinline__ float footprint(const FieldView &f, float t, float r, const float p[3],
+                                           const float *du, const float *dv) {
+    if (!f.contract) return t * r * f.inv_ext;
+    float x[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) x[k] = (p[k] - f.cen[k]) * f.inv_h;
+    if (du) {
+        const float st = t * f.inv_h;
+        float acc = 0.0f;
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const float *da = a ? dv : du;
+            const float v[3] = {st * da[0], st * da[1], st * da[2]};
+            float jv[3];
+            contract_jv(x, v, jv);
+            acc += sqrtf(fmaf(jv[0], jv[0], fmaf(jv[1], jv[1], jv[2] * jv[2])));
+        }
+        return f.radius_scale * 0.125f * acc;
+    }
+    const float m = fmaxf(fmaxf(fabsf(x[0]), fabsf(x[1])), fabsf(x[2]));
+    const float j = m <= 1.0f ? 1.0f : cbrtf((2.0f * m - 1.0f) * (2.0f * m - 1.0f)) / (m * m);
+    return t * r * f.inv_h * j * 0.25f;
 }
 
 // Corner indices of level l (corner b at offset (b&1, b>>1&1, b>>2&1)) and
@@ -362,8 +469,13 @@ __device__ __forceinline__ void sh16(float x, float y, float z, float s[16]) {
 // ---------------------------------------------------------------------------
 // Ray slots: camera mode maps slot -> (view, pixel) in 8x4 tiles.
 // ---------------------------------------------------------------------------
+// adj (optional, camera mode only): the direction offsets to the pixels to
+// the right and below, d(u+1, v) - d(u, v) and d(u, v+1) - d(u, v), which set
+// the footprint of a contracted scene; returns *has_adj = false for explicit rays.
 __device__ __forceinline__ bool slot_ray(const RaySource &src, const FieldView &f, long long slot,
-                                         float o[3], float d[3], float &r, long long &pix) {
+                                         float o[3], float d[3], float &r, long long &pix,
+                                         float *adj = nullptr, bool *has_adj = nullptr) {
+    if (has_adj) *has_adj = src.n_views != 0;
     if (src.n_views == 0) {
         pix = slot;
 #pragma unroll
@@ -384,6 +496,16 @@ __device__ __forceinline__ bool slot_ray(const RaySource &src, const FieldView &
     if (px >= vi.W || py >= vi.H) return false;
     const float *K = src.K + 4 * v;
     camera_ray(src.c2w + 12 * v, K, px, py, o, d);
+    if (adj) {
+        float oo[3], du[3], dv[3];
+        camera_ray(src.c2w + 12 * v, K, px + 1, py, oo, du);
+        camera_ray(src.c2w + 12 * v, K, px, py + 1, oo, dv);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            adj[k] = __fsub_rn(du[k], d[k]);
+            adj[3 + k] = __fsub_rn(dv[k], d[k]);
+        }
+    }
     r = __fdiv_rn(f.radius_scale, __ldg(K));
     pix = vi.pix_begin + (long long)py * vi.W + px;
     return true;

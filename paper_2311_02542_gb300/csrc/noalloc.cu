@@ -88,6 +88,9 @@ void derive_view_fixed(const vrnerf_field_desc &d, FieldView &f, float *t_tab) {
         if (ext > ext_max) ext_max = ext;
     }
     f.inv_ext = (float)(1.0 / ext_max);
+    f.contract = d.contract;
+    for (int k = 0; k < 3; ++k) f.cen[k] = (float)(0.5 * ((double)d.aabb_min[k] + (double)d.aabb_max[k]));
+    f.inv_h = (float)(2.0 / ext_max);
     f.two_s = (float)(2.0 * d.base_res);
     f.inv_ln_f = (float)(1.0 / log(d.growth));
     f.lod_bias = d.lod_bias;

@@ -19,6 +19,17 @@ namespace vrn {
 
 cudaError_t launch_build_dist(const FieldView &f, uint8_t *dist, cudaStream_t st);
 
+// World position of a contracted point y (|y|_inf < 2): the inverse
+// contraction x = y for |y|_inf <= 1, else y / (m (2 - m)); false at m >= 2.
+__device__ __forceinline__ bool uncontract_world(const FieldView &f, const float y[3], float p[3]) {
+    const float m = fmaxf(fmaxf(fabsf(y[0]), fabsf(y[1])), fabsf(y[2]));
+    if (m >= 2.0f) return false;
+    const float sc = m <= 1.0f ? 1.0f : 1.0f / (m * (2.0f - m));
+#pragma unroll
+    for (int a = 0; a < 3; ++a) p[a] = f.cen[a] + y[a] * sc / f.inv_h;
+    return true;
+}
+
 template <int L>
 __global__ void __launch_bounds__(256)
 prune_kernel(const FieldView f, const float *__restrict__ cams, int n_cams, int k, float threshold,
@@ -42,12 +53,30 @@ prune_kernel(const FieldView f, const float *__restrict__ cams, int n_cams, int 
             cell[a] = 1.0f / f.inv_cell[a];
             lo[a] = f.mn[a] + (float)vv[a] * cell[a];
         }
-        float smax = 0.0f;
+        float smax = 0.0f, dmin = INFINITY;
         for (int i = lane; i < k * k * k; i += 32) {
             const int j[3] = {i % k, (i / k) % k, i / (k * k)};
             float p[3];
+            if (f.contract) {
+                // lattice point of the contracted voxel, mapped back to world space
+                float y[3];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) p[a] = lo[a] + ((float)j[a] + 0.5f) / (float)k * cell[a];
+                for (int a = 0; a < 3; ++a)
+                    y[a] = 4.0f * ((float)vv[a] + ((float)j[a] + 0.5f) / (float)k) / f.res_f[a] - 2.0f;
+                uncontract_world(f, y, p);
+                for (int c = 0; c < n_cams; ++c) {
+                    float s2 = 0.0f;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const float e = p[a] - __ldg(cams + 3 * c + a);
+                        s2 = fmaf(e, e, s2);
+                    }
+                    dmin = fminf(dmin, sqrtf(s2));
+                }
+            } else {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) p[a] = lo[a] + ((float)j[a] + 0.5f) / (float)k * cell[a];
+            }
             float feat[D];
             gather_features<L>(f, p, 0.0f, feat);
             float o0 = 0.0f;
@@ -60,18 +89,63 @@ prune_kernel(const FieldView f, const float *__restrict__ cams, int n_cams, int 
             smax = fmaxf(smax, expf(o0 + f.density_bias));
         }
 #pragma unroll
-        for (int s = 16; s > 0; s >>= 1) smax = fmaxf(smax, __shfl_xor_sync(0xffffffffu, smax, s));
+        for (int s = 16; s > 0; s >>= 1) {
+            smax = fmaxf(smax, __shfl_xor_sync(0xffffffffu, smax, s));
+            dmin = fminf(dmin, __shfl_xor_sync(0xffffffffu, dmin, s));
+        }
         if (lane == 0) {
-            float dmin = INFINITY;
-            for (int c = 0; c < n_cams; ++c) {
-                float s2 = 0.0f;
+            if (f.contract) {
+                // the voxel's world region: a box inside the inner cube, else the
+                // lattice points (above) and the finite corner pre-images
+                float ylo[3], yhi[3];
+                bool inner = true;
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    const float cc = cams[3 * c + a], l = lo[a], h = lo[a] + cell[a];
-                    const float dd = cc < l ? l - cc : (cc > h ? cc - h : 0.0f);
-                    s2 = fmaf(dd, dd, s2);
+                    ylo[a] = 4.0f * (float)vv[a] / f.res_f[a] - 2.0f;
+                    yhi[a] = 4.0f * (float)(vv[a] + 1) / f.res_f[a] - 2.0f;
+                    if (ylo[a] < -1.0f || yhi[a] > 1.0f) inner = false;
                 }
-                dmin = fminf(dmin, sqrtf(s2));
+                if (inner) {
+                    dmin = INFINITY;
+                    for (int c = 0; c < n_cams; ++c) {
+                        float s2 = 0.0f;
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            const float l = f.cen[a] + ylo[a] / f.inv_h, h = f.cen[a] + yhi[a] / f.inv_h;
+                            const float cc = __ldg(cams + 3 * c + a);
+                            const float dd = cc < l ? l - cc : (cc > h ? cc - h : 0.0f);
+                            s2 = fmaf(dd, dd, s2);
+                        }
+                        dmin = fminf(dmin, sqrtf(s2));
+                    }
+                } else {
+                    for (int b = 0; b < 8; ++b) {
+                        float y[3], q[3];
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) y[a] = (b >> a) & 1 ? yhi[a] : ylo[a];
+                        if (!uncontract_world(f, y, q)) continue;
+                        for (int c = 0; c < n_cams; ++c) {
+                            float s2 = 0.0f;
+#pragma unroll
+                            for (int a = 0; a < 3; ++a) {
+                                const float e = q[a] - __ldg(cams + 3 * c + a);
+                                s2 = fmaf(e, e, s2);
+                            }
+                            dmin = fminf(dmin, sqrtf(s2));
+                        }
+                    }
+                }
+            } else {
+                for (int c = 0; c < n_cams; ++c) {
+                    float s2 = 0.0f;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const float cc = __ldg(cams + 3 * c + a), l = lo[a], h = lo[a] + cell[a];
+                        const float dd = cc < l ? l - cc : (cc > h ? cc - h : 0.0f);
+                        s2 = fmaf(dd, dd, s2);
+                    }
+                    dmin = fminf(dmin, sqrtf(s2));
+                }
             }
             // interval [t_i, t_i+1) holding dmin (i clamped to [0, S-1])
             int lo_i = 0, hi_i = f.S - 1;

@@ -162,10 +162,12 @@ __device__ __forceinline__ void density_feat_grad(const float *__restrict__ s, c
     }
 }
 
-// v = sum_q g_q d feat_q / d p at a fixed footprint: per level, w_l N_l /
-// extent times the derivative of the trilinear interpolation along each
-// axis (the corner weight's factor of that axis replaced by +-1). The
-// corners are fetched again (L2-resident) instead of kept from the gather.
+// v = sum_q g_q d feat_q / d p at a fixed footprint: per level, w_l N_l
+// times the derivative of the trilinear interpolation along each axis (the
+// corner weight's factor of that axis replaced by +-1) gives the gradient in
+// grid coordinates, then the grid map's Jacobian (1 / extent, or the
+// contraction's) takes it to world coordinates. The corners are fetched
+// again (L2-resident) instead of kept from the gather.
 template <int L>
 __device__ __forceinline__ void feature_pos_grad(const FieldView &f, const float p[3], float r_norm,
                                                  const float g[2 * L], float v[3]) {
@@ -194,13 +196,25 @@ __device__ __forceinline__ void feature_pos_grad(const FieldView &f, const float
                 d1[k] = fmaf(dw[k], e.y, d1[k]);
             }
         }
-        const float sc = wl * (float)f.N[l] * f.inv_ext;
+        const float sc = wl * (float)f.N[l];
 #pragma unroll
         for (int k = 0; k < 3; ++k) v[k] = fmaf(sc, fmaf(g[2 * l], d0[k], g[2 * l + 1] * d1[k]), v[k]);
     }
+    // v is the gradient with respect to the grid position ph; chain to p
+    if (f.contract) {
+        float x[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) x[k] = (p[k] - f.cen[k]) * f.inv_h;
+        contract_jtv(x, v);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) v[k] *= 0.25f * f.inv_h;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) v[k] *= f.inv_ext;
+    }
 }
 
-template <int L, bool NRM>
+template <int L, bool NRM, bool CT>
 __global__ void __launch_bounds__(kSimtThreads, 4)
 render_simt_kernel(const FieldView f, const RaySource src, const RenderOut out,
                    unsigned long long *__restrict__ counter) {
@@ -219,6 +233,8 @@ render_simt_kernel(const FieldView f, const RaySource src, const RenderOut out,
     MarchRay mr;
     float r = 0.0f, T = 1.0f, C[3] = {0, 0, 0}, Dp = 0.0f;
     float Nm[3] = {0, 0, 0};
+    float adj[CT ? 6 : 1];  // contracted scenes: offsets to the adjacent pixels' rays
+    bool has_adj = false;
     int n_eval = 0;
     unsigned st_samples = 0, st_levels = 0, st_steps = 0, st_rays = 0;
 
@@ -238,7 +254,8 @@ render_simt_kernel(const FieldView f, const RaySource src, const RenderOut out,
                     long long slot = (long long)base + __popc(m & ((1u << lane) - 1u));
                     if (slot >= src.n_slots) {
                         exhausted = true;
-                    } else if (slot_ray(src, f, slot, mr.o, mr.d, r, pix)) {
+                    } else if (slot_ray(src, f, slot, mr.o, mr.d, r, pix, CT ? adj : nullptr,
+                                        CT ? &has_adj : nullptr)) {
                         march_init(f, mr);
                         ray = slot;
                         n_eval = 0;
@@ -265,7 +282,11 @@ render_simt_kernel(const FieldView f, const RaySource src, const RenderOut out,
         // ---- phase 2: features, MLPs, compositing ----
         if (have) {
             const float t = sT[mr.step], delta = sT[mr.step + 1] - t;
-            const float r_norm = t * r * f.inv_ext;
+            float r_norm;
+            if constexpr (CT)
+                r_norm = footprint(f, t, r, p, has_adj ? adj : nullptr, has_adj ? adj + 3 : nullptr);
+            else
+                r_norm = t * r * f.inv_ext;
             float feat[D];
             st_levels += gather_features<L>(f, p, r_norm, feat);
             ++st_samples;
@@ -319,7 +340,7 @@ query_simt_kernel(const FieldView f, const float *__restrict__ pos, const float 
     float p[3] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
     float dd[3] = {dir[3 * i], dir[3 * i + 1], dir[3 * i + 2]};
     float feat[D];
-    gather_features<L>(f, p, radius[i] * f.inv_ext, feat);
+    gather_features<L>(f, p, footprint(f, 1.0f, radius[i], p, nullptr, nullptr), feat);
     float sigma, rgb[3];
     mlp_simt<D>(sW, feat, dd, f.density_bias, sigma, rgb);
     sigma_out[i] = sigma;
@@ -397,13 +418,13 @@ size_t simt_smem_bytes(const FieldView &f) {
     return sizeof(float) * (size_t)(wsize + f.S + 1);
 }
 
-template <int L, bool NRM>
+template <int L, bool NRM, bool CT>
 static cudaError_t render_simt_t(const FieldView &f, const RaySource &src, const RenderOut &out,
                                  unsigned long long *counter, cudaStream_t st) {
     static int blocks_per_sm = 0;
     static size_t configured_smem = 0;
     const size_t smem = simt_smem_bytes(f);
-    auto kern = render_simt_kernel<L, NRM>;
+    auto kern = render_simt_kernel<L, NRM, CT>;
     if (smem != configured_smem) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -422,11 +443,17 @@ static cudaError_t render_simt_t(const FieldView &f, const RaySource &src, const
 
 cudaError_t launch_render_simt(const FieldView &f, const RaySource &src, const RenderOut &out,
                                unsigned long long *counter, cudaStream_t st) {
-    if (out.normal)
-        return f.L == 8 ? render_simt_t<8, true>(f, src, out, counter, st)
-                        : render_simt_t<16, true>(f, src, out, counter, st);
-    return f.L == 8 ? render_simt_t<8, false>(f, src, out, counter, st)
-                    : render_simt_t<16, false>(f, src, out, counter, st);
+    const bool nrm = out.normal != nullptr, ct = f.contract != 0;
+    if (f.L == 8) {
+        if (ct) return nrm ? render_simt_t<8, true, true>(f, src, out, counter, st)
+                           : render_simt_t<8, false, true>(f, src, out, counter, st);
+        return nrm ? render_simt_t<8, true, false>(f, src, out, counter, st)
+                   : render_simt_t<8, false, false>(f, src, out, counter, st);
+    }
+    if (ct) return nrm ? render_simt_t<16, true, true>(f, src, out, counter, st)
+                       : render_simt_t<16, false, true>(f, src, out, counter, st);
+    return nrm ? render_simt_t<16, true, false>(f, src, out, counter, st)
+               : render_simt_t<16, false, false>(f, src, out, counter, st);
 }
 
 template <int L>

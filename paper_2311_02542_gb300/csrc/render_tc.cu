@@ -23,7 +23,7 @@
 
 namespace vrn {
 
-template <int L, int FMT>
+template <int L, int FMT, bool CT>
 __global__ void __launch_bounds__(kTcThreads, kTcMinBlocks)
 render_tc_kernel(const FieldView f, const RaySource src, const RenderOut out,
                  unsigned long long *__restrict__ counter, const uint4 *__restrict__ wimg,
@@ -40,6 +40,8 @@ render_tc_kernel(const FieldView f, const RaySource src, const RenderOut out,
     bool exhausted = false, ok = true;
     MarchRay mr;
     float r = 0.0f, T = 1.0f, C[3] = {0, 0, 0}, Dp = 0.0f;
+    float adj[CT ? 6 : 1];  // contracted scenes: offsets to the adjacent pixels' rays
+    bool has_adj = false;
     int n_eval = 0;
     uint32_t phase = 0;
     unsigned st_samples = 0, st_levels = 0, st_steps = 0, st_rays = 0;
@@ -60,7 +62,8 @@ render_tc_kernel(const FieldView f, const RaySource src, const RenderOut out,
                     const long long slot = (long long)base + __popc(m & ((1u << lane) - 1u));
                     if (slot >= src.n_slots) {
                         exhausted = true;
-                    } else if (slot_ray(src, f, slot, mr.o, mr.d, r, pix)) {
+                    } else if (slot_ray(src, f, slot, mr.o, mr.d, r, pix, CT ? adj : nullptr,
+                                        CT ? &has_adj : nullptr)) {
                         march_init(f, mr);
                         ray = slot;
                         n_eval = 0;
@@ -88,7 +91,12 @@ render_tc_kernel(const FieldView f, const RaySource src, const RenderOut out,
         if (have) {
             t = sT[mr.step];
             delta = sT[mr.step + 1] - t;
-            st_levels += gather_to_tile<L, FMT == 1 ? 1 : 0>(f, p, t * r * f.inv_ext, S.act, threadIdx.x);
+            float r_norm;
+            if constexpr (CT)
+                r_norm = footprint(f, t, r, p, has_adj ? adj : nullptr, has_adj ? adj + 3 : nullptr);
+            else
+                r_norm = t * r * f.inv_ext;
+            st_levels += gather_to_tile<L, FMT == 1 ? 1 : 0>(f, p, r_norm, S.act, threadIdx.x);
             ++st_samples;
         } else {
             uint32_t z[D / 2];
@@ -137,7 +145,7 @@ query_tc_kernel(const FieldView f, const float *__restrict__ pos, const float *_
         dd[0] = dir[3 * i];
         dd[1] = dir[3 * i + 1];
         dd[2] = dir[3 * i + 2];
-        gather_features<L>(f, p, radius[i] * f.inv_ext, feat);
+        gather_features<L>(f, p, footprint(f, 1.0f, radius[i], p, nullptr, nullptr), feat);
     } else {
 #pragma unroll
         for (int k = 0; k < D; ++k) feat[k] = 0.0f;
@@ -248,10 +256,10 @@ __global__ void build_tc_image_fp8_kernel(const float *__restrict__ mlp, int D, 
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-template <int L, int FMT>
-static cudaError_t render_tc_t(vrnerf_field *F, const RaySource &src, const RenderOut &out, cudaStream_t st) {
+template <int L, int FMT, bool CT>
+static cudaError_t render_tc_ct(vrnerf_field *F, const RaySource &src, const RenderOut &out, cudaStream_t st) {
     const size_t smem = tc_smem_bytes(2 * L, 0);
-    auto kern = render_tc_kernel<L, FMT>;
+    auto kern = render_tc_kernel<L, FMT, CT>;
     int bps = 0;
     cudaError_t e = prepare_tc(kern, smem, bps);
     if (e != cudaSuccess) return e;
@@ -263,6 +271,11 @@ static cudaError_t render_tc_t(vrnerf_field *F, const RaySource &src, const Rend
     kern<<<(unsigned)grid, kTcThreads, smem, st>>>(F->view, src, out, cnt, static_cast<const uint4 *>(F->tc_w),
                                                    cnt + 1);
     return cudaGetLastError();
+}
+
+template <int L, int FMT>
+static cudaError_t render_tc_t(vrnerf_field *F, const RaySource &src, const RenderOut &out, cudaStream_t st) {
+    return F->view.contract ? render_tc_ct<L, FMT, true>(F, src, out, st) : render_tc_ct<L, FMT, false>(F, src, out, st);
 }
 
 static int fmt_of(int prec) { return prec == VRNERF_BF16 ? 1 : (prec == VRNERF_FP8 ? 2 : 0); }

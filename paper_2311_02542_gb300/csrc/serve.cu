@@ -78,7 +78,7 @@ __device__ __forceinline__ T *ldcg_ptr(T *const *p) {
     return reinterpret_cast<T *>(__ldcg(reinterpret_cast<const unsigned long long *>(p)));
 }
 
-template <int L, int FMT>
+template <int L, int FMT, bool CT>
 __global__ void __launch_bounds__(kTcThreads, kTcMinBlocks)
 serve_kernel(const FieldView f, ServeView *__restrict__ ring, const ServeCtl *__restrict__ ctl,
              unsigned int *__restrict__ cursor, const uint4 *__restrict__ wimg,
@@ -95,6 +95,7 @@ serve_kernel(const FieldView f, ServeView *__restrict__ ring, const ServeCtl *__
     bool live = false, ok = true;
     MarchRay mr;
     float r = 0.0f, T = 1.0f, C[3] = {0, 0, 0};
+    float adj[CT ? 6 : 1];  // contracted scenes: offsets to the adjacent pixels' rays
     float *dst = nullptr;
     int view = -1, cnt_view = -1;
     unsigned int cnt = 0;  // finished slots of cnt_view not yet reported
@@ -193,6 +194,16 @@ serve_kernel(const FieldView f, ServeView *__restrict__ ring, const ServeCtl *__
                             K[2] = k4.z;
                             K[3] = k4.w;
                             camera_ray(c2w, K, px, py, mr.o, mr.d);
+                            if constexpr (CT) {
+                                float oo[3], du[3], dv[3];
+                                camera_ray(c2w, K, px + 1, py, oo, du);
+                                camera_ray(c2w, K, px, py + 1, oo, dv);
+#pragma unroll
+                                for (int k = 0; k < 3; ++k) {
+                                    adj[k] = __fsub_rn(du[k], mr.d[k]);
+                                    adj[3 + k] = __fsub_rn(dv[k], mr.d[k]);
+                                }
+                            }
                             r = __fdiv_rn(f.radius_scale, K[0]);
                             march_init(f, mr);
                             dst = ldcg_ptr(&sv->out) + 3ll * ((long long)py * W + px);
@@ -236,7 +247,12 @@ serve_kernel(const FieldView f, ServeView *__restrict__ ring, const ServeCtl *__
         if (have) {
             const float t = sT[mr.step];
             delta = sT[mr.step + 1] - t;
-            gather_to_tile<L, FMT == 1 ? 1 : 0>(f, p, t * r * f.inv_ext, S.act, threadIdx.x);
+            float r_norm;
+            if constexpr (CT)
+                r_norm = footprint(f, t, r, p, adj, adj + 3);
+            else
+                r_norm = t * r * f.inv_ext;
+            gather_to_tile<L, FMT == 1 ? 1 : 0>(f, p, r_norm, S.act, threadIdx.x);
         } else {
             uint32_t z[D / 2];
 #pragma unroll
@@ -260,11 +276,11 @@ serve_kernel(const FieldView f, ServeView *__restrict__ ring, const ServeCtl *__
     tc_teardown(S, status);
 }
 
-template <int L, int FMT>
-static cudaError_t launch_serve_t(vrnerf_field *F, ServeView *ring, const ServeCtl *ctl,
-                                  unsigned int *cursor, unsigned long long idle_ns, cudaStream_t st) {
+template <int L, int FMT, bool CT>
+static cudaError_t launch_serve_ct(vrnerf_field *F, ServeView *ring, const ServeCtl *ctl,
+                                   unsigned int *cursor, unsigned long long idle_ns, cudaStream_t st) {
     const size_t smem = tc_smem_bytes(2 * L, 0);
-    auto kern = serve_kernel<L, FMT>;
+    auto kern = serve_kernel<L, FMT, CT>;
     int bps = 0;
     cudaError_t e = prepare_tc(kern, smem, bps);
     if (e != cudaSuccess) return e;
@@ -272,6 +288,13 @@ static cudaError_t launch_serve_t(vrnerf_field *F, ServeView *ring, const ServeC
     kern<<<num_sms() * bps, kTcThreads, smem, st>>>(F->view, ring, ctl, cursor,
                                                     static_cast<const uint4 *>(F->tc_w), idle_ns, status);
     return cudaGetLastError();
+}
+
+template <int L, int FMT>
+static cudaError_t launch_serve_t(vrnerf_field *F, ServeView *ring, const ServeCtl *ctl,
+                                  unsigned int *cursor, unsigned long long idle_ns, cudaStream_t st) {
+    return F->view.contract ? launch_serve_ct<L, FMT, true>(F, ring, ctl, cursor, idle_ns, st)
+                            : launch_serve_ct<L, FMT, false>(F, ring, ctl, cursor, idle_ns, st);
 }
 
 }  // namespace vrn

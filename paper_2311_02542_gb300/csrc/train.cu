@@ -179,7 +179,7 @@ backward_kernel(const FieldView f, const float *__restrict__ o_in, const float *
         if (have) {
             t = sT[mr.step];
             delta = sT[mr.step + 1] - t;
-            rn = t * r * f.inv_ext;
+            rn = footprint(f, t, r, p, nullptr, nullptr);  // explicit rays
             gather_features<L>(f, p, rn, feat);
             dir[0] = mr.d[0];
             dir[1] = mr.d[1];

@@ -147,6 +147,18 @@ def cfg_room_paper_grid(surface: bool = False) -> FieldConfig:
     return c
 
 
+def cfg_room_unbounded(surface: bool = False) -> FieldConfig:
+    """The room of cfg_room with windows, inside an unbounded outdoor scene
+    (Sec. 4: far field through the L-infinity contraction; most of the
+    paper's scenes with views through windows use it, Table 5). Occupancy
+    256^3 over the contracted cube [-2, 2]^3 around the room's centre (inner
+    cube: 20 m wide), samples out to 4 km."""
+    c = cfg_room(surface)
+    c.contract = True
+    c.t_far = 4000.0
+    return c
+
+
 # ----------------------------------------------------------------------------
 # Parameter blob
 # ----------------------------------------------------------------------------
@@ -251,6 +263,87 @@ def occupancy_room(res=(256, 256, 256), aabb_max=(20.0, 20.0, 3.0), target=0.05,
     return (occ, boxes) if return_boxes else occ
 
 
+def _uncontract_np(y):
+    m = np.maximum(np.abs(y).max(axis=-1, keepdims=True), 1.0)
+    return y / (m * (2.0 - np.minimum(m, 2.0 - 1e-9)))
+
+
+def unbounded_boxes(cfg: FieldConfig, seed=2, furniture=40, buildings=60):
+    """World-space boxes (lo, hi) of the unbounded room: ground (z <= 0
+    everywhere), the room's walls (0.2 m thick, windows 1.4 m tall at 0.9 m
+    on every wall), its ceiling, seeded furniture, and seeded buildings 40 m
+    to 1.5 km away (8-40 m footprint, 5-80 m tall)."""
+    rng = np.random.Generator(np.random.Philox(seed + 7000))
+    X, Y, Z = cfg.aabb_max
+    big = 1e7
+    boxes = [((-big, -big, -1.0), (big, big, 0.0)),           # ground / floor
+             ((-0.2, -0.2, Z), (X + 0.2, Y + 0.2, Z + 0.2))]  # ceiling
+    win_lo, win_hi = 0.9, 2.3
+    spans = [(0.0, 3.0), (7.0, 9.0), (11.0, 13.0), (17.0, 20.0)]  # wall between windows
+    for wall in range(4):
+        # full-height pieces between windows, sill and lintel pieces under / over them
+        pieces = [(a, b, 0.0, Z) for a, b in spans]
+        for a, b in ((3.0, 7.0), (9.0, 11.0), (13.0, 17.0)):
+            pieces += [(a, b, 0.0, win_lo), (a, b, win_hi, Z)]
+        for a, b, z0, z1 in pieces:
+            if wall == 0:
+                boxes.append(((-0.2, a, z0), (0.0, b, z1)))
+            elif wall == 1:
+                boxes.append(((X, a, z0), (X + 0.2, b, z1)))
+            elif wall == 2:
+                boxes.append(((a, -0.2, z0), (b, 0.0, z1)))
+            else:
+                boxes.append(((a, Y, z0), (b, Y + 0.2, z1)))
+    for _ in range(furniture):
+        w, d = rng.uniform(0.3, 2.0, 2)
+        h = rng.uniform(0.4, 2.0)
+        x0 = rng.uniform(0.2, X - 0.2 - w)
+        y0 = rng.uniform(0.2, Y - 0.2 - d)
+        boxes.append(((x0, y0, 0.0), (x0 + w, y0 + d, h)))
+    for _ in range(buildings):
+        dist = math.exp(rng.uniform(math.log(40.0), math.log(1500.0)))
+        ang = rng.uniform(0, 2 * math.pi)
+        w, d = rng.uniform(8.0, 40.0, 2)
+        h = rng.uniform(5.0, 80.0)
+        cx, cy = X / 2 + dist * math.cos(ang), Y / 2 + dist * math.sin(ang)
+        boxes.append(((cx - w / 2, cy - d / 2, 0.0), (cx + w / 2, cy + d / 2, h)))
+    return boxes
+
+
+def occupancy_unbounded(cfg: FieldConfig, seed=2, build_res=128):
+    """Contracted-grid occupancy of unbounded_boxes: a voxel of a
+    build_res^3 grid over [-2, 2]^3 is occupied when the bounding box of its
+    corners' pre-images overlaps a box; then repeated up to cfg.occ_res."""
+    boxes = unbounded_boxes(cfg, seed)
+    lo_b = np.array([b[0] for b in boxes])
+    hi_b = np.array([b[1] for b in boxes])
+    cen = (np.array(cfg.aabb_min) + np.array(cfg.aabb_max)) / 2
+    h = 0.5 * max(cfg.aabb_max[k] - cfg.aabb_min[k] for k in range(3))
+    n = build_res
+    e = 4.0 * np.arange(n + 1) / n - 2.0
+    occ = np.zeros((n, n, n), bool)
+    yy, xx = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    for z in range(n):
+        corners = []
+        for c in range(8):
+            y = np.stack([e[xx + (c & 1)], e[yy + ((c >> 1) & 1)],
+                          np.full(xx.shape, e[z + ((c >> 2) & 1)])], axis=-1)
+            y = np.clip(y, -2.0 + 1e-9, 2.0 - 1e-9)
+            corners.append(_uncontract_np(y) * h + cen)
+        corners = np.stack(corners)
+        vlo, vhi = corners.min(axis=0), corners.max(axis=0)     # [n][n][3]
+        slo, shi = vlo.reshape(-1, 3).min(0), vhi.reshape(-1, 3).max(0)
+        hit = np.zeros((n, n), bool)
+        for blo, bhi in zip(lo_b, hi_b):
+            if (blo > shi).any() or (bhi < slo).any():
+                continue
+            hit |= ((vlo[..., 0] <= bhi[0]) & (vhi[..., 0] >= blo[0]) & (vlo[..., 1] <= bhi[1]) &
+                    (vhi[..., 1] >= blo[1]) & (vlo[..., 2] <= bhi[2]) & (vhi[..., 2] >= blo[2]))
+        occ[z] = hit
+    f = [cfg.occ_res[k] // n for k in range(3)]
+    return occ.repeat(f[2], 0).repeat(f[1], 1).repeat(f[0], 2)
+
+
 # ----------------------------------------------------------------------------
 # Cameras: c2w [3][4] fp32 (columns: right, down, forward, centre; OpenCV
 # convention, the camera looks down +z of its own frame), intrinsics
@@ -291,8 +384,16 @@ def intrinsics_fov(width, height, fov_deg=90.0) -> np.ndarray:
 
 def _free_at(occ, cfg: FieldConfig, p) -> bool:
     rx, ry, rz = cfg.occ_res
-    g = [(p[k] - cfg.aabb_min[k]) / (cfg.aabb_max[k] - cfg.aabb_min[k]) * cfg.occ_res[k]
-         for k in range(3)]
+    if getattr(cfg, "contract", False):
+        cen = [(cfg.aabb_min[k] + cfg.aabb_max[k]) / 2 for k in range(3)]
+        h = 0.5 * max(cfg.aabb_max[k] - cfg.aabb_min[k] for k in range(3))
+        x = np.array([(p[k] - cen[k]) / h for k in range(3)])
+        m = np.abs(x).max()
+        y = x if m <= 1 else (2 - 1 / m) * x / m
+        g = [(y[k] + 2) / 4 * cfg.occ_res[k] for k in range(3)]
+    else:
+        g = [(p[k] - cfg.aabb_min[k]) / (cfg.aabb_max[k] - cfg.aabb_min[k]) * cfg.occ_res[k]
+             for k in range(3)]
     i = [int(math.floor(v)) for v in g]
     if any(i[k] < 0 or i[k] >= cfg.occ_res[k] for k in range(3)):
         return False
@@ -445,6 +546,9 @@ def make_scene(name: str, seed: int | None = None, with_params: bool = True) -> 
     elif name == "room_paper_grid":
         cfg, s = cfg_room_paper_grid(), 2 if seed is None else seed
         occ = occupancy_room(cfg.occ_res, cfg.aabb_max, 0.05, s)
+    elif name in ("room_unbounded", "room_unbounded_surface"):
+        cfg, s = cfg_room_unbounded(surface=name.endswith("surface")), 2 if seed is None else seed
+        occ = occupancy_unbounded(cfg, s)
     else:
         raise ValueError(name)
     grid = grid_params(cfg, s) if with_params else None

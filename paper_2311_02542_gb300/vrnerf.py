@@ -40,6 +40,7 @@ class FieldDesc(ctypes.Structure):
         ("t_near", ctypes.c_float), ("t_far", ctypes.c_float),
         ("lod_bias", ctypes.c_float), ("T_eps", ctypes.c_float),
         ("radius_scale", ctypes.c_float), ("density_bias", ctypes.c_float),
+        ("contract", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
 
@@ -146,6 +147,7 @@ def desc(cfg) -> FieldDesc:
     d.t_near, d.t_far = cfg.t_near, cfg.t_far
     d.lod_bias, d.T_eps = cfg.lod_bias, cfg.T_eps
     d.radius_scale, d.density_bias = cfg.radius_scale, cfg.density_bias
+    d.contract = int(getattr(cfg, "contract", False))
     return d
 
 

@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--serving-requests", type=int, default=300,
                     help="requests of the Poisson serving stream (0: skip)")
     ap.add_argument("--train-steps", type=int, default=5, help="timed 2^20-ray train steps (0: skip)")
+    ap.add_argument("--no-extra-workloads", action="store_true",
+                    help="skip the paper-grid / unbounded-room frames and the pruning pass")
     ap.add_argument("--profile-case", action="store_true",
                     help="small case for ncu: two renders of a 1024x1024 window of the room frame")
     return ap.parse_args()
@@ -240,8 +242,8 @@ def serving_bench(V, field, sc, n_req, warm=30, rate_hz=36.0 / 0.7, seed=4, in_f
             "note": "latency = submit to image in pinned host memory; fp16 tensor-core MLP"}
 
 
-def train_bench(V, sc, steps):
-    """Training step on a 2^20-ray batch drawn from 64 synthetic HDR views
+def train_bench(V, sc, steps, batch=1 << 20):
+    """Training step on a batch of rays drawn from 64 synthetic HDR views
     (targets log-uniform in [1e-3, 1e3]); forward, loss, backward, Adam."""
     import torch
     from paper_2311_02542_gb300 import synth as S
@@ -249,7 +251,7 @@ def train_bench(V, sc, steps):
     poses, intr = S.training_views(sc.occ, sc.cfg, n_views=64)
     batches = []
     for k in range(2):
-        o, d, r, tgt = S.training_batch(poses, intr, 1 << 20, seed=5, step=k)
+        o, d, r, tgt = S.training_batch(poses, intr, batch, seed=5, step=k)
         batches.append([torch.from_numpy(a).cuda() for a in (o, d, r, tgt)])
     for k in range(2):
         V.vrnerf_train_step(field, *batches[k % 2])
@@ -265,9 +267,63 @@ def train_bench(V, sc, steps):
     ms = float(np.mean([a.elapsed_time(b) for a, b in ts]))
     loss = V.vrnerf_backward(field, *batches[0])
     field.close()
-    return {"batch_rays": 1 << 20, "ms_per_step": round(ms, 3),
-            "Mrays_s": round((1 << 20) / (ms * 1e-3) / 1e6, 2), "loss": round(float(loss), 6),
+    return {"batch_rays": batch, "ms_per_step": round(ms, 3),
+            "Mrays_s": round(batch / (ms * 1e-3) / 1e6, 2), "loss": round(float(loss), 6),
             "steps": steps, "mlp": "fp32 (CUDA cores)"}
+
+
+def workload_bench(V, name, precision, steps, flush):
+    """One 2048^2 eye buffer of another scene shape: Mrays/s and work counters."""
+    import torch
+    from paper_2311_02542_gb300 import synth as S
+    sc = S.make_scene(name)
+    field = V.Field(sc.cfg, sc.grid, sc.mlp, sc.occ_bits)
+    c2w, K, res = S.camera_room(sc.occ, sc.cfg, 2, 2048, 2048)
+    cams, intr = torch.from_numpy(c2w).cuda(), torch.from_numpy(K).cuda()
+    rays = 2048 * 2048
+    out = torch.empty((rays, 3), device="cuda")
+    stats = torch.zeros(4, dtype=torch.int64, device="cuda")
+    V.vrnerf_render(field, cams, intr, res, out=out, precision=precision, stats=stats)
+    for _ in range(2):
+        V.vrnerf_render(field, cams, intr, res, out=out, precision=precision)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        V.vrnerf_render(field, cams, intr, res, out=out, precision=precision)
+        b.record()
+        ts.append((a, b))
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ts]))
+    n_samples, n_levels, n_steps, _ = [int(x) for x in stats.cpu()]
+    field.close()
+    cfg = sc.cfg
+    return {"Mrays_s": round(rays / (ms * 1e-3) / 1e6, 2), "ms_per_frame": round(ms, 3),
+            "samples_per_ray": round(n_samples / rays, 3), "steps_per_ray": round(n_steps / rays, 2),
+            "levels_per_sample": round(n_levels / max(n_samples, 1), 3),
+            "grid": {"levels": cfg.levels, "base_res": cfg.base_res, "growth": round(cfg.growth, 4),
+                     "log2_T": cfg.log2_T}, "contract": bool(cfg.contract), "t_far": cfg.t_far}
+
+
+def prune_bench(V, sc, k=4):
+    """One joint history/grid pruning pass (Sec. 4.3.2) over the scene's
+    occupancy grid, k^3 density evaluations per occupied voxel."""
+    import torch
+    from paper_2311_02542_gb300 import synth as S
+    field = V.Field(sc.cfg, sc.grid, sc.mlp, sc.occ_bits)
+    poses, _ = S.training_views(sc.occ, sc.cfg, n_views=64)
+    cams = poses[:, :3, 3].astype(np.float32)
+    V.vrnerf_history_reset(field)
+    V.vrnerf_prune(field, cams, k, 0.2, apply=False)
+    t0 = time.perf_counter()
+    kept, _, _ = V.vrnerf_prune(field, cams, k, 0.2, apply=False)
+    dt = time.perf_counter() - t0
+    occupied = int(sc.occ.sum())
+    field.close()
+    return {"ms": round(dt * 1e3, 2), "points_per_voxel": k ** 3, "occupied_voxels": occupied,
+            "kept_at_0.2": int(kept), "Mpoints_s": round(occupied * k ** 3 / dt / 1e6, 1)}
 
 
 def profile_case(args):
@@ -454,6 +510,16 @@ def main():
                                                   warm=10, rate_hz=1e9)
     if args.train_steps > 0:
         line["train_step"] = train_bench(V, sc, args.train_steps)
+        # the paper's batch: 12 800 rays (256 rays from each of 50 images)
+        line["train_step_paper_batch"] = train_bench(V, sc, max(args.train_steps, 20), batch=12800)
+    if not args.no_extra_workloads:
+        line["workloads"] = {
+            "room_paper_grid_2048": workload_bench(V, "room_paper_grid", tuned, max(3, args.steps // 2), flush),
+            "room_unbounded_2048": workload_bench(V, "room_unbounded", tuned, max(3, args.steps // 2), flush),
+            "room_unbounded_surface_2048": workload_bench(V, "room_unbounded_surface", tuned,
+                                                          max(3, args.steps // 2), flush),
+        }
+        line["prune_room_k4"] = prune_bench(V, sc)
     if rank == 0 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
         crays, cdt = run_oracle_sample(sc, c2w, K, args.cpu_seconds, threads)

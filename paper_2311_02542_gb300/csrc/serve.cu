@@ -20,8 +20,9 @@
 //    so the host sees a view complete only after its output is written; the
 //    host then copies the output slice to the request's buffer;
 //  - when a CTA has no rays and nothing is published, it polls with
-//    __nanosleep and leaves after an idle time limit (or on stop); the host
-//    relaunches the kernel when new work arrives and none is running.
+//    __nanosleep; the launch leaves as a whole once every CTA has been idle
+//    past a time limit (or on stop), and the host relaunches the kernel when
+//    new work arrives and none is running.
 // No device-side wait is unbounded.
 #include <algorithm>
 #include <atomic>
@@ -83,6 +84,7 @@ __global__ void __launch_bounds__(kTcThreads, kTcMinBlocks)
 serve_kernel(const FieldView f, ServeView *__restrict__ ring, const ServeCtl *__restrict__ ctl,
              unsigned int *__restrict__ cursor, const uint4 *__restrict__ wimg,
              unsigned long long idle_ns, unsigned long long *__restrict__ status) {
+    unsigned int *idle = cursor + 1;  // idle CTAs of this launch | quitting bit
     constexpr int D = 2 * L;
     extern __shared__ __align__(1024) unsigned char smem[];
     float *unused;
@@ -225,15 +227,38 @@ serve_kernel(const FieldView f, ServeView *__restrict__ ring, const ServeCtl *__
             if (__all_sync(FULL, have || starved)) break;
         }
         if (!__syncthreads_or(have)) {
-            // nothing to shade in this CTA: report, then wait for work or stop
+            // Nothing to shade in this CTA: report, then wait for work or stop.
+            // The kernel leaves as a whole: a CTA may only quit once every CTA
+            // of the launch is idle (idle[0] counts them; bit 31 marks the
+            // launch as quitting, after which no CTA takes work again). A CTA
+            // that left alone would shrink the kernel for as long as the
+            // others stay busy, and the host relaunches only a finished kernel.
             flush();
             if (threadIdx.x == 0) {
+                constexpr unsigned kQuit = 1u << 31;
                 s_quit = 0;
+                atomicAdd(idle, 1u);
                 const uint64_t t0 = tc::globaltimer_ns();
                 while (true) {
-                    if (ld_acquire_sys_s32(&ctl->stop)) { s_quit = 1; break; }
-                    if (atomicAdd(cursor, 0u) < ld_acquire_sys_u32(&ctl->n_views)) break;
-                    if (tc::globaltimer_ns() - t0 > idle_ns) { s_quit = 1; break; }
+                    const uint64_t waited = tc::globaltimer_ns() - t0;
+                    // after 500 idle limits a CTA quits whatever the others do
+                    // (bounded wait) and takes the launch with it
+                    if (ld_acquire_sys_s32(&ctl->stop) || waited > 500ull * idle_ns) {
+                        atomicOr(idle, kQuit);
+                        s_quit = 1;
+                        break;
+                    }
+                    const unsigned st = atomicAdd(idle, 0u);
+                    if (st & kQuit) { s_quit = 1; break; }
+                    if (atomicAdd(cursor, 0u) < ld_acquire_sys_u32(&ctl->n_views)) {
+                        if (atomicCAS(idle, st, st - 1u) == st) break;  // back to work
+                        continue;                                        // state moved: look again
+                    }
+                    // every CTA idle past the limit: the launch quits
+                    if (waited > idle_ns && atomicCAS(idle, gridDim.x, gridDim.x | kQuit) == gridDim.x) {
+                        s_quit = 1;
+                        break;
+                    }
                     __nanosleep(2000);
                 }
             }
@@ -468,6 +493,7 @@ int vrnerf_server::ensure_kernel() {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaError_t e = ensure_tc_image(F, prec == VRNERF_BF16 ? 1 : 0, kst);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cursor + 1, 0, sizeof(unsigned int), kst);  // idle state
     if (e == cudaSuccess) {
         const int fmt = prec == VRNERF_BF16 ? 1 : 0;
         if (F->view.L == 8)
@@ -566,8 +592,8 @@ int vrnerf_server_create(vrnerf_field *F, uint64_t hbm_budget_bytes, int32_t pre
     if (e == cudaSuccess) e = cudaHostAlloc(&S->done_h, sizeof(unsigned int) * kRing, cudaHostAllocMapped);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer(&S->ctl_d, S->ctl_h, 0);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer(&S->done_d, S->done_h, 0);
-    if (e == cudaSuccess) e = cudaMalloc(&S->cursor, sizeof(unsigned int));
-    if (e == cudaSuccess) e = cudaMemset(S->cursor, 0, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMalloc(&S->cursor, 2 * sizeof(unsigned int));  // cursor, idle state
+    if (e == cudaSuccess) e = cudaMemset(S->cursor, 0, 2 * sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMalloc(&S->arena_d, hbm_budget_bytes);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->kernel_done, cudaEventDisableTiming);
     if (e != cudaSuccess) {

@@ -125,7 +125,14 @@ void derive_view(const vrnerf_field_desc &d, FieldView &f, std::vector<float> &t
         c_max = fmax(c_max, (double)f.inv_cell[k]);
     }
     const double err = ldexp(1.0, -24) * (c_max * ((double)d.t_far + 2.0 * A + ext_max) + res_max);
-    f.skip = (16.0 * err < (double)f.skip_eps && !d.contract) ? 1 : 0;
+    f.skip = (16.0 * err < (double)f.skip_eps) ? 1 : 0;
+    if (d.contract) {
+        // contracted coordinates stay within [-2, 2]: a sample's rounding
+        // error there is a few ulps of 2 plus that of x = (p - cen) / h near
+        // the inner cube; the skip bound itself keeps a relative slack
+        const double err_c = ldexp(1.0, -24) * (8.0 + 4.0 * A * (double)f.inv_h) * res_max / 4.0;
+        f.skip = (16.0 * err_c < (double)f.skip_eps) ? 1 : 0;
+    }
     f.ln_tn = logf(d.t_near);
     f.inv_ln_q = (float)((double)d.max_steps / log((double)d.t_far / (double)d.t_near));
     // exponential sample distances t_i = t_near (t_far / t_near)^(i / S), fp64 -> fp32

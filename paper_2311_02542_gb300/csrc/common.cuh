@@ -131,7 +131,7 @@ __device__ __forceinline__ void contracted_position(const FieldView &f, const fl
 // The grid of a contracted scene covers all of space (coordinates clamped to
 // the last voxel, reached only where 2 - 1/m rounds to 2).
 __device__ __forceinline__ bool sample_voxel(const FieldView &f, const float o[3], const float d[3],
-                                             float t, float p[3], int &vox, int v[3]) {
+                                             float t, float p[3], int &vox, int v[3], float *gc = nullptr) {
 #pragma unroll
     for (int k = 0; k < 3; ++k) p[k] = __fadd_rn(o[k], __fmul_rn(t, d[k]));
     if (f.contract) {
@@ -139,7 +139,9 @@ __device__ __forceinline__ bool sample_voxel(const FieldView &f, const float o[3
         contracted_position(f, p, ph);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const int c = (int)floorf(__fmul_rn(ph[k], f.res_f[k]));
+            const float g = __fmul_rn(ph[k], f.res_f[k]);
+            if (gc) gc[k] = g;
+            const int c = (int)floorf(g);
             v[k] = c < 0 ? 0 : (c > f.res[k] - 1 ? f.res[k] - 1 : c);
         }
     } else {
@@ -178,6 +180,15 @@ __device__ __forceinline__ bool occupied(const uint32_t *__restrict__ occ, int v
 // skip_eps is far above the rounding error of the fp32 position and of the
 // exit distance (checked when the field is created), so each of those
 // samples would have been found, one by one, in an empty voxel of the cube.
+//
+// Contracted scenes: the ray is a curve in the grid, so the exit is bounded
+// instead of solved. With a = |x(s) - x(t)|_inf (x = (p - cen) / h), the
+// contracted point moves by at most K a in the L-infinity norm, K the largest
+// row sum of J_C on the way: 1 inside the inner cube, 4/m - 3/m^2 <= 4/3
+// outside, and <= 4/m for m >= 3; m >= m(t) - a along the segment. So with D
+// the clearance (grid cube shrunk by skip_eps, in contracted units) every
+// sample with a <= max(3D/4, D m / (4 + D) when m(t) >= 3 (4 + D) / 4) lies
+// in the cube; the faces on the grid's outer boundary are never crossed.
 // ---------------------------------------------------------------------------
 struct MarchRay {
     float o[3], d[3];
@@ -218,7 +229,8 @@ __device__ __forceinline__ int march_next(const FieldView &f, const float *__res
         if (m.step >= f.S) return MARCH_END;
         const float t = sT[m.step];
         int vox, v[3];
-        if (!sample_voxel(f, m.o, m.d, t, p, vox, v)) return MARCH_END;
+        float gc[3];
+        if (!sample_voxel(f, m.o, m.d, t, p, vox, v, gc)) return MARCH_END;
         ++tested;
         if (!f.skip) {
             if (occupied(f.occ, vox)) {
@@ -232,6 +244,27 @@ __device__ __forceinline__ int march_next(const FieldView &f, const float *__res
         if (dv == 0) {
             m.vox = vox;
             return MARCH_SAMPLE;
+        }
+        if (f.contract) {
+            float D = INFINITY, mx = 0.0f, dinf = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const int lo_i = v[k] - (dv - 1), hi_i = v[k] + dv;
+                const float cu = 4.0f / f.res_f[k];  // contracted units per voxel
+                if (lo_i > 0) D = fminf(D, (gc[k] - ((float)lo_i + f.skip_eps)) * cu);
+                if (hi_i < f.res[k]) D = fminf(D, (((float)hi_i - f.skip_eps) - gc[k]) * cu);
+                mx = fmaxf(mx, fabsf((p[k] - f.cen[k]) * f.inv_h));
+                dinf = fmaxf(dinf, fabsf(m.d[k]));
+            }
+            if (D > 0.0f && dinf > 0.0f) {
+                float a = 0.75f * D;
+                if (mx >= 0.75f * (4.0f + D)) a = fmaxf(a, D * mx / (4.0f + D));
+                const float t_skip = t + a / (dinf * f.inv_h);
+                m.step = first_sample_at(f, sT, t_skip, m.step + 1);
+            } else {
+                ++m.step;
+            }
+            continue;
         }
         float t_in = -INFINITY, t_out = INFINITY;
         bool ok = true;

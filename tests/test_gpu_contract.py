@@ -280,3 +280,36 @@ def test_contracted_serving_matches_rendering_alone(V, room):
     assert np.all(np.abs(out - want) <= TC_RTOL * np.abs(want) + TC_ATOL)
     srv.close()
     f.close()
+
+
+def test_contracted_skip_stress_room(V, room):
+    """The contracted empty-space skip (a Lipschitz bound of the contraction
+    along the ray) must reproduce the per-sample rule: camera rays through the
+    windows out to 4 km, rays from far outside, grazing and axis-parallel rays."""
+    cfg = room.cfg
+    f = V.Field(cfg, room.grid, room.mlp, room.occ_bits)
+    F = O.Field(cfg, room.grid, room.mlp, room.occ_bits)
+    rng = np.random.default_rng(22)
+    c2w, K, _ = S.camera_room(room.occ, cfg, 5, 2048, 2048, n=4)
+    o_list, d_list = [], []
+    for v in range(4):
+        Kc = S.crop_camera(K[v:v + 1], int(rng.integers(0, 1900)), int(rng.integers(0, 1900)))
+        o, d, _ = O.camera_rays(cfg, c2w[v:v + 1], Kc, np.array([[64, 64]], np.int32))
+        o_list.append(o)
+        d_list.append(d)
+    n = 6000
+    far_o = (np.array([10.0, 10.0, 1.5]) + rng.normal(size=(n, 3)) * rng.choice([5.0, 100.0, 2000.0], (n, 1)))
+    far_d = rng.normal(size=(n, 3))
+    far_d[: n // 6] = 0
+    far_d[np.arange(n // 6), rng.integers(0, 3, n // 6)] = rng.choice([-1.0, 1.0], n // 6)
+    far_d[n // 6: n // 3, 2] = rng.uniform(-1e-3, 1e-3, n // 6)  # nearly horizontal
+    far_d /= np.linalg.norm(far_d, axis=1, keepdims=True)
+    o = np.concatenate(o_list + [far_o.astype(np.float32)])
+    d = np.concatenate(d_list + [far_d.astype(np.float32)])
+    cap = cfg.max_steps
+    ri, rv, cnt = F.march(o, d, cap)
+    gi, gv, gc = (t.cpu().numpy() for t in V.vrnerf_debug_march(f, _cuda(o), _cuda(d), cap))
+    assert (gc == cnt).all()
+    assert (gi == ri).all() and (gv == rv).all()
+    assert cnt.sum() > 50000
+    f.close()

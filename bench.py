@@ -39,6 +39,12 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "room_2048x2048_single_eye"
 
 
+# DRAM bytes read + written by one 2048x2048 launch of render_tc_kernel<16, 0, 0>
+# (ncu dram__bytes_read.sum + dram__bytes_write.sum, one capture of the benchmark
+# frame); to be taken again whenever that kernel changes.
+NCU_TRAFFIC_BYTES = 53212928 + 25871616
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -494,7 +500,8 @@ def main():
         "e2e": {"value": round(e2e_v, 3), "unit": "Mrays/s", "h2d_bytes_per_step": 64,
                 "d2h_bytes_per_step": rays * 12},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": hbm_peak,
-                     "unit": "GB/s", "frac": round(achieved / hbm_peak, 5), "traffic": None,
+                     "unit": "GB/s", "frac": round(achieved / hbm_peak, 5),
+                     "traffic": NCU_TRAFFIC_BYTES if precision_name == "fp16" and args.variant == "room" else None,
                      "peak_kind": peak_kind, "kernel": "render (fused march+gather+MLP+composite)"},
         "gpu_launches": args.steps,
         "clocks": clocks,

@@ -20,7 +20,8 @@ Parity status per function (what pins it, see tests/test_oracle_*.py):
                           empty grid, early-termination bound, slab brute force;
                           depth: opaque first sample, bounds by t and opacity
   march                   brute-force occupancy visits on tiny grids
-  backward                central finite differences in fp64
+  backward / backward_grad central finite differences in fp64 (of the L1 loss, and of a
+                          random linear functional of the PQ colours)
   adam                    closed-form first and second steps
   prune / history         thresholds 0 and > 1, monotone in the threshold, constant-density
                           opacity against a brute-force nearest-camera spacing; history
@@ -154,6 +155,8 @@ def lib():
                                      _I32, _I32]),
                 "orc_backward": (ctypes.c_double, [_DP, _F64, _F64, _U32, _F32, _F32, _F32, _F32,
                                                    ctypes.c_int32, _F64, _F64]),
+                "orc_backward_grad": (None, [_DP, _F64, _F64, _U32, _F32, _F32, _F32, _F64,
+                                             ctypes.c_int32, _F64, _F64]),
                 "orc_adam": (None, [_F64, _F64, _F64, _F64, ctypes.c_int64, ctypes.c_int32,
                                     ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_double]),
@@ -417,6 +420,17 @@ class Field:
                                   _p(r, ctypes.c_float), _p(tgt, ctypes.c_float), B,
                                   _p(gg, ctypes.c_double), _p(gm, ctypes.c_double))
         return loss, gg, gm
+
+    def backward_grad(self, o, dd, r, gC):
+        """Gradients of sum_i gC_i . C_pq(ray i) for an upstream gradient gC [B][3]."""
+        o, dd, r = _f32(o).reshape(-1, 3), _f32(dd).reshape(-1, 3), _f32(r).reshape(-1)
+        g = _f64(gC).reshape(-1, 3)
+        gg = np.zeros_like(self.grid)
+        gm = np.zeros_like(self.mlp)
+        lib().orc_backward_grad(*self._args(), _p(self.occ, ctypes.c_uint32), _p(o, ctypes.c_float),
+                                _p(dd, ctypes.c_float), _p(r, ctypes.c_float), _p(g, ctypes.c_double),
+                                o.shape[0], _p(gg, ctypes.c_double), _p(gm, ctypes.c_double))
+        return gg, gm
 
 
 def prune(F, cams, k, threshold, hist=None):

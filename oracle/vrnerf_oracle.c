@@ -916,6 +916,39 @@ static void mlp_backward(const orc_desc *D, const double *mlp, orc_sample *s, do
 
 /* Loss and gradients for a batch of explicit rays. grid_grad [L][T][F] and
  * mlp_grad are overwritten. Returns the loss. */
+/* Back-propagates dL/dC_pq = gC of one ray through compositing (suffix
+ * sums S_i = sum_{j>i} w_j c_j, walked from the back), the MLPs and the
+ * hash-grid interpolation, adding into grid_grad and mlp_grad. */
+static void backprop_ray(const orc_desc *D, const orc_geom *g, const double *grid, const double *mlp,
+                         const double *dir, const orc_ray_out *ro, const orc_tape *tape, const double *gC,
+                         double *grid_grad, double *mlp_grad)
+{
+    int F = D->feats;
+    double suffix[3] = {0, 0, 0};
+    for (int32_t k = ro->n_eval - 1; k >= 0; --k) {
+        const orc_tape *e = &tape[k];
+        double w = e->Tin * e->alpha, Tout = e->Tin * (1.0 - e->alpha);
+        double dc[3], dsig = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            dc[c] = w * gC[c];
+            dsig += gC[c] * e->delta * (Tout * e->c[c] - suffix[c]);
+        }
+        orc_sample s;
+        sample_feats(D, g, grid, e->p, e->r_norm, &s);
+        mlp_forward(D, mlp, dir, &s);
+        double dfeat[ORC_MAX_LEVELS * 2];
+        mlp_backward(D, mlp, &s, dsig, dc, mlp_grad, dfeat);
+        for (int32_t l = 0; l < D->levels; ++l) {
+            if (s.wl[l] == 0.0) continue;
+            for (int b = 0; b < 8; ++b) {
+                double *gg = grid_grad + ((int64_t)l * g->T + s.idx[l][b]) * F;
+                for (int f = 0; f < F; ++f) gg[f] += s.wl[l] * s.cw[l][b] * dfeat[l * F + f];
+            }
+        }
+        for (int c = 0; c < 3; ++c) suffix[c] += w * e->c[c];
+    }
+}
+
 double orc_backward(const orc_desc *D, const double *grid, const double *mlp, const uint32_t *occ,
                     const float *o, const float *d, const float *r, const float *target_lin,
                     int32_t B, double *grid_grad, double *mlp_grad)
@@ -929,7 +962,6 @@ double orc_backward(const orc_desc *D, const double *grid, const double *mlp, co
     orc_sample_table(D, t_tab);
     orc_tape *tape = (orc_tape *)malloc(sizeof(orc_tape) * D->max_steps);
     double loss = 0.0;
-    int F = D->feats;
     for (int32_t i = 0; i < B; ++i) {
         const float *oi = o + 3 * i, *di = d + 3 * i;
         double dir[3] = {di[0], di[1], di[2]};
@@ -942,34 +974,36 @@ double orc_backward(const orc_desc *D, const double *grid, const double *mlp, co
             loss += fabs(diff);
             gC[c] = (diff > 0.0 ? 1.0 : (diff < 0.0 ? -1.0 : 0.0)) / (3.0 * B);
         }
-        /* suffix sums S_i = sum_{j>i} w_j c_j, walked from the back */
-        double suffix[3] = {0, 0, 0};
-        for (int32_t k = ro.n_eval - 1; k >= 0; --k) {
-            orc_tape *e = &tape[k];
-            double w = e->Tin * e->alpha, Tout = e->Tin * (1.0 - e->alpha);
-            double dc[3], dsig = 0.0;
-            for (int c = 0; c < 3; ++c) {
-                dc[c] = w * gC[c];
-                dsig += gC[c] * e->delta * (Tout * e->c[c] - suffix[c]);
-            }
-            orc_sample s;
-            sample_feats(D, &g, grid, e->p, e->r_norm, &s);
-            mlp_forward(D, mlp, dir, &s);
-            double dfeat[ORC_MAX_LEVELS * 2];
-            mlp_backward(D, mlp, &s, dsig, dc, mlp_grad, dfeat);
-            for (int32_t l = 0; l < D->levels; ++l) {
-                if (s.wl[l] == 0.0) continue;
-                for (int b = 0; b < 8; ++b) {
-                    double *gg = grid_grad + ((int64_t)l * g.T + s.idx[l][b]) * F;
-                    for (int f = 0; f < F; ++f) gg[f] += s.wl[l] * s.cw[l][b] * dfeat[l * F + f];
-                }
-            }
-            for (int c = 0; c < 3; ++c) suffix[c] += w * e->c[c];
-        }
+        backprop_ray(D, &g, grid, mlp, dir, &ro, tape, gC, grid_grad, mlp_grad);
     }
     free(tape);
     free(t_tab);
     return loss / (3.0 * B);
+}
+
+/* Gradient of sum_i gC_i . C_pq(ray i) for a given upstream gradient gC
+ * [B][3] (any loss on the PQ colours): grid_grad and mlp_grad overwritten. */
+void orc_backward_grad(const orc_desc *D, const double *grid, const double *mlp, const uint32_t *occ,
+                       const float *o, const float *d, const float *r, const double *gC, int32_t B,
+                       double *grid_grad, double *mlp_grad)
+{
+    orc_geom g;
+    geom_init(D, &g);
+    int64_t ngrid = (int64_t)D->levels * g.T * D->feats;
+    memset(grid_grad, 0, sizeof(double) * ngrid);
+    memset(mlp_grad, 0, sizeof(double) * orc_mlp_count(D));
+    float *t_tab = (float *)malloc(sizeof(float) * (D->max_steps + 1));
+    orc_sample_table(D, t_tab);
+    orc_tape *tape = (orc_tape *)malloc(sizeof(orc_tape) * D->max_steps);
+    for (int32_t i = 0; i < B; ++i) {
+        const float *oi = o + 3 * i, *di = d + 3 * i;
+        double dir[3] = {di[0], di[1], di[2]};
+        orc_ray_out ro;
+        render_one(D, &g, grid, mlp, occ, t_tab, oi, di, (double)r[i], NULL, NULL, &ro, tape, 0);
+        backprop_ray(D, &g, grid, mlp, dir, &ro, tape, gC + 3 * i, grid_grad, mlp_grad);
+    }
+    free(tape);
+    free(t_tab);
 }
 
 /* Adam (Kingma and Ba 2015) on one parameter array, step number t >= 1. */

@@ -469,6 +469,55 @@ def test_backward_matches_finite_differences():
     assert bad <= 2, bad  # at most a ReLU kink crossed by the finite step
 
 
+def test_backward_grad_matches_finite_differences():
+    """Gradient of a random linear functional sum_i gC_i . C_pq(ray i) of the
+    PQ colours (the upstream gradient of an arbitrary loss) against central
+    differences of that functional through the fp64 render."""
+    cfg = replace(S.cfg_unit_cube(), levels=4, log2_T=9, occ_res=(16, 16, 16), max_steps=48,
+                  T_eps=0.0)
+    rng = np.random.default_rng(16)
+    grid = rng.uniform(-1, 1, (cfg.levels, cfg.T, cfg.feats))
+    mlp = rng.normal(size=O.mlp_count(cfg)) * 0.4
+    occ = rng.uniform(size=(16, 16, 16)) < 0.4
+    F = O.Field(cfg, grid, mlp, S.pack_bits(occ))
+    B = 6
+    o = rng.uniform(0.3, 0.7, (B, 3)).astype(np.float32)
+    d = rng.normal(size=(B, 3))
+    d = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
+    r = np.full(B, 2e-3, np.float32)
+    gC = rng.normal(size=(B, 3))
+    gg, gm = F.backward_grad(o, d, r, gC)
+
+    def functional(g, m):
+        return float((O.Field(cfg, g, m, S.pack_bits(occ)).render_rays(o, d, r, threads=1)["pq"] * gC).sum())
+
+    h = 1e-6
+    touched = np.nonzero(gg.reshape(-1))[0]
+    picks = [("g", i) for i in rng.choice(touched, 40, replace=False)]
+    picks += [("m", i) for i in rng.choice(mlp.size, 100, replace=False)]
+    bad = 0
+    for kind, i in picks:
+        g2, m2 = grid.reshape(-1).copy(), mlp.copy()
+        arr = g2 if kind == "g" else m2
+        arr[i] += h
+        fp = functional(g2, m2)
+        arr[i] -= 2 * h
+        fm = functional(g2, m2)
+        fd = (fp - fm) / (2 * h)
+        an = (gg.reshape(-1) if kind == "g" else gm)[i]
+        if abs(fd - an) > 1e-7 + 1e-4 * abs(an):
+            bad += 1
+    assert bad <= 2, bad  # at most a ReLU kink crossed by the finite step
+    # with the L1 loss's upstream gradient it is the fused L1 backward
+    tgt = np.full((B, 3), 1e-3, np.float32)
+    C = F.render_rays(o, d, r, threads=1)["pq"]
+    g1 = np.sign(C - np.array([O.linear_to_pq(1e-3)] * 3)) / (3 * B)
+    _, ga, ma = F.backward(o, d, r, tgt)
+    gb, mb = F.backward_grad(o, d, r, g1)
+    np.testing.assert_allclose(gb, ga, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(mb, ma, rtol=1e-12, atol=1e-15)
+
+
 def test_adam_closed_form():
     g1 = np.array([0.5, -2e-3, 0.0, 7.0])
     g2 = np.array([-0.25, 4e-3, 1.0, 7.0])

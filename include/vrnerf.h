@@ -236,6 +236,29 @@ int vrnerf_backward(vrnerf_field *field, const float *rays_o, const float *rays_
                     const float *radii, const float *target_linear, int32_t B, float *loss_host,
                     void *stream);
 
+/* Backward for an arbitrary loss on the PQ colours (the hand-written
+ * backward behind an autograd function): the gradient of
+ * sum_i grad_pq[i] . C_pq(ray i) with respect to every hash-grid entry and
+ * MLP weight into the field's gradient buffers (overwritten). pq_fwd [B][3]
+ * and n_fwd [B] are the PQ colours and sample counts that vrnerf_render_rays
+ * (VRNERF_FP32) returned for the same rays and parameters; the samples are
+ * recomputed per ray, none are stored. All arrays device memory; asynchronous
+ * on `stream`. EINVAL, ENOMEM, ECUDA. */
+int vrnerf_backward_from_grad(vrnerf_field *field, const float *rays_o, const float *rays_d,
+                              const float *radii, int32_t B, const float *pq_fwd,
+                              const int32_t *n_fwd, const float *grad_pq, void *stream);
+
+/* Device pointers of the field's parameters ([L][T][F] grid in its storage
+ * type, fp32 MLP) and fp32 gradient buffers (allocated on the first call
+ * that asks for them), valid until vrnerf_field_destroy; any output may be
+ * NULL. For frameworks that view them as tensors. A caller that writes the
+ * parameters must then call vrnerf_field_params_changed, which refreshes the
+ * derived copies (tensor-core weight images, the fp32 master of an fp16
+ * grid). EINVAL, ENOMEM. */
+int vrnerf_field_param_ptrs(vrnerf_field *field, void **grid, float **mlp, float **grid_grad,
+                            float **mlp_grad);
+int vrnerf_field_params_changed(vrnerf_field *field);
+
 /* Display tonemapping of an existing PQ image (the exposure sweep of the
  * paper's results: PQ colour to sRGB at a chosen exposure, without
  * re-rendering). pq [n][3] and optional T [n] (NULL: alpha 255) in device

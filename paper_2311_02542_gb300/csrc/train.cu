@@ -462,7 +462,7 @@ void release_train_scratch(vrnerf_field *F) {
 
 template <int L>
 static cudaError_t launch_backward_t(vrnerf_field *F, const float *o, const float *d, const float *r, int B,
-                                     const TrainScratch &S, cudaStream_t st) {
+                                     const float *C_fin, const int *n_fin, const float *gC, cudaStream_t st) {
     constexpr int D = 2 * L;
     const size_t smem = sizeof(float) * ((size_t)GradSm<D>::size + ((F->view.S + 1 + 3) & ~3) +
                                          (size_t)(kBwdThreads / 32) * 2 * 32 * kStride);
@@ -476,7 +476,7 @@ static cudaError_t launch_backward_t(vrnerf_field *F, const float *o, const floa
     if (want < grid) grid = want;
     unsigned long long *cnt = reinterpret_cast<unsigned long long *>(F->counter);
     if ((e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
-    kern<<<(unsigned)grid, kBwdThreads, smem, st>>>(F->view, o, d, r, B, S.C, S.n, S.gC, F->grid_grad, F->mlp_grad,
+    kern<<<(unsigned)grid, kBwdThreads, smem, st>>>(F->view, o, d, r, B, C_fin, n_fin, gC, F->grid_grad, F->mlp_grad,
                                                    cnt);
     return cudaGetLastError();
 }
@@ -517,8 +517,8 @@ int vrnerf_backward(vrnerf_field *F, const float *rays_o, const float *rays_d, c
             e = cudaGetLastError();
         }
         if (e == cudaSuccess)
-            e = F->view.L == 8 ? launch_backward_t<8>(F, rays_o, rays_d, radii, B, S, st)
-                               : launch_backward_t<16>(F, rays_o, rays_d, radii, B, S, st);
+            e = F->view.L == 8 ? launch_backward_t<8>(F, rays_o, rays_d, radii, B, S.C, S.n, S.gC, st)
+                               : launch_backward_t<16>(F, rays_o, rays_d, radii, B, S.C, S.n, S.gC, st);
         if (e != cudaSuccess) return cuda_fail(e, "backward");
         if (loss_host) {
             float sum = 0.0f;
@@ -531,6 +531,55 @@ int vrnerf_backward(vrnerf_field *F, const float *rays_o, const float *rays_d, c
     } catch (...) {
         return fail(VRNERF_EINVAL, "backward: unexpected C++ exception");
     }
+}
+
+int vrnerf_backward_from_grad(vrnerf_field *F, const float *rays_o, const float *rays_d, const float *radii,
+                              int32_t B, const float *pq_fwd, const int32_t *n_fwd, const float *grad_pq,
+                              void *stream) {
+    try {
+        if (!F || !rays_o || !rays_d || !radii || !pq_fwd || !n_fwd || !grad_pq)
+            return fail(VRNERF_EINVAL, "NULL argument");
+        if (B < 1) return fail(VRNERF_EINVAL, "B must be >= 1");
+        int rc = ensure_train(F, 1);
+        if (rc) return rc;
+        cudaStream_t st = (cudaStream_t)stream;
+        cudaError_t e = cudaMemsetAsync(F->grid_grad, 0, grid_entries(F->desc) * sizeof(float), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(F->mlp_grad, 0, sizeof(float) * F->view.n_mlp, st);
+        if (e == cudaSuccess)
+            e = F->view.L == 8 ? launch_backward_t<8>(F, rays_o, rays_d, radii, B, pq_fwd, n_fwd, grad_pq, st)
+                               : launch_backward_t<16>(F, rays_o, rays_d, radii, B, pq_fwd, n_fwd, grad_pq, st);
+        if (e != cudaSuccess) return cuda_fail(e, "backward_from_grad");
+        return VRNERF_OK;
+    } catch (...) {
+        return fail(VRNERF_EINVAL, "backward_from_grad: unexpected C++ exception");
+    }
+}
+
+int vrnerf_field_param_ptrs(vrnerf_field *F, void **grid, float **mlp, float **grid_grad, float **mlp_grad) {
+    if (!F) return fail(VRNERF_EINVAL, "field is NULL");
+    if (grid_grad || mlp_grad) {
+        int rc = ensure_train(F, 1);
+        if (rc) return rc;
+    }
+    if (grid) *grid = F->grid;
+    if (mlp) *mlp = F->mlp;
+    if (grid_grad) *grid_grad = F->grid_grad;
+    if (mlp_grad) *mlp_grad = F->mlp_grad;
+    return VRNERF_OK;
+}
+
+int vrnerf_field_params_changed(vrnerf_field *F) {
+    if (!F) return fail(VRNERF_EINVAL, "field is NULL");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess && F->grid_master && F->desc.feat_fp16) {
+        const long long ng = (long long)grid_entries(F->desc);
+        half_to_float_kernel<<<num_sms() * 8, 256>>>(static_cast<const __half *>(F->grid), F->grid_master, ng);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "params_changed");
+    ++F->mlp_version;
+    return VRNERF_OK;
 }
 
 int vrnerf_field_get_grads(vrnerf_field *F, float *grid_grad_host, float *mlp_grad_host) {

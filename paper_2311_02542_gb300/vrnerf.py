@@ -66,6 +66,9 @@ _SIGS = {
     "vrnerf_field_set_occupancy": (ctypes.c_int, [_VP, _VP]),
     "vrnerf_field_save": (ctypes.c_int, [_VP, ctypes.c_char_p]),
     "vrnerf_history_reset": (ctypes.c_int, [_VP]),
+    "vrnerf_backward_from_grad": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP, _VP]),
+    "vrnerf_field_param_ptrs": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "vrnerf_field_params_changed": (ctypes.c_int, [_VP]),
     "vrnerf_tonemap": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, _F, _VP, _VP]),
     "vrnerf_occupancy_upsample": (ctypes.c_int, [_VP, _I32]),
     "vrnerf_field_get_occupancy": (ctypes.c_int, [_VP, _VP]),
@@ -258,6 +261,92 @@ def vrnerf_tonemap(pq, T=None, exposure_ev=0.0, out=None, stream=None):
     _check(load().vrnerf_tonemap(_ptr(_dev(pq)), _ptr(None if T is None else _dev(T)), n,
                                  float(exposure_ev), _ptr(_dev(out, torch.int32)), _stream(stream)))
     return out
+
+
+def vrnerf_backward_from_grad(field: Field, rays_o, rays_d, radii, pq_fwd, n_fwd, grad_pq, stream=None):
+    B = rays_o.shape[0]
+    _check(load().vrnerf_backward_from_grad(field.h, _ptr(_dev(rays_o)), _ptr(_dev(rays_d)), _ptr(_dev(radii)),
+                                            B, _ptr(_dev(pq_fwd)), _ptr(_dev(n_fwd, torch.int32)),
+                                            _ptr(_dev(grad_pq)), _stream(stream)))
+
+
+class _DeviceArray:
+    """A device buffer of the library described by __cuda_array_interface__,
+    so that torch.as_tensor views it without a copy."""
+
+    def __init__(self, ptr, shape, typestr, owner):
+        self.owner = owner  # keeps the field alive as long as the view
+        self.__cuda_array_interface__ = {"shape": tuple(int(x) for x in shape), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3, "strides": None}
+
+
+def vrnerf_field_param_views(field: Field, grads=True):
+    """Zero-copy torch views of the field's parameters (grid [L][T][F] in its
+    storage type, mlp fp32) and, with grads, of its fp32 gradient buffers."""
+    cfg = field.cfg
+    g, m, gg, gm = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    _check(load().vrnerf_field_param_ptrs(field.h, ctypes.byref(g), ctypes.byref(m),
+                                          ctypes.byref(gg) if grads else None,
+                                          ctypes.byref(gm) if grads else None))
+    shape = (cfg.levels, cfg.T, cfg.feats)
+    out = {"grid": torch.as_tensor(_DeviceArray(g.value, shape, "<f2" if cfg.feat_fp16 else "<f4", field),
+                                   device="cuda"),
+           "mlp": torch.as_tensor(_DeviceArray(m.value, (cfg.n_mlp(),), "<f4", field), device="cuda")}
+    if grads:
+        out["grid_grad"] = torch.as_tensor(_DeviceArray(gg.value, shape, "<f4", field), device="cuda")
+        out["mlp_grad"] = torch.as_tensor(_DeviceArray(gm.value, (cfg.n_mlp(),), "<f4", field), device="cuda")
+    return out
+
+
+def vrnerf_field_params_changed(field: Field):
+    _check(load().vrnerf_field_params_changed(field.h))
+
+
+class RenderRaysFunction(torch.autograd.Function):
+    """PQ colours of explicit rays (fp32 path) as a differentiable function of
+    the field's parameters: forward renders through the library, backward
+    runs its hand-written backward kernel (samples recomputed per ray)."""
+
+    @staticmethod
+    def forward(ctx, field, rays_o, rays_d, radii, grid, mlp):
+        B = rays_o.shape[0]
+        pq = torch.empty((B, 3), device=rays_o.device, dtype=torch.float32)
+        n = torch.empty(B, device=rays_o.device, dtype=torch.int32)
+        vrnerf_render_rays(field, rays_o, rays_d, radii, precision=FP32, out_pq=pq, out_n=n)
+        ctx.field = field
+        ctx.save_for_backward(rays_o, rays_d, radii, pq, n)
+        return pq
+
+    @staticmethod
+    def backward(ctx, grad_pq):
+        o, d, r, pq, n = ctx.saved_tensors
+        field = ctx.field
+        vrnerf_backward_from_grad(field, o, d, r, pq, n, grad_pq.contiguous())
+        v = vrnerf_field_param_views(field)
+        gg = v["grid_grad"].clone()
+        if field.cfg.feat_fp16:
+            gg = gg.to(torch.float16)
+        return None, None, None, None, gg, v["mlp_grad"].clone()
+
+
+class FieldModule(torch.nn.Module):
+    """The field as a torch module: parameters are views of the library's
+    buffers, forward(rays_o, rays_d, radii) returns PQ colours [B][3]. After
+    changing the parameters outside the library (a torch optimiser step),
+    call params_changed() before rendering with the tensor-core paths."""
+
+    def __init__(self, field: Field):
+        super().__init__()
+        self.field = field
+        v = vrnerf_field_param_views(field, grads=False)
+        self.grid = torch.nn.Parameter(v["grid"])
+        self.mlp = torch.nn.Parameter(v["mlp"])
+
+    def forward(self, rays_o, rays_d, radii):
+        return RenderRaysFunction.apply(self.field, rays_o, rays_d, radii, self.grid, self.mlp)
+
+    def params_changed(self):
+        vrnerf_field_params_changed(self.field)
 
 
 def vrnerf_history_reset(field: Field):

@@ -231,7 +231,11 @@ int vrnerf_debug_corners(vrnerf_field *field, const float *pos, int32_t n, uint3
  * |C_pq - PQ(target / 100)| and its gradient with respect to every hash-grid
  * entry and MLP weight into the field's gradient buffers (overwritten).
  * target_linear [B][3] device memory. loss_host (may be NULL) receives the
- * loss; when it is non-NULL the call synchronises `stream`. EINVAL, ECUDA. */
+ * loss. The batch runs sample-parallel: rays are marched and their samples
+ * listed, evaluated one thread per sample, composited per ray, and
+ * back-propagated one thread per sample (recomputing features and
+ * activations). The call waits for `stream` once (the sample count sizes
+ * its buffers). EINVAL, ENOMEM, ECUDA. */
 int vrnerf_backward(vrnerf_field *field, const float *rays_o, const float *rays_d,
                     const float *radii, const float *target_linear, int32_t B, float *loss_host,
                     void *stream);
@@ -239,14 +243,16 @@ int vrnerf_backward(vrnerf_field *field, const float *rays_o, const float *rays_
 /* Backward for an arbitrary loss on the PQ colours (the hand-written
  * backward behind an autograd function): the gradient of
  * sum_i grad_pq[i] . C_pq(ray i) with respect to every hash-grid entry and
- * MLP weight into the field's gradient buffers (overwritten). pq_fwd [B][3]
- * and n_fwd [B] are the PQ colours and sample counts that vrnerf_render_rays
- * (VRNERF_FP32) returned for the same rays and parameters; the samples are
- * recomputed per ray, none are stored. All arrays device memory; asynchronous
- * on `stream`. EINVAL, ENOMEM, ECUDA. */
+ * MLP weight into the field's gradient buffers (overwritten). n_fwd [B] are
+ * the sample counts that vrnerf_render_rays (VRNERF_FP32) returned for the
+ * same rays and parameters: ray i composites exactly n_fwd[i] samples, as in
+ * that forward pass; samples are recomputed, only sigma, colour and their
+ * gradients are kept per sample. All arrays device memory; the call waits
+ * for `stream` once (the sample count sizes its buffers). EINVAL, ENOMEM,
+ * ECUDA. */
 int vrnerf_backward_from_grad(vrnerf_field *field, const float *rays_o, const float *rays_d,
-                              const float *radii, int32_t B, const float *pq_fwd,
-                              const int32_t *n_fwd, const float *grad_pq, void *stream);
+                              const float *radii, int32_t B, const int32_t *n_fwd,
+                              const float *grad_pq, void *stream);
 
 /* Device pointers of the field's parameters ([L][T][F] grid in its storage
  * type, fp32 MLP) and fp32 gradient buffers (allocated on the first call

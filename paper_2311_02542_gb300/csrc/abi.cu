@@ -397,7 +397,6 @@ static int render_common(vrnerf_field *F, const RaySource &src, float *out,
                  opts ? opts->out_n : nullptr,
                  opts ? reinterpret_cast<unsigned long long *>(opts->stats) : nullptr,
                  opts ? opts->out_depth : nullptr,
-                 nullptr,
                  opts ? opts->out_normal : nullptr,
                  opts ? reinterpret_cast<unsigned int *>(opts->out_rgba8) : nullptr,
                  opts ? exp2f(opts->exposure_ev) : 1.0f};

@@ -71,7 +71,6 @@ struct RenderOut {
     int *n;       // optional
     unsigned long long *stats;  // optional [4]: samples, levels fetched, steps tested, rays
     float *depth;               // optional: sum_i w_i t_i
-    float *hist;                // optional per-voxel max opacity of composited samples
     float *normal;              // optional [rays][3]: sum_i w_i n_i (fp32 kernel only)
     unsigned int *rgba8;        // optional [rays]: sRGB8 + coverage at `exposure`
     float exposure;             // 2^ev, linear scale applied before the sRGB encoding
@@ -194,7 +193,6 @@ struct MarchRay {
     float o[3], d[3];
     float g0[3], inv_s[3];  // grid coordinate at t = 0 and 1 / (grid units per unit t)
     int step;
-    int vox;                // voxel of the sample last returned
 };
 
 __device__ __forceinline__ void march_init(const FieldView &f, MarchRay &m) {
@@ -233,18 +231,12 @@ __device__ __forceinline__ int march_next(const FieldView &f, const float *__res
         if (!sample_voxel(f, m.o, m.d, t, p, vox, v, gc)) return MARCH_END;
         ++tested;
         if (!f.skip) {
-            if (occupied(f.occ, vox)) {
-                m.vox = vox;
-                return MARCH_SAMPLE;
-            }
+            if (occupied(f.occ, vox)) return MARCH_SAMPLE;
             ++m.step;
             continue;
         }
         const int dv = (int)__ldg(f.dist + vox);
-        if (dv == 0) {
-            m.vox = vox;
-            return MARCH_SAMPLE;
-        }
+        if (dv == 0) return MARCH_SAMPLE;
         if (f.contract) {
             float D = INFINITY, mx = 0.0f, dinf = 0.0f;
 #pragma unroll

@@ -2,24 +2,33 @@
 // Design"): L1 loss in PQ space, its gradient through compositing, the
 // colour and density MLPs and the hash grid, and Adam.
 //
-// 1. forward: the fp32 renderer on the batch's rays gives each ray's
-//    composited PQ colour C and the number n of composited samples;
-// 2. loss: mean |C - PQ(target / 100)|, dL/dC = sign(C - target) / (3B);
-// 3. backward: every ray is marched again and its samples recomputed in order
-//    (nothing per sample is stored between the passes). With w_i = T_i a_i
-//    and the suffix S_i = C - sum_{j<=i} w_j c_j:
-//        dL/dc_i = w_i dL/dC,   dL/dsigma_i = delta_i (T_{i+1} c_i - S_i) . dL/dC,
-//    then the colour and density MLPs are back-propagated per sample on the
-//    CUDA cores; each warp stages its 32 samples' layer inputs and deltas in
-//    shared memory and accumulates the weight gradients as 32-sample
-//    mini-GEMMs into a per-CTA accumulator; feature gradients are scattered
-//    into the hash grid with float2 atomics (weight w_l x trilinear weight).
-// 4. Adam (beta = 0.9, 0.99, eps = 1e-15): fp32 master parameters, first and
+// The batch is processed sample-parallel, so that small batches (the paper's
+// 12 800 rays) still fill the GPU:
+// 1. count / emit: every ray is marched (occupancy rule of Sec. 4.3, no
+//    early termination) and its evaluated samples are listed contiguously
+//    as (ray, step) records;
+// 2. sample forward: one thread per sample gathers the LOD-weighted features
+//    and runs the fp32 MLPs: sigma and PQ colour per sample;
+// 3. ray composite: one thread per ray composites its samples front to back
+//    (stopping where transmittance drops below T_eps, or after the number of
+//    samples a forward pass reported), forms dL/dC (L1: sign(C - target) /
+//    3B, or a given upstream gradient) and walks its samples backwards: with
+//    w_i = T_i a_i and the suffix S_i = C - sum_{j<=i} w_j c_j,
+//        dL/dc_i = w_i dL/dC,   dL/dsigma_i = delta_i (T_{i+1} c_i - S_i) . dL/dC;
+// 4. sample backward: one thread per sample recomputes its features and
+//    activations (nothing but sigma, colour and these two gradients is kept
+//    per sample) and back-propagates the MLPs; each warp stages its 32
+//    samples' layer inputs and deltas in shared memory and accumulates the
+//    weight gradients as 32-sample mini-GEMMs into a per-CTA accumulator;
+//    feature gradients are scattered into the hash grid with float2 atomics
+//    (weight w_l x trilinear weight).
+// 5. Adam (beta = 0.9, 0.99, eps = 1e-15): fp32 master parameters, first and
 //    second moments; an fp16 grid is rewritten from its master copy.
 #include <cmath>
 #include <cstring>
 
 #include "field.h"
+#include "simt_mlp.cuh"
 
 namespace vrn {
 
@@ -102,136 +111,252 @@ __device__ __forceinline__ void minigemm_cols(const float *sD, const float *sA, 
     }
 }
 
+// ---- 1. count / emit ----------------------------------------------------
+// Evaluated samples of ray b (no early termination) and the start of its
+// records: one atomic per warp reserves the warp's records.
+__global__ void __launch_bounds__(128)
+count_kernel(const FieldView f, const float *__restrict__ o_in, const float *__restrict__ d_in, int B,
+             int *__restrict__ cnt, long long *__restrict__ off, unsigned long long *__restrict__ total) {
+    const int lane = threadIdx.x & 31;
+    for (long long b0 = (long long)blockIdx.x * blockDim.x; b0 < B; b0 += (long long)gridDim.x * blockDim.x) {
+        const long long b = b0 + threadIdx.x;
+        int n = 0;
+        if (b < B) {
+            MarchRay m;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                m.o[k] = o_in[3 * b + k];
+                m.d[k] = d_in[3 * b + k];
+            }
+            march_init(f, m);
+            unsigned tested = 0;
+            float p[3];
+            while (march_next(f, f.t_tab, m, p, 1 << 30, tested) == MARCH_SAMPLE) {
+                ++n;
+                ++m.step;
+            }
+        }
+        int incl = n;
+#pragma unroll
+        for (int s = 1; s < 32; s <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, s);
+            if (lane >= s) incl += v;
+        }
+        unsigned long long base = 0;
+        if (lane == 31) base = atomicAdd(total, (unsigned long long)incl);
+        base = __shfl_sync(0xffffffffu, base, 31);
+        if (b < B) {
+            cnt[b] = n;
+            off[b] = (long long)base + incl - n;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(128)
+emit_kernel(const FieldView f, const float *__restrict__ o_in, const float *__restrict__ d_in, int B,
+            const long long *__restrict__ off, int2 *__restrict__ rec) {
+    for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < B; b += (long long)gridDim.x * blockDim.x) {
+        MarchRay m;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            m.o[k] = o_in[3 * b + k];
+            m.d[k] = d_in[3 * b + k];
+        }
+        march_init(f, m);
+        unsigned tested = 0;
+        float p[3];
+        long long q = off[b];
+        while (march_next(f, f.t_tab, m, p, 1 << 30, tested) == MARCH_SAMPLE) {
+            rec[q++] = make_int2((int)b, m.step);
+            ++m.step;
+        }
+    }
+}
+
+// ---- 2. sample forward ------------------------------------------------------
+template <int L>
+__global__ void __launch_bounds__(128)
+sample_fwd_kernel(const FieldView f, const float *__restrict__ o_in, const float *__restrict__ d_in,
+                  const float *__restrict__ r_in, const int2 *__restrict__ rec, long long n,
+                  float4 *__restrict__ sc) {
+    constexpr int D = 2 * L;
+    extern __shared__ float4 smem4[];
+    float *sW = reinterpret_cast<float *>(smem4);
+    load_weights_simt<D>(f.mlp, sW);
+    __syncthreads();
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int2 q = rec[i];
+        const long long b = q.x;
+        const float o[3] = {o_in[3 * b], o_in[3 * b + 1], o_in[3 * b + 2]};
+        const float d[3] = {d_in[3 * b], d_in[3 * b + 1], d_in[3 * b + 2]};
+        const float t = f.t_tab[q.y];
+        float p[3];
+        int vox;
+        sample_voxel(f, o, d, t, p, vox);  // the march's fp32 position
+        float feat[D], sigma, rgb[3];
+        gather_features<L>(f, p, footprint(f, t, r_in[b], p, nullptr, nullptr), feat);
+        mlp_simt<D>(sW, feat, d, f.density_bias, sigma, rgb);
+        sc[i] = make_float4(sigma, rgb[0], rgb[1], rgb[2]);
+    }
+}
+
+// ---- 3. ray composite: C, dL/dC, per-sample gradients -----------------------
+// n_given (nullable): composite exactly that many samples (a forward pass's
+// count); else stop after the sample where T < T_eps. target (nullable): L1
+// loss against PQ(target / 100), else gC_given is dL/dC. Overwrites sc with
+// (dL/dsigma, dL/dz_0..2) of every composited sample (z: pre-sigmoid colour)
+// and zeros for the rest.
+__global__ void __launch_bounds__(128)
+ray_comp_kernel(const FieldView f, const float *__restrict__ o_in, const float *__restrict__ d_in, int B,
+                const int *__restrict__ cnt, const long long *__restrict__ off, const int2 *__restrict__ rec,
+                const int *__restrict__ n_given, const float *__restrict__ target, const float *__restrict__ gC_given,
+                float inv_n, float4 *__restrict__ sc, int *__restrict__ n_used, float *__restrict__ loss_sum,
+                float *__restrict__ hist) {
+    float loss = 0.0f;
+    for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < B; b += (long long)gridDim.x * blockDim.x) {
+        const long long k0 = off[b];
+        const int m = cnt[b];
+        const int lim = n_given ? min(n_given[b], m) : m;
+        float T = 1.0f, C[3] = {0, 0, 0};
+        int n = 0;
+        while (n < lim) {
+            const float4 v = sc[k0 + n];
+            const int step = rec[k0 + n].y;
+            const float t = f.t_tab[step], sd = v.x * (f.t_tab[step + 1] - t);
+            const float alpha = -expm1f(-sd), w = T * alpha;
+            C[0] += w * v.y;
+            C[1] += w * v.z;
+            C[2] += w * v.w;
+            if (hist) {
+                const float o[3] = {o_in[3 * b], o_in[3 * b + 1], o_in[3 * b + 2]};
+                const float d[3] = {d_in[3 * b], d_in[3 * b + 1], d_in[3 * b + 2]};
+                float p[3];
+                int vox;
+                sample_voxel(f, o, d, t, p, vox);
+                atomicMax(reinterpret_cast<int *>(hist) + vox, __float_as_int(alpha));
+            }
+            T *= expf(-sd);
+            ++n;
+            if (!n_given && T < f.T_eps) break;
+        }
+        float g[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            if (target) {
+                const float diff = C[c] - linear_to_pq(target[3 * b + c]);
+                g[c] = diff > 0.0f ? inv_n : (diff < 0.0f ? -inv_n : 0.0f);
+                loss += fabsf(diff);
+            } else {
+                g[c] = gC_given[3 * b + c];
+            }
+        }
+        float Cpre[3] = {0, 0, 0};
+        T = 1.0f;
+        for (int k = 0; k < n; ++k) {
+            const float4 v = sc[k0 + k];
+            const int step = rec[k0 + k].y;
+            const float delta = f.t_tab[step + 1] - f.t_tab[step], sd = v.x * delta;
+            const float alpha = -expm1f(-sd), Tn = T * expf(-sd), w = T * alpha;
+            const float cc[3] = {v.y, v.z, v.w};
+            float dsig = 0.0f, dz[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float suffix = C[c] - (Cpre[c] + w * cc[c]);
+                dsig += g[c] * delta * (Tn * cc[c] - suffix);
+                dz[c] = w * g[c] * cc[c] * (1.0f - cc[c]);
+                Cpre[c] += w * cc[c];
+            }
+            sc[k0 + k] = make_float4(dsig, dz[0], dz[1], dz[2]);
+            T = Tn;
+        }
+        for (int k = n; k < m; ++k) sc[k0 + k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        n_used[b] = n;
+    }
+    if (loss_sum) {
+#pragma unroll
+        for (int k = 16; k > 0; k >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, k);
+        if ((threadIdx.x & 31) == 0 && loss != 0.0f) atomicAdd(loss_sum, loss);
+    }
+}
+
+// ---- 4. sample backward -------------------------------------------------------
 template <int L>
 __global__ void __launch_bounds__(kBwdThreads)
-backward_kernel(const FieldView f, const float *__restrict__ o_in, const float *__restrict__ d_in,
-                const float *__restrict__ r_in, int B, const float *__restrict__ C_fin,
-                const int *__restrict__ n_fin, const float *__restrict__ gC_in,
-                float *__restrict__ grid_grad, float *__restrict__ mlp_grad,
-                unsigned long long *__restrict__ counter) {
+sample_bwd_kernel(const FieldView f, const float *__restrict__ o_in, const float *__restrict__ d_in,
+                  const float *__restrict__ r_in, const int2 *__restrict__ rec, const long long *__restrict__ off,
+                  const int *__restrict__ n_used, long long n_samples, const float4 *__restrict__ grad_s,
+                  float *__restrict__ grid_grad, float *__restrict__ mlp_grad) {
     constexpr int D = 2 * L;
     using G = GradSm<D>;
     extern __shared__ float4 smem4[];
     float *sG = reinterpret_cast<float *>(smem4);
-    float *sT = sG + G::size;
-    float *stage = sT + ((f.S + 1 + 3) & ~3);
+    float *stage = sG + G::size;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float *sA = stage + warp * 2 * 32 * kStride;
     float *sD = sA + 32 * kStride;
     for (int i = threadIdx.x; i < G::size; i += blockDim.x) sG[i] = 0.0f;
-    for (int i = threadIdx.x; i <= f.S; i += blockDim.x) sT[i] = f.t_tab[i];
     __syncthreads();
 
     const float *W1 = f.mlp, *W2 = W1 + 64 * D, *W3 = W2 + 16 * 64, *W4 = W3 + 64 * 32, *W5 = W4 + 64 * 64;
     constexpr unsigned FULL = 0xffffffffu;
-    long long ray = -1;
-    bool exhausted = false;
-    MarchRay mr;
-    float r = 0.0f, T = 1.0f, Cpre[3] = {0, 0, 0}, Cf[3] = {0, 0, 0}, g[3] = {0, 0, 0};
-    int k_done = 0, n_tot = 0;
-    unsigned tested = 0;
-
-    while (true) {
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long base = ((long long)blockIdx.x * (blockDim.x >> 5) + warp) * 32; base < n_samples;
+         base += warps * 32) {
+        const long long i = base + lane;
         bool have = false;
-        float p[3] = {0, 0, 0};
-        while (true) {
-            const bool need = ray < 0 && !exhausted;
-            const unsigned m = __ballot_sync(FULL, need);
-            if (m) {
-                const int leader = __ffs(m) - 1;
-                unsigned long long base = 0;
-                if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(m));
-                base = __shfl_sync(FULL, base, leader);
-                if (need) {
-                    const long long b = (long long)base + __popc(m & ((1u << lane) - 1u));
-                    if (b >= B) {
-                        exhausted = true;
-                    } else if (n_fin[b] > 0) {
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            mr.o[c] = o_in[3 * b + c];
-                            mr.d[c] = d_in[3 * b + c];
-                            Cf[c] = C_fin[3 * b + c];
-                            g[c] = gC_in[3 * b + c];
-                            Cpre[c] = 0.0f;
-                        }
-                        r = r_in[b];
-                        march_init(f, mr);
-                        T = 1.0f;
-                        k_done = 0;
-                        n_tot = n_fin[b];
-                        ray = b;
-                    }
-                }
+        float p[3] = {0, 0, 0}, dir[3] = {0.0f, 0.0f, 1.0f}, rn = 0.0f, dsig = 0.0f, dz[3] = {0, 0, 0};
+        if (i < n_samples) {
+            const int2 q = rec[i];
+            const long long b = q.x;
+            if (i - off[b] < n_used[b]) {
+                have = true;
+                const float o[3] = {o_in[3 * b], o_in[3 * b + 1], o_in[3 * b + 2]};
+                dir[0] = d_in[3 * b];
+                dir[1] = d_in[3 * b + 1];
+                dir[2] = d_in[3 * b + 2];
+                const float t = f.t_tab[q.y];
+                int vox;
+                sample_voxel(f, o, dir, t, p, vox);
+                rn = footprint(f, t, r_in[b], p, nullptr, nullptr);
+                const float4 gs = grad_s[i];
+                dsig = gs.x;
+                dz[0] = gs.y;
+                dz[1] = gs.z;
+                dz[2] = gs.w;
             }
-            if (ray >= 0 && !have) {
-                const int mres = march_next(f, sT, mr, p, 8, tested);
-                if (mres == MARCH_SAMPLE) have = true;
-                else if (mres == MARCH_END) ray = -1;  // cannot happen before n_tot samples
-            }
-            if (__all_sync(FULL, have || exhausted)) break;
         }
-        if (!__any_sync(FULL, have)) break;
+        if (!__any_sync(FULL, have)) continue;
 
         // ---- recompute the sample: features and forward MLPs ----
-        float feat[D], dir[3] = {0.0f, 0.0f, 1.0f};
-        float t = 0.0f, delta = 0.0f, rn = 0.0f;
+        float feat[D];
         if (have) {
-            t = sT[mr.step];
-            delta = sT[mr.step + 1] - t;
-            rn = footprint(f, t, r, p, nullptr, nullptr);  // explicit rays
             gather_features<L>(f, p, rn, feat);
-            dir[0] = mr.d[0];
-            dir[1] = mr.d[1];
-            dir[2] = mr.d[2];
         } else {
 #pragma unroll
             for (int k = 0; k < D; ++k) feat[k] = 0.0f;
         }
         float o[16];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) o[i] = 0.0f;
+        for (int k = 0; k < 16; ++k) o[k] = 0.0f;
 #pragma unroll 2
         for (int j = 0; j < 64; ++j) {
             const float h = fmaxf(dot_row(W1 + j * D, feat, D), 0.0f);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) o[i] = fmaf(__ldg(W2 + i * 64 + j), h, o[i]);
+            for (int k = 0; k < 16; ++k) o[k] = fmaf(__ldg(W2 + k * 64 + j), h, o[k]);
         }
         const float sigma = expf(o[0] + f.density_bias);
         float h1[64];
         {
             float x[32];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) x[i] = o[i];
+            for (int k = 0; k < 16; ++k) x[k] = o[k];
             sh16(dir[0], dir[1], dir[2], x + 16);
 #pragma unroll
             for (int j = 0; j < 64; ++j) h1[j] = fmaxf(dot_row(W3 + j * 32, x, 32), 0.0f);
         }
-        float z0 = 0.0f, z1 = 0.0f, z2 = 0.0f;
 #pragma unroll 2
-        for (int j = 0; j < 64; ++j) {
-            const float h2 = fmaxf(dot_row(W4 + j * 64, h1, 64), 0.0f);
-            sA[lane * kStride + j] = h2;
-            z0 = fmaf(__ldg(W5 + j), h2, z0);
-            z1 = fmaf(__ldg(W5 + 64 + j), h2, z1);
-            z2 = fmaf(__ldg(W5 + 128 + j), h2, z2);
-        }
-        const float c0 = 1.0f / (1.0f + expf(-z0)), c1 = 1.0f / (1.0f + expf(-z1)),
-                    c2 = 1.0f / (1.0f + expf(-z2));
+        for (int j = 0; j < 64; ++j) sA[lane * kStride + j] = fmaxf(dot_row(W4 + j * 64, h1, 64), 0.0f);
 
-        // ---- compositing gradient ----
-        const float sd = sigma * delta;
-        const float alpha = -expm1f(-sd), Tn = T * expf(-sd), w = T * alpha;
-        float dz[3] = {0, 0, 0}, dsig = 0.0f;
-        if (have) {
-            const float cc[3] = {c0, c1, c2};
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float suffix = Cf[c] - (Cpre[c] + w * cc[c]);
-                dsig += g[c] * delta * (Tn * cc[c] - suffix);
-                dz[c] = w * g[c] * cc[c] * (1.0f - cc[c]);
-            }
-        }
         // ---- W5: dz x h2 ----
         sD[lane * kStride + 0] = dz[0];
         sD[lane * kStride + 1] = dz[1];
@@ -293,12 +418,12 @@ backward_kernel(const FieldView f, const float *__restrict__ o_in, const float *
         minigemm_rows<64, 32>(sD, sA, sG + G::g3, G::s3, lane);
         float dout[16];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) dout[i] = 0.0f;
+        for (int k = 0; k < 16; ++k) dout[k] = 0.0f;
 #pragma unroll 4
         for (int j = 0; j < 64; ++j) {
             const float d = sD[lane * kStride + j];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) dout[i] = fmaf(__ldg(W3 + j * 32 + i), d, dout[i]);
+            for (int k = 0; k < 16; ++k) dout[k] = fmaf(__ldg(W3 + j * 32 + k), d, dout[k]);
         }
         dout[0] += dsig * sigma;
         __syncwarp();
@@ -307,7 +432,7 @@ backward_kernel(const FieldView f, const float *__restrict__ o_in, const float *
 #pragma unroll
         for (int j = 0; j < 64; ++j) h[j] = fmaxf(dot_row(W1 + j * D, feat, D), 0.0f);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) sD[lane * kStride + i] = dout[i];
+        for (int k = 0; k < 16; ++k) sD[lane * kStride + k] = dout[k];
 #pragma unroll
         for (int j = 0; j < 64; ++j) sA[lane * kStride + j] = h[j];
         __syncwarp();
@@ -317,7 +442,7 @@ backward_kernel(const FieldView f, const float *__restrict__ o_in, const float *
         for (int j = 0; j < 64; ++j) {
             float a = 0.0f;
 #pragma unroll
-            for (int i = 0; i < 16; ++i) a = fmaf(__ldg(W2 + i * 64 + j), dout[i], a);
+            for (int k = 0; k < 16; ++k) a = fmaf(__ldg(W2 + k * 64 + j), dout[k], a);
             dh[j] = h[j] > 0.0f ? a : 0.0f;
         }
         __syncwarp();
@@ -339,7 +464,7 @@ backward_kernel(const FieldView f, const float *__restrict__ o_in, const float *
         }
         __syncwarp();
 
-        // ---- hash-grid scatter and compositing state ----
+        // ---- hash-grid scatter ----
         if (have) {
             const float Ls = lod_star(f, rn);
             for (int l = 0; l < L; ++l) {
@@ -348,20 +473,14 @@ backward_kernel(const FieldView f, const float *__restrict__ o_in, const float *
                 uint32_t idx[8];
                 float fr[3];
                 level_corners(f, l, p, idx, fr);
-                float2 *base = reinterpret_cast<float2 *>(grid_grad) + (size_t)l * (f.T_mask + 1u);
+                float2 *gbase = reinterpret_cast<float2 *>(grid_grad) + (size_t)l * (f.T_mask + 1u);
 #pragma unroll
                 for (int b = 0; b < 8; ++b) {
                     const float cw = (b & 1 ? fr[0] : 1.0f - fr[0]) * (b & 2 ? fr[1] : 1.0f - fr[1]) *
                                      (b & 4 ? fr[2] : 1.0f - fr[2]) * wl;
-                    atomicAdd(base + idx[b], make_float2(cw * dfeat[2 * l], cw * dfeat[2 * l + 1]));
+                    atomicAdd(gbase + idx[b], make_float2(cw * dfeat[2 * l], cw * dfeat[2 * l + 1]));
                 }
             }
-            Cpre[0] += w * c0;
-            Cpre[1] += w * c1;
-            Cpre[2] += w * c2;
-            T = Tn;
-            ++mr.step;
-            if (++k_done >= n_tot) ray = -1;
         }
     }
     __syncthreads();
@@ -376,20 +495,6 @@ backward_kernel(const FieldView f, const float *__restrict__ o_in, const float *
         const float val = sG[v];
         if (val != 0.0f) atomicAdd(mlp_grad + e, val);
     }
-}
-
-// loss = sum |C - PQ(target / 100)| (divided by 3B on the host); dL/dC.
-__global__ void loss_kernel(const float *__restrict__ C, const float *__restrict__ target, int n3, float inv,
-                            float *__restrict__ gC, float *__restrict__ loss_sum) {
-    float s = 0.0f;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += gridDim.x * blockDim.x) {
-        const float diff = C[i] - linear_to_pq(target[i]);
-        gC[i] = diff > 0.0f ? inv : (diff < 0.0f ? -inv : 0.0f);
-        s += fabsf(diff);
-    }
-#pragma unroll
-    for (int k = 16; k > 0; k >>= 1) s += __shfl_xor_sync(0xffffffffu, s, k);
-    if ((threadIdx.x & 31) == 0) atomicAdd(loss_sum, s);
 }
 
 __global__ void adam_kernel(float *__restrict__ p32, __half *__restrict__ p16, const float *__restrict__ g,
@@ -418,10 +523,18 @@ __global__ void half_to_float_kernel(const __half *__restrict__ a, float *__rest
 // host side
 // ---------------------------------------------------------------------------
 struct TrainScratch {
-    float *C = nullptr, *gC = nullptr;
-    int *n = nullptr;
+    // per ray
+    int *cnt = nullptr, *n_used = nullptr;
+    long long *off = nullptr;
     int cap = 0;
+    // per sample
+    int2 *rec = nullptr;
+    float4 *sc = nullptr;
+    long long scap = 0;
+    unsigned long long *total = nullptr;   // device counter of records
+    unsigned long long *total_h = nullptr; // pinned host copy
 };
+
 static int ensure_train(vrnerf_field *F, int B) {
     cudaError_t e = cudaSuccess;
     const uint64_t ng = grid_entries(F->desc);
@@ -434,51 +547,128 @@ static int ensure_train(vrnerf_field *F, int B) {
         return fail(VRNERF_ENOMEM, "loss: %s", cudaGetErrorString(e));
     if (!F->train_scratch) F->train_scratch = new TrainScratch();
     TrainScratch &S = *static_cast<TrainScratch *>(F->train_scratch);
+    if (!S.total) {
+        if ((e = cudaMalloc(&S.total, sizeof(unsigned long long))) != cudaSuccess ||
+            (e = cudaMallocHost(&S.total_h, sizeof(unsigned long long))) != cudaSuccess)
+            return fail(VRNERF_ENOMEM, "training scratch: %s", cudaGetErrorString(e));
+    }
     if (B > S.cap) {
-        if (S.C) cudaFree(S.C);
-        if (S.gC) cudaFree(S.gC);
-        if (S.n) cudaFree(S.n);
-        S.C = S.gC = nullptr;
-        S.n = nullptr;
+        cudaFree(S.cnt);
+        cudaFree(S.n_used);
+        cudaFree(S.off);
+        S.cnt = S.n_used = nullptr;
+        S.off = nullptr;
         S.cap = 0;
-        if ((e = cudaMalloc(&S.C, sizeof(float) * 3 * (size_t)B)) != cudaSuccess ||
-            (e = cudaMalloc(&S.gC, sizeof(float) * 3 * (size_t)B)) != cudaSuccess ||
-            (e = cudaMalloc(&S.n, sizeof(int) * (size_t)B)) != cudaSuccess)
+        if ((e = cudaMalloc(&S.cnt, sizeof(int) * (size_t)B)) != cudaSuccess ||
+            (e = cudaMalloc(&S.n_used, sizeof(int) * (size_t)B)) != cudaSuccess ||
+            (e = cudaMalloc(&S.off, sizeof(long long) * (size_t)B)) != cudaSuccess)
             return fail(VRNERF_ENOMEM, "training scratch: %s", cudaGetErrorString(e));
         S.cap = B;
     }
     return VRNERF_OK;
 }
 
+static int ensure_samples(TrainScratch &S, long long n) {
+    if (n <= S.scap) return VRNERF_OK;
+    cudaFree(S.rec);
+    cudaFree(S.sc);
+    S.rec = nullptr;
+    S.sc = nullptr;
+    S.scap = 0;
+    const long long want = n + n / 4 + 1024;
+    cudaError_t e;
+    if ((e = cudaMalloc(&S.rec, sizeof(int2) * (size_t)want)) != cudaSuccess ||
+        (e = cudaMalloc(&S.sc, sizeof(float4) * (size_t)want)) != cudaSuccess)
+        return fail(VRNERF_ENOMEM, "sample records (%lld): %s", want, cudaGetErrorString(e));
+    S.scap = want;
+    return VRNERF_OK;
+}
+
 void release_train_scratch(vrnerf_field *F) {
     if (!F->train_scratch) return;
     TrainScratch *S = static_cast<TrainScratch *>(F->train_scratch);
-    if (S->C) cudaFree(S->C);
-    if (S->gC) cudaFree(S->gC);
-    if (S->n) cudaFree(S->n);
+    cudaFree(S->cnt);
+    cudaFree(S->n_used);
+    cudaFree(S->off);
+    cudaFree(S->rec);
+    cudaFree(S->sc);
+    cudaFree(S->total);
+    if (S->total_h) cudaFreeHost(S->total_h);
     delete S;
     F->train_scratch = nullptr;
 }
 
-template <int L>
-static cudaError_t launch_backward_t(vrnerf_field *F, const float *o, const float *d, const float *r, int B,
-                                     const float *C_fin, const int *n_fin, const float *gC, cudaStream_t st) {
-    constexpr int D = 2 * L;
-    const size_t smem = sizeof(float) * ((size_t)GradSm<D>::size + ((F->view.S + 1 + 3) & ~3) +
-                                         (size_t)(kBwdThreads / 32) * 2 * 32 * kStride);
-    auto kern = backward_kernel<L>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+template <typename K>
+static cudaError_t grid_for(K kern, int threads, size_t smem, long long work, int &blocks) {
     int bps = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kBwdThreads, smem)) != cudaSuccess) return e;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, threads, smem);
+    if (e != cudaSuccess) return e;
     if (bps < 1) bps = 1;
-    long long grid = (long long)num_sms() * bps, want = (B + kBwdThreads - 1) / kBwdThreads;
-    if (want < grid) grid = want;
-    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(F->counter);
-    if ((e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
-    kern<<<(unsigned)grid, kBwdThreads, smem, st>>>(F->view, o, d, r, B, C_fin, n_fin, gC, F->grid_grad, F->mlp_grad,
-                                                   cnt);
-    return cudaGetLastError();
+    long long g = (long long)num_sms() * bps, want = (work + threads - 1) / threads;
+    blocks = (int)(want < g ? (want < 1 ? 1 : want) : g);
+    return cudaSuccess;
+}
+
+// The sample-parallel backward (header comment): gradients into the field's
+// buffers (zeroed here). target != nullptr: L1 loss, accumulated into
+// F->loss_acc; else gC (dL/dC per ray) and n_given (composited samples).
+template <int L>
+static int backward_t(vrnerf_field *F, const float *o, const float *d, const float *r, int B, const float *target,
+                      const float *gC, const int *n_given, cudaStream_t st) {
+    constexpr int D = 2 * L;
+    TrainScratch &S = *static_cast<TrainScratch *>(F->train_scratch);
+    const FieldView &f = F->view;
+    cudaError_t e = cudaMemsetAsync(F->grid_grad, 0, grid_entries(F->desc) * sizeof(float), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(F->mlp_grad, 0, sizeof(float) * f.n_mlp, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(F->loss_acc, 0, 64, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S.total, 0, sizeof(unsigned long long), st);
+    int blocks = 0;
+    if (e == cudaSuccess) e = grid_for(count_kernel, 128, 0, B, blocks);
+    if (e == cudaSuccess) {
+        count_kernel<<<blocks, 128, 0, st>>>(f, o, d, B, S.cnt, S.off, S.total);
+        e = cudaGetLastError();
+    }
+    // the record count sizes the per-sample buffers: one small read-back
+    if (e == cudaSuccess) e = cudaMemcpyAsync(S.total_h, S.total, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "backward: count");
+    const long long n = (long long)*S.total_h;
+    int rc = ensure_samples(S, n);
+    if (rc) return rc;
+    if (n > 0) {
+        e = grid_for(emit_kernel, 128, 0, B, blocks);
+        if (e == cudaSuccess) {
+            emit_kernel<<<blocks, 128, 0, st>>>(f, o, d, B, S.off, S.rec);
+            e = cudaGetLastError();
+        }
+        const size_t smem_f = sizeof(float) * SimtW<D>::size;
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(sample_fwd_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_f);
+        if (e == cudaSuccess) e = grid_for(sample_fwd_kernel<L>, 128, smem_f, n, blocks);
+        if (e == cudaSuccess) {
+            sample_fwd_kernel<L><<<blocks, 128, smem_f, st>>>(f, o, d, r, S.rec, n, S.sc);
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess) e = grid_for(ray_comp_kernel, 128, 0, B, blocks);
+    if (e == cudaSuccess) {
+        ray_comp_kernel<<<blocks, 128, 0, st>>>(f, o, d, B, S.cnt, S.off, S.rec, n_given, target, gC,
+                                                1.0f / (3.0f * B), S.sc, S.n_used, target ? F->loss_acc : nullptr,
+                                                F->hist);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && n > 0) {
+        const size_t smem_b = sizeof(float) * ((size_t)GradSm<D>::size + (size_t)(kBwdThreads / 32) * 2 * 32 * kStride);
+        e = cudaFuncSetAttribute(sample_bwd_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b);
+        if (e == cudaSuccess) e = grid_for(sample_bwd_kernel<L>, kBwdThreads, smem_b, n, blocks);
+        if (e == cudaSuccess) {
+            sample_bwd_kernel<L><<<blocks, kBwdThreads, smem_b, st>>>(f, o, d, r, S.rec, S.off, S.n_used, n, S.sc,
+                                                                      F->grid_grad, F->mlp_grad);
+            e = cudaGetLastError();
+        }
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "backward");
+    return VRNERF_OK;
 }
 
 }  // namespace vrn
@@ -494,35 +684,13 @@ int vrnerf_backward(vrnerf_field *F, const float *rays_o, const float *rays_d, c
         if (B < 1) return fail(VRNERF_EINVAL, "B must be >= 1");
         int rc = ensure_train(F, B);
         if (rc) return rc;
-        TrainScratch &S = *static_cast<TrainScratch *>(F->train_scratch);
         cudaStream_t st = (cudaStream_t)stream;
-        cudaError_t e = cudaMemsetAsync(F->grid_grad, 0, grid_entries(F->desc) * sizeof(float), st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(F->mlp_grad, 0, sizeof(float) * F->view.n_mlp, st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(F->loss_acc, 0, 64, st);
-        // forward: composited PQ colour and sample count of every ray
-        RaySource src;
-        memset(&src, 0, sizeof src);
-        src.o = rays_o;
-        src.d = rays_d;
-        src.r = radii;
-        src.n_slots = B;
-        // (the linear colour is not needed: it lands in gC, which the loss kernel fills next)
-        RenderOut ro{S.gC, S.C, nullptr, S.n, nullptr, nullptr, F->hist};
-        if (e == cudaSuccess) e = cudaMemsetAsync(F->counter, 0, sizeof(unsigned long long), st);
-        if (e == cudaSuccess)
-            e = launch_render_simt(F->view, src, ro, reinterpret_cast<unsigned long long *>(F->counter), st);
-        if (e == cudaSuccess) {
-            loss_kernel<<<num_sms() * 4, 256, 0, st>>>(S.C, target_linear, 3 * B, 1.0f / (3.0f * B), S.gC,
-                                                        F->loss_acc);
-            e = cudaGetLastError();
-        }
-        if (e == cudaSuccess)
-            e = F->view.L == 8 ? launch_backward_t<8>(F, rays_o, rays_d, radii, B, S.C, S.n, S.gC, st)
-                               : launch_backward_t<16>(F, rays_o, rays_d, radii, B, S.C, S.n, S.gC, st);
-        if (e != cudaSuccess) return cuda_fail(e, "backward");
+        rc = F->view.L == 8 ? backward_t<8>(F, rays_o, rays_d, radii, B, target_linear, nullptr, nullptr, st)
+                            : backward_t<16>(F, rays_o, rays_d, radii, B, target_linear, nullptr, nullptr, st);
+        if (rc) return rc;
         if (loss_host) {
             float sum = 0.0f;
-            e = cudaMemcpyAsync(&sum, F->loss_acc, sizeof(float), cudaMemcpyDeviceToHost, st);
+            cudaError_t e = cudaMemcpyAsync(&sum, F->loss_acc, sizeof(float), cudaMemcpyDeviceToHost, st);
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
             if (e != cudaSuccess) return cuda_fail(e, "backward: loss");
             *loss_host = sum / (3.0f * B);
@@ -534,22 +702,15 @@ int vrnerf_backward(vrnerf_field *F, const float *rays_o, const float *rays_d, c
 }
 
 int vrnerf_backward_from_grad(vrnerf_field *F, const float *rays_o, const float *rays_d, const float *radii,
-                              int32_t B, const float *pq_fwd, const int32_t *n_fwd, const float *grad_pq,
-                              void *stream) {
+                              int32_t B, const int32_t *n_fwd, const float *grad_pq, void *stream) {
     try {
-        if (!F || !rays_o || !rays_d || !radii || !pq_fwd || !n_fwd || !grad_pq)
-            return fail(VRNERF_EINVAL, "NULL argument");
+        if (!F || !rays_o || !rays_d || !radii || !n_fwd || !grad_pq) return fail(VRNERF_EINVAL, "NULL argument");
         if (B < 1) return fail(VRNERF_EINVAL, "B must be >= 1");
-        int rc = ensure_train(F, 1);
+        int rc = ensure_train(F, B);
         if (rc) return rc;
         cudaStream_t st = (cudaStream_t)stream;
-        cudaError_t e = cudaMemsetAsync(F->grid_grad, 0, grid_entries(F->desc) * sizeof(float), st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(F->mlp_grad, 0, sizeof(float) * F->view.n_mlp, st);
-        if (e == cudaSuccess)
-            e = F->view.L == 8 ? launch_backward_t<8>(F, rays_o, rays_d, radii, B, pq_fwd, n_fwd, grad_pq, st)
-                               : launch_backward_t<16>(F, rays_o, rays_d, radii, B, pq_fwd, n_fwd, grad_pq, st);
-        if (e != cudaSuccess) return cuda_fail(e, "backward_from_grad");
-        return VRNERF_OK;
+        return F->view.L == 8 ? backward_t<8>(F, rays_o, rays_d, radii, B, nullptr, grad_pq, n_fwd, st)
+                              : backward_t<16>(F, rays_o, rays_d, radii, B, nullptr, grad_pq, n_fwd, st);
     } catch (...) {
         return fail(VRNERF_EINVAL, "backward_from_grad: unexpected C++ exception");
     }

@@ -66,7 +66,7 @@ _SIGS = {
     "vrnerf_field_set_occupancy": (ctypes.c_int, [_VP, _VP]),
     "vrnerf_field_save": (ctypes.c_int, [_VP, ctypes.c_char_p]),
     "vrnerf_history_reset": (ctypes.c_int, [_VP]),
-    "vrnerf_backward_from_grad": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP, _VP]),
+    "vrnerf_backward_from_grad": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP]),
     "vrnerf_field_param_ptrs": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
     "vrnerf_field_params_changed": (ctypes.c_int, [_VP]),
     "vrnerf_tonemap": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, _F, _VP, _VP]),
@@ -263,11 +263,11 @@ def vrnerf_tonemap(pq, T=None, exposure_ev=0.0, out=None, stream=None):
     return out
 
 
-def vrnerf_backward_from_grad(field: Field, rays_o, rays_d, radii, pq_fwd, n_fwd, grad_pq, stream=None):
+def vrnerf_backward_from_grad(field: Field, rays_o, rays_d, radii, n_fwd, grad_pq, stream=None):
     B = rays_o.shape[0]
     _check(load().vrnerf_backward_from_grad(field.h, _ptr(_dev(rays_o)), _ptr(_dev(rays_d)), _ptr(_dev(radii)),
-                                            B, _ptr(_dev(pq_fwd)), _ptr(_dev(n_fwd, torch.int32)),
-                                            _ptr(_dev(grad_pq)), _stream(stream)))
+                                            B, _ptr(_dev(n_fwd, torch.int32)), _ptr(_dev(grad_pq)),
+                                            _stream(stream)))
 
 
 class _DeviceArray:
@@ -314,14 +314,14 @@ class RenderRaysFunction(torch.autograd.Function):
         n = torch.empty(B, device=rays_o.device, dtype=torch.int32)
         vrnerf_render_rays(field, rays_o, rays_d, radii, precision=FP32, out_pq=pq, out_n=n)
         ctx.field = field
-        ctx.save_for_backward(rays_o, rays_d, radii, pq, n)
+        ctx.save_for_backward(rays_o, rays_d, radii, n)
         return pq
 
     @staticmethod
     def backward(ctx, grad_pq):
-        o, d, r, pq, n = ctx.saved_tensors
+        o, d, r, n = ctx.saved_tensors
         field = ctx.field
-        vrnerf_backward_from_grad(field, o, d, r, pq, n, grad_pq.contiguous())
+        vrnerf_backward_from_grad(field, o, d, r, n, grad_pq.contiguous())
         v = vrnerf_field_param_views(field)
         gg = v["grid_grad"].clone()
         if field.cfg.feat_fp16:

@@ -240,13 +240,21 @@ int vrnerf_backward(vrnerf_field *field, const float *rays_o, const float *rays_
                     const float *radii, const float *target_linear, int32_t B, float *loss_host,
                     void *stream);
 
+/* The forward of the training path for explicit rays: PQ colour out_pq
+ * [B][3] and composited sample count out_n [B] (the render of
+ * vrnerf_render_rays with VRNERF_FP32, early termination included),
+ * computed sample-parallel like vrnerf_backward, so that small batches fill
+ * the GPU. Device memory; waits for `stream` once. EINVAL, ENOMEM, ECUDA. */
+int vrnerf_forward_rays(vrnerf_field *field, const float *rays_o, const float *rays_d,
+                        const float *radii, int32_t B, float *out_pq, int32_t *out_n, void *stream);
+
 /* Backward for an arbitrary loss on the PQ colours (the hand-written
  * backward behind an autograd function): the gradient of
  * sum_i grad_pq[i] . C_pq(ray i) with respect to every hash-grid entry and
  * MLP weight into the field's gradient buffers (overwritten). n_fwd [B] are
- * the sample counts that vrnerf_render_rays (VRNERF_FP32) returned for the
- * same rays and parameters: ray i composites exactly n_fwd[i] samples, as in
- * that forward pass; samples are recomputed, only sigma, colour and their
+ * the sample counts that vrnerf_forward_rays (or vrnerf_render_rays with
+ * VRNERF_FP32) returned for the same rays and parameters: ray i composites
+ * exactly n_fwd[i] samples, as in that forward pass; samples are recomputed, only sigma, colour and their
  * gradients are kept per sample. All arrays device memory; the call waits
  * for `stream` once (the sample count sizes its buffers). EINVAL, ENOMEM,
  * ECUDA. */

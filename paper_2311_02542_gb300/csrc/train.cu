@@ -211,7 +211,7 @@ ray_comp_kernel(const FieldView f, const float *__restrict__ o_in, const float *
                 const int *__restrict__ cnt, const long long *__restrict__ off, const int2 *__restrict__ rec,
                 const int *__restrict__ n_given, const float *__restrict__ target, const float *__restrict__ gC_given,
                 float inv_n, float4 *__restrict__ sc, int *__restrict__ n_used, float *__restrict__ loss_sum,
-                float *__restrict__ hist) {
+                float *__restrict__ hist, float *__restrict__ C_out) {
     float loss = 0.0f;
     for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < B; b += (long long)gridDim.x * blockDim.x) {
         const long long k0 = off[b];
@@ -238,6 +238,13 @@ ray_comp_kernel(const FieldView f, const float *__restrict__ o_in, const float *
             T *= expf(-sd);
             ++n;
             if (!n_given && T < f.T_eps) break;
+        }
+        if (C_out) {  // forward only: composited PQ colour and sample count
+            C_out[3 * b] = C[0];
+            C_out[3 * b + 1] = C[1];
+            C_out[3 * b + 2] = C[2];
+            n_used[b] = n;
+            continue;
         }
         float g[3];
 #pragma unroll
@@ -614,13 +621,17 @@ static cudaError_t grid_for(K kern, int threads, size_t smem, long long work, in
 // F->loss_acc; else gC (dL/dC per ray) and n_given (composited samples).
 template <int L>
 static int backward_t(vrnerf_field *F, const float *o, const float *d, const float *r, int B, const float *target,
-                      const float *gC, const int *n_given, cudaStream_t st) {
+                      const float *gC, const int *n_given, cudaStream_t st, float *C_out = nullptr,
+                      int *n_out = nullptr) {
     constexpr int D = 2 * L;
     TrainScratch &S = *static_cast<TrainScratch *>(F->train_scratch);
     const FieldView &f = F->view;
-    cudaError_t e = cudaMemsetAsync(F->grid_grad, 0, grid_entries(F->desc) * sizeof(float), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(F->mlp_grad, 0, sizeof(float) * f.n_mlp, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(F->loss_acc, 0, 64, st);
+    cudaError_t e = cudaSuccess;
+    if (!C_out) {
+        e = cudaMemsetAsync(F->grid_grad, 0, grid_entries(F->desc) * sizeof(float), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(F->mlp_grad, 0, sizeof(float) * f.n_mlp, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(F->loss_acc, 0, 64, st);
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(S.total, 0, sizeof(unsigned long long), st);
     int blocks = 0;
     if (e == cudaSuccess) e = grid_for(count_kernel, 128, 0, B, blocks);
@@ -653,11 +664,11 @@ static int backward_t(vrnerf_field *F, const float *o, const float *d, const flo
     if (e == cudaSuccess) e = grid_for(ray_comp_kernel, 128, 0, B, blocks);
     if (e == cudaSuccess) {
         ray_comp_kernel<<<blocks, 128, 0, st>>>(f, o, d, B, S.cnt, S.off, S.rec, n_given, target, gC,
-                                                1.0f / (3.0f * B), S.sc, S.n_used, target ? F->loss_acc : nullptr,
-                                                F->hist);
+                                                1.0f / (3.0f * B), S.sc, C_out ? n_out : S.n_used,
+                                                target ? F->loss_acc : nullptr, C_out ? nullptr : F->hist, C_out);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess && n > 0) {
+    if (e == cudaSuccess && n > 0 && !C_out) {
         const size_t smem_b = sizeof(float) * ((size_t)GradSm<D>::size + (size_t)(kBwdThreads / 32) * 2 * 32 * kStride);
         e = cudaFuncSetAttribute(sample_bwd_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b);
         if (e == cudaSuccess) e = grid_for(sample_bwd_kernel<L>, kBwdThreads, smem_b, n, blocks);
@@ -698,6 +709,22 @@ int vrnerf_backward(vrnerf_field *F, const float *rays_o, const float *rays_d, c
         return VRNERF_OK;
     } catch (...) {
         return fail(VRNERF_EINVAL, "backward: unexpected C++ exception");
+    }
+}
+
+int vrnerf_forward_rays(vrnerf_field *F, const float *rays_o, const float *rays_d, const float *radii, int32_t B,
+                        float *out_pq, int32_t *out_n, void *stream) {
+    try {
+        if (!F || !rays_o || !rays_d || !radii || !out_pq || !out_n) return fail(VRNERF_EINVAL, "NULL argument");
+        if (B < 1) return fail(VRNERF_EINVAL, "B must be >= 1");
+        int rc = ensure_train(F, B);
+        if (rc) return rc;
+        cudaStream_t st = (cudaStream_t)stream;
+        return F->view.L == 8
+                   ? backward_t<8>(F, rays_o, rays_d, radii, B, nullptr, nullptr, nullptr, st, out_pq, out_n)
+                   : backward_t<16>(F, rays_o, rays_d, radii, B, nullptr, nullptr, nullptr, st, out_pq, out_n);
+    } catch (...) {
+        return fail(VRNERF_EINVAL, "forward_rays: unexpected C++ exception");
     }
 }
 

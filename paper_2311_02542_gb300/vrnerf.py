@@ -66,6 +66,7 @@ _SIGS = {
     "vrnerf_field_set_occupancy": (ctypes.c_int, [_VP, _VP]),
     "vrnerf_field_save": (ctypes.c_int, [_VP, ctypes.c_char_p]),
     "vrnerf_history_reset": (ctypes.c_int, [_VP]),
+    "vrnerf_forward_rays": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP]),
     "vrnerf_backward_from_grad": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP]),
     "vrnerf_field_param_ptrs": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
     "vrnerf_field_params_changed": (ctypes.c_int, [_VP]),
@@ -263,6 +264,18 @@ def vrnerf_tonemap(pq, T=None, exposure_ev=0.0, out=None, stream=None):
     return out
 
 
+def vrnerf_forward_rays(field: Field, rays_o, rays_d, radii, out_pq=None, out_n=None, stream=None):
+    """PQ colours [B][3] and sample counts [B] of explicit rays, sample-parallel."""
+    B = rays_o.shape[0]
+    if out_pq is None:
+        out_pq = torch.empty((B, 3), device=rays_o.device, dtype=torch.float32)
+    if out_n is None:
+        out_n = torch.empty(B, device=rays_o.device, dtype=torch.int32)
+    _check(load().vrnerf_forward_rays(field.h, _ptr(_dev(rays_o)), _ptr(_dev(rays_d)), _ptr(_dev(radii)), B,
+                                      _ptr(_dev(out_pq)), _ptr(_dev(out_n, torch.int32)), _stream(stream)))
+    return out_pq, out_n
+
+
 def vrnerf_backward_from_grad(field: Field, rays_o, rays_d, radii, n_fwd, grad_pq, stream=None):
     B = rays_o.shape[0]
     _check(load().vrnerf_backward_from_grad(field.h, _ptr(_dev(rays_o)), _ptr(_dev(rays_d)), _ptr(_dev(radii)),
@@ -304,15 +317,12 @@ def vrnerf_field_params_changed(field: Field):
 
 class RenderRaysFunction(torch.autograd.Function):
     """PQ colours of explicit rays (fp32 path) as a differentiable function of
-    the field's parameters: forward renders through the library, backward
-    runs its hand-written backward kernel (samples recomputed per ray)."""
+    the field's parameters: forward and backward run the library's
+    sample-parallel training kernels (samples recomputed in backward)."""
 
     @staticmethod
     def forward(ctx, field, rays_o, rays_d, radii, grid, mlp):
-        B = rays_o.shape[0]
-        pq = torch.empty((B, 3), device=rays_o.device, dtype=torch.float32)
-        n = torch.empty(B, device=rays_o.device, dtype=torch.int32)
-        vrnerf_render_rays(field, rays_o, rays_d, radii, precision=FP32, out_pq=pq, out_n=n)
+        pq, n = vrnerf_forward_rays(field, rays_o, rays_d, radii)
         ctx.field = field
         ctx.save_for_backward(rays_o, rays_d, radii, n)
         return pq

@@ -109,3 +109,20 @@ def test_torch_optimiser_trains_the_field(V):
     assert np.all(np.abs(a - b) <= 2e-3 * np.abs(a) + 1e-4)
     V.vrnerf_field_status(f)
     f.close()
+
+
+def test_forward_rays_equals_render_rays(V):
+    """The sample-parallel forward gives the fp32 renderer's PQ colours and
+    sample counts on the same rays (same arithmetic, another schedule)."""
+    sc = S.make_scene("room")
+    f = V.Field(sc.cfg, sc.grid, sc.mlp, sc.occ_bits)
+    poses, intr = S.training_views(sc.occ, sc.cfg, n_views=16)
+    o, d, r, _ = (_cuda(a) for a in S.training_batch(poses, intr, 12800, seed=5, step=1))
+    pq_a, n_a = V.vrnerf_forward_rays(f, o, d, r)
+    pq_b = torch.empty_like(pq_a)
+    n_b = torch.empty_like(n_a)
+    V.vrnerf_render_rays(f, o, d, r, precision="fp32", out_pq=pq_b, out_n=n_b)
+    same = n_a == n_b
+    assert same.float().mean() > 0.999  # a flip at T_eps only if fp32 rounding differs
+    assert torch.allclose(pq_a[same], pq_b[same], rtol=1e-5, atol=1e-7)
+    f.close()

@@ -72,6 +72,22 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x, device=None):
+    """Largest x over the ranks of the default process group (x alone)."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mrays(rays_per_rank, world, ms_max):
+    """Rays of all ranks (each renders its own frame) over the slowest rank's time."""
+    return world * rays_per_rank / (ms_max * 1e-3) / 1e6
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -410,22 +426,24 @@ def main():
     torch.cuda.synchronize()
     n_samples, n_levels, n_steps, n_rays_done = [int(x) for x in stats.cpu()]
 
-    # timed region: tuned path, bracketed by barrier + synchronize
+    # timed region: tuned path (its warm-up steps run first, untimed),
+    # bracketed by barrier + synchronize on both sides
+    for _ in range(args.warmup):
+        V.vrnerf_render(field, cams, intr, res, out=out, precision=tuned)
+    torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clk = Clocks(local)
     t_wall0 = time.perf_counter()
-    ms = timed(tuned, args.steps, args.warmup)
+    ms = timed(tuned, args.steps, 0)
     torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
     wall = time.perf_counter() - t_wall0
     clocks = clk.stop()
-    ms_step = float(ms.mean())
-    if world > 1:
-        t = torch.tensor([ms_step], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = world * rays / (ms_step * 1e-3) / 1e6
+    ms_step = max_over_ranks(float(ms.mean()), dev)
+    value = whole_job_mrays(rays, world, ms_step)
 
     # plain fp32 path on the same frame
     ms32 = timed(V.FP32, max(3, args.steps // 2), 2) if tuned != V.FP32 else ms

@@ -62,6 +62,7 @@ extern "C" {
 #define VRNERF_EBUSY (-5)     /* admission refused: over budget or queue full */
 #define VRNERF_ENOTFOUND (-6) /* unknown ticket */
 #define VRNERF_ECANCELED (-7) /* request was cancelled */
+#define VRNERF_ECHECK (-8)    /* a bounds check of the checked build failed */
 
 /* Arithmetic of the MLP. Hash features, transmittance and PQ are always fp32. */
 #define VRNERF_FP32 0 /* plain fp32 on the CUDA cores */
@@ -272,6 +273,17 @@ int vrnerf_backward_from_grad(vrnerf_field *field, const float *rays_o, const fl
 int vrnerf_field_param_ptrs(vrnerf_field *field, void **grid, float **mlp, float **grid_grad,
                             float **mlp_grad);
 int vrnerf_field_params_changed(vrnerf_field *field);
+
+/* Checked builds (libvrnerf_checked.so, compiled with VRNERF_CHECKED=1)
+ * verify hash-grid indices, occupancy voxels, sample indices, output pixels
+ * and training records on the device; a failed check sets a bit that the
+ * next vrnerf_field_status reports as VRNERF_ECHECK, and the access is
+ * skipped or clamped (no trap). vrnerf_build_checked returns 1 in such a
+ * build, else 0. vrnerf_debug_check_trigger sets the test bit (32) through
+ * a kernel, so that the reporting path can be tested; EINVAL in release
+ * builds. */
+int vrnerf_build_checked(void);
+int vrnerf_debug_check_trigger(vrnerf_field *field, void *stream);
 
 /* Display tonemapping of an existing PQ image (the exposure sweep of the
  * paper's results: PQ colour to sRGB at a chosen exposure, without

@@ -18,6 +18,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libvrnerf.so")
+BUILD_CHECKED = BUILD + "_checked"
+LIB_CHECKED = os.path.join(BUILD_CHECKED, "libvrnerf_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -50,15 +52,35 @@ def _stale(obj: str, src: str) -> bool:
     return any(os.path.getmtime(d) > os.path.getmtime(obj) for d in deps)
 
 
-def build(verbose: bool = False, force: bool = False) -> str:
+def _link(objs, lib, force):
+    if force or not os.path.exists(lib) or any(os.path.getmtime(o) > os.path.getmtime(lib) for o in objs):
+        tmp = lib + f".{os.getpid()}.tmp"
+        libdir = cuda_lib_dir()
+        cmd = [nvcc(), *ARCH, "-shared", "-cudart", "shared", *objs, "-o", tmp, f"-L{libdir}",
+               "-Xlinker", f"-rpath,{libdir}"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, lib)
+
+
+def build(verbose: bool = False, force: bool = False, checked: bool = True) -> str:
+    """Compiles the release library and (checked=True) the checked one, whose
+    device code verifies its indices (VRNERF_CHECKED=1), in one parallel pass."""
     os.makedirs(BUILD, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     cc = nvcc()
+    variants = [(BUILD, LIB, [])]
+    if checked:
+        os.makedirs(BUILD_CHECKED, exist_ok=True)
+        variants.append((BUILD_CHECKED, LIB_CHECKED, ["-DVRNERF_CHECKED=1"]))
+    jobs = [(src, os.path.join(d, os.path.basename(src)[:-3] + ".o"), extra) for d, _, extra in variants
+            for src in srcs]
 
-    def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+    def compile_one(job):
+        src, obj, extra = job
         if force or _stale(obj, src):
-            cmd = [cc, *flags(), "-c", src, "-o", obj]
+            cmd = [cc, *flags(extra), "-c", src, "-o", obj]
             r = subprocess.run(cmd, capture_output=True, text=True)
             if r.returncode != 0:
                 raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{r.stdout}\n{r.stderr}")
@@ -66,17 +88,12 @@ def build(verbose: bool = False, force: bool = False) -> str:
                 print(r.stdout + r.stderr, file=sys.stderr)
         return obj
 
-    with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(compile_one, srcs))
-    if force or not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
-        tmp = LIB + f".{os.getpid()}.tmp"
-        libdir = cuda_lib_dir()
-        cmd = [cc, *ARCH, "-shared", "-cudart", "shared", *objs, "-o", tmp, f"-L{libdir}",
-               "-Xlinker", f"-rpath,{libdir}"]
-        r = subprocess.run(cmd, capture_output=True, text=True)
-        if r.returncode != 0:
-            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
+    # the heaviest translation units first, so the pool stays busy
+    jobs.sort(key=lambda j: -os.path.getsize(j[0]))
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
+        objs = list(ex.map(compile_one, jobs))
+    for d, lib, _ in variants:
+        _link([o for o in objs if os.path.dirname(o) == d], lib, force)
     return LIB
 
 

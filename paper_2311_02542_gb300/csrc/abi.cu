@@ -46,6 +46,9 @@ int num_sms() {
 // ---------------------------------------------------------------------------
 // description checks and derived geometry
 // ---------------------------------------------------------------------------
+// Sets the test bit of the bounds-check word (checked builds only).
+__global__ void check_trigger_kernel(const FieldView f) { vrn_check(f.check, threadIdx.x != 0, kCheckTrigger); }
+
 int check_desc(const vrnerf_field_desc *d) {
     if (!d) return fail(VRNERF_EINVAL, "desc is NULL");
     if (d->feats != 2) return fail(VRNERF_EINVAL, "feats must be 2 (got %d)", d->feats);
@@ -305,6 +308,7 @@ int vrnerf_field_create(const vrnerf_field_desc *desc, const void *grid_host, co
     F->view.occ = F->occ;
     F->view.t_tab = F->t_tab;
     F->view.dist = F->dist;
+    F->view.check = reinterpret_cast<unsigned long long *>(F->counter) + 2;
     if (e == cudaSuccess) e = launch_build_dist(F->view, F->dist, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -333,13 +337,15 @@ void vrnerf_field_destroy(vrnerf_field *F) {
 int vrnerf_field_status(vrnerf_field *F) {
     ABI_GUARD_BEGIN
     if (!F) return fail(VRNERF_EINVAL, "field is NULL");
-    unsigned long long st = 0;
+    unsigned long long w[2] = {0, 0};  // status word, bounds-check bits (checked builds)
+    unsigned long long *dev = reinterpret_cast<unsigned long long *>(F->counter) + 1;
     cudaError_t e = cudaDeviceSynchronize();
-    if (e == cudaSuccess)
-        e = cudaMemcpy(&st, reinterpret_cast<unsigned long long *>(F->counter) + 1, sizeof st, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess && st) e = cudaMemset(reinterpret_cast<unsigned long long *>(F->counter) + 1, 0, sizeof st);
+    if (e == cudaSuccess) e = cudaMemcpy(w, dev, sizeof w, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && (w[0] || w[1])) e = cudaMemset(dev, 0, sizeof w);
     if (e != cudaSuccess) return cuda_fail(e, "field_status");
-    if (st) return fail(-(int)st, "a device-side wait timed out; the last kernel stopped early");
+    if (w[0]) return fail(-(int)w[0], "a device-side wait timed out; the last kernel stopped early");
+    if (w[1]) return fail(VRNERF_ECHECK, "bounds checks failed (bits 0x%llx: 1 hash index, 2 voxel, 4 sample, "
+                                         "8 pixel, 16 training record, 32 test trigger)", w[1]);
     return VRNERF_OK;
     ABI_GUARD_END
 }
@@ -368,6 +374,19 @@ int vrnerf_tonemap(const float *pq, const float *T, int64_t n, float exposure_ev
     ABI_GUARD_END
 }
 
+int vrnerf_build_checked(void) { return VRN_CHECKED; }
+
+int vrnerf_debug_check_trigger(vrnerf_field *F, void *stream) {
+    ABI_GUARD_BEGIN
+    if (!F) return fail(VRNERF_EINVAL, "field is NULL");
+    if (!VRN_CHECKED) return fail(VRNERF_EINVAL, "not a checked build");
+    check_trigger_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(F->view);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "debug_check_trigger");
+    return VRNERF_OK;
+    ABI_GUARD_END
+}
+
 int vrnerf_field_set_occupancy(vrnerf_field *F, const uint32_t *occ) {
     ABI_GUARD_BEGIN
     if (!F || !occ) return fail(VRNERF_EINVAL, "NULL argument");
@@ -385,7 +404,7 @@ static int check_precision(int p) {
 }
 
 static int render_common(vrnerf_field *F, const RaySource &src, float *out,
-                         const vrnerf_render_opts *opts, cudaStream_t st) {
+                         const vrnerf_render_opts *opts, cudaStream_t st, long long n_pix) {
     const int prec = opts ? opts->precision : VRNERF_FP32;
     int rc = check_precision(prec);
     if (rc) return rc;
@@ -399,7 +418,8 @@ static int render_common(vrnerf_field *F, const RaySource &src, float *out,
                  opts ? opts->out_depth : nullptr,
                  opts ? opts->out_normal : nullptr,
                  opts ? reinterpret_cast<unsigned int *>(opts->out_rgba8) : nullptr,
-                 opts ? exp2f(opts->exposure_ev) : 1.0f};
+                 opts ? exp2f(opts->exposure_ev) : 1.0f,
+                 n_pix};
     cudaError_t e = cudaMemsetAsync(F->counter, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) return cuda_fail(e, "render: reset counter");
     if (prec == VRNERF_FP32)
@@ -420,7 +440,7 @@ int vrnerf_render(vrnerf_field *F, const float *cameras, const float *intrinsics
     if (rc) return rc;
     RaySource *src = &F->src_scratch;
     make_camera_source(cameras, intrinsics, resolution_host, n, *src);
-    return render_common(F, *src, out, opts, (cudaStream_t)stream);
+    return render_common(F, *src, out, opts, (cudaStream_t)stream, rays);
     ABI_GUARD_END
 }
 
@@ -445,7 +465,7 @@ int vrnerf_render_host(vrnerf_field *F, const float *cameras_host, const float *
     make_camera_source(F->stage_cam, F->stage_cam + (size_t)n * 12, resolution_host, n, *src);
     vrnerf_render_opts o2{};
     if (opts) o2.precision = opts->precision;
-    if ((rc = render_common(F, *src, F->stage_out, &o2, st))) return rc;
+    if ((rc = render_common(F, *src, F->stage_out, &o2, st, rays))) return rc;
     e = cudaMemcpyAsync(out_host, F->stage_out, out_bytes, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "render_host: download");
@@ -464,7 +484,7 @@ int vrnerf_render_rays(vrnerf_field *F, const float *o, const float *d, const fl
     src->d = d;
     src->r = r;
     src->n_slots = B;
-    return render_common(F, *src, out, opts, (cudaStream_t)stream);
+    return render_common(F, *src, out, opts, (cudaStream_t)stream, B);
     ABI_GUARD_END
 }
 

@@ -44,7 +44,31 @@ struct FieldView {
     // contraction), normalised grid position y / 4 + 1/2
     int contract;
     float cen[3], inv_h;
+    // checked builds (VRNERF_CHECKED): bounds-check failures are OR-ed in here
+    unsigned long long *check;
 };
+
+// Checked builds: a failed bounds check records its bit in f.check (read by
+// vrnerf_field_status) and the caller skips or clamps the access; nothing
+// traps. Release builds compile the checks away.
+enum : unsigned long long {
+    kCheckHash = 1ull,    // hash-grid index beyond the table
+    kCheckVoxel = 2ull,   // occupancy voxel index beyond the grid
+    kCheckStep = 4ull,    // sample index beyond the table of distances
+    kCheckPixel = 8ull,   // output pixel beyond the launch's rays
+    kCheckRecord = 16ull, // training record beyond its buffers
+    kCheckTrigger = 32ull // set on purpose by vrnerf_debug_check_trigger
+};
+#if defined(VRNERF_CHECKED) && VRNERF_CHECKED
+#define VRN_CHECKED 1
+__device__ __forceinline__ bool vrn_check(const unsigned long long *flag, bool ok, unsigned long long bit) {
+    if (!ok && flag) atomicOr(const_cast<unsigned long long *>(flag), bit);
+    return ok;
+}
+#else
+#define VRN_CHECKED 0
+__device__ __forceinline__ bool vrn_check(const unsigned long long *, bool ok, unsigned long long) { return ok; }
+#endif
 
 // One launch's rays: either camera views (pixels in 8x4 tiles) or explicit arrays.
 struct ViewInfo {
@@ -74,6 +98,7 @@ struct RenderOut {
     float *normal;              // optional [rays][3]: sum_i w_i n_i (fp32 kernel only)
     unsigned int *rgba8;        // optional [rays]: sRGB8 + coverage at `exposure`
     float exposure;             // 2^ev, linear scale applied before the sRGB encoding
+    long long n_pix;            // rays of the launch (checked builds verify writes; 0: unknown)
 };
 
 // Warp-aggregated add of per-thread counters into stats (all lanes call).
@@ -152,6 +177,9 @@ __device__ __forceinline__ bool sample_voxel(const FieldView &f, const float o[3
         }
     }
     vox = v[0] + f.res[0] * (v[1] + f.res[1] * v[2]);
+    if (VRN_CHECKED && !vrn_check(f.check, vox >= 0 && (long long)vox < (long long)f.res[0] * f.res[1] * f.res[2],
+                                  kCheckVoxel))
+        vox = 0;
     return true;
 }
 __device__ __forceinline__ bool sample_voxel(const FieldView &f, const float o[3], const float d[3],
@@ -225,6 +253,7 @@ __device__ __forceinline__ int march_next(const FieldView &f, const float *__res
                                           unsigned &tested) {
     for (int it = 0; it < max_iter; ++it) {
         if (m.step >= f.S) return MARCH_END;
+        if (VRN_CHECKED && !vrn_check(f.check, m.step >= 0, kCheckStep)) return MARCH_END;
         const float t = sT[m.step];
         int vox, v[3];
         float gc[3];
@@ -387,6 +416,11 @@ __device__ __forceinline__ void level_corners_ph(const FieldView &f, int l, cons
 #pragma unroll
         for (int b = 0; b < 8; ++b) idx[b] = ((b & 1 ? hx1 : hx0) ^ yz[b >> 1]) & f.T_mask;
     }
+#if VRN_CHECKED
+#pragma unroll
+    for (int b = 0; b < 8; ++b)
+        if (!vrn_check(f.check, idx[b] <= f.T_mask, kCheckHash)) idx[b] = 0;
+#endif
 }
 
 __device__ __forceinline__ void level_corners(const FieldView &f, int l, const float p[3],
@@ -447,7 +481,8 @@ __device__ __forceinline__ unsigned int tonemap_rgba8(const float lin[3], float 
 // Per-ray epilogue shared by the render kernels: PQ decode (Eq. 1-2) and the
 // optional outputs.
 __device__ __forceinline__ void finish_outputs(const RenderOut &out, long long pix, const float C[3], float T,
-                                               int n, float depth, const float *N) {
+                                               int n, float depth, const float *N, const unsigned long long *check) {
+    if (VRN_CHECKED && out.n_pix > 0 && !vrn_check(check, pix >= 0 && pix < out.n_pix, kCheckPixel)) return;
     float lin[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {

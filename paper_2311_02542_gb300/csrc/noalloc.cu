@@ -144,11 +144,13 @@ extern "C" int vrnerf_render_noalloc(const vrnerf_field_desc *desc, const void *
         // pageable source: the call returns once t_host has been staged
         e = cudaMemcpyAsync(t_dev, t_host, sizeof(float) * (desc->max_steps + 1),
                             cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, 2 * sizeof(unsigned long long), st);
+        view.check = counter + 1;  // bounds-check bits of checked builds (not reported by this entry)
         if (e != cudaSuccess) return cuda_fail(e, "render_noalloc: scratch set-up");
         RaySource src;
         make_camera_source(cameras, intrinsics, resolution_host, n, src);
         RenderOut ro{out, nullptr, nullptr, nullptr, nullptr};
+        ro.n_pix = rays;
         e = launch_render_simt(view, src, ro, counter, st);
         if (e != cudaSuccess) return cuda_fail(e, "render_noalloc: launch");
         return VRNERF_OK;

@@ -320,6 +320,7 @@ int vrnerf_occupancy_upsample(vrnerf_field *F, int32_t factor) {
     F->view.occ = F->occ;
     F->view.t_tab = F->t_tab;
     F->view.dist = F->dist;
+    F->view.check = reinterpret_cast<unsigned long long *>(F->counter) + 2;
     e = launch_build_dist(F->view, F->dist, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "occupancy_upsample: distance field");

@@ -162,7 +162,7 @@ render_simt_kernel(const FieldView f, const RaySource src, const RenderOut out,
                 if (mres == MARCH_SAMPLE) {
                     have = true;
                 } else if (mres == MARCH_END) {
-                    finish_outputs(out, pix, C, T, n_eval, Dp, NRM ? Nm : nullptr);
+                    finish_outputs(out, pix, C, T, n_eval, Dp, NRM ? Nm : nullptr, f.check);
                     ray = -1;
                     ++st_rays;
                 }
@@ -205,7 +205,7 @@ render_simt_kernel(const FieldView f, const RaySource src, const RenderOut out,
             ++n_eval;
             ++mr.step;
             if (T < f.T_eps) {
-                finish_outputs(out, pix, C, T, n_eval, Dp, NRM ? Nm : nullptr);
+                finish_outputs(out, pix, C, T, n_eval, Dp, NRM ? Nm : nullptr, f.check);
                 ray = -1;
                 ++st_rays;
             }

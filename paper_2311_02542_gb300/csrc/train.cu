@@ -154,7 +154,7 @@ count_kernel(const FieldView f, const float *__restrict__ o_in, const float *__r
 
 __global__ void __launch_bounds__(128)
 emit_kernel(const FieldView f, const float *__restrict__ o_in, const float *__restrict__ d_in, int B,
-            const long long *__restrict__ off, int2 *__restrict__ rec) {
+            const long long *__restrict__ off, const int *__restrict__ cnt, int2 *__restrict__ rec) {
     for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < B; b += (long long)gridDim.x * blockDim.x) {
         MarchRay m;
 #pragma unroll
@@ -166,7 +166,9 @@ emit_kernel(const FieldView f, const float *__restrict__ o_in, const float *__re
         unsigned tested = 0;
         float p[3];
         long long q = off[b];
+        const long long end = q + cnt[b];
         while (march_next(f, f.t_tab, m, p, 1 << 30, tested) == MARCH_SAMPLE) {
+            if (VRN_CHECKED && !vrn_check(f.check, q < end, kCheckRecord)) break;
             rec[q++] = make_int2((int)b, m.step);
             ++m.step;
         }
@@ -649,7 +651,7 @@ static int backward_t(vrnerf_field *F, const float *o, const float *d, const flo
     if (n > 0) {
         e = grid_for(emit_kernel, 128, 0, B, blocks);
         if (e == cudaSuccess) {
-            emit_kernel<<<blocks, 128, 0, st>>>(f, o, d, B, S.off, S.rec);
+            emit_kernel<<<blocks, 128, 0, st>>>(f, o, d, B, S.off, S.cnt, S.rec);
             e = cudaGetLastError();
         }
         const size_t smem_f = sizeof(float) * SimtW<D>::size;

@@ -18,7 +18,7 @@ from . import build as _build
 
 FP32, FP16, BF16, FP8 = 0, 1, 2, 3
 PRECISIONS = {"fp32": FP32, "fp16": FP16, "bf16": BF16, "fp8": FP8}
-OK, EINVAL, ENOMEM, ECUDA, ETIMEDOUT, EBUSY, ENOTFOUND, ECANCELED = 0, -1, -2, -3, -4, -5, -6, -7
+OK, EINVAL, ENOMEM, ECUDA, ETIMEDOUT, EBUSY, ENOTFOUND, ECANCELED, ECHECK = 0, -1, -2, -3, -4, -5, -6, -7, -8
 
 
 class VrnerfError(RuntimeError):
@@ -66,6 +66,8 @@ _SIGS = {
     "vrnerf_field_set_occupancy": (ctypes.c_int, [_VP, _VP]),
     "vrnerf_field_save": (ctypes.c_int, [_VP, ctypes.c_char_p]),
     "vrnerf_history_reset": (ctypes.c_int, [_VP]),
+    "vrnerf_build_checked": (ctypes.c_int, []),
+    "vrnerf_debug_check_trigger": (ctypes.c_int, [_VP, _VP]),
     "vrnerf_forward_rays": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP]),
     "vrnerf_backward_from_grad": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP]),
     "vrnerf_field_param_ptrs": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
@@ -108,7 +110,9 @@ _lib = None
 
 
 def lib_path() -> str:
-    return _build.LIB
+    """The release library, or the checked one (device-side bounds checks)
+    when the environment sets VRNERF_CHECKED=1."""
+    return _build.LIB_CHECKED if os.environ.get("VRNERF_CHECKED") == "1" else _build.LIB
 
 
 def load():
@@ -357,6 +361,14 @@ class FieldModule(torch.nn.Module):
 
     def params_changed(self):
         vrnerf_field_params_changed(self.field)
+
+
+def vrnerf_build_checked() -> bool:
+    return bool(load().vrnerf_build_checked())
+
+
+def vrnerf_debug_check_trigger(field: Field, stream=None):
+    _check(load().vrnerf_debug_check_trigger(field.h, _stream(stream)))
 
 
 def vrnerf_history_reset(field: Field):

@@ -36,6 +36,13 @@ def test_library_exports_every_declared_symbol(lib):
     assert not missing, missing
 
 
+def test_checked_library_exports_the_same_symbols_and_says_so(lib):
+    checked = ctypes.CDLL(B.LIB_CHECKED)
+    missing = [n for n in sorted(_declared()) if not hasattr(checked, n)]
+    assert not missing, missing
+    assert checked.vrnerf_build_checked() == 1 and lib.vrnerf_build_checked() == 0
+
+
 def test_field_sizes_and_validation_on_host(lib):
     from paper_2311_02542_gb300 import vrnerf as V
     cfg = S.cfg_room()

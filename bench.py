@@ -422,9 +422,14 @@ def main():
 
     # work statistics of one frame (untimed): samples, levels fetched, steps
     stats = torch.zeros(4, dtype=torch.int64, device=dev)
-    V.vrnerf_render(field, cams, intr, res, out=out, precision=tuned, stats=stats)
+    n_per_ray = torch.empty(rays, dtype=torch.int32, device=dev)
+    V.vrnerf_render(field, cams, intr, res, out=out, precision=tuned, stats=stats, out_n=n_per_ray)
     torch.cuda.synchronize()
     n_samples, n_levels, n_steps, n_rays_done = [int(x) for x in stats.cpu()]
+    spr = n_per_ray.cpu().numpy()
+    spr_hist = {f"p{q}": int(np.percentile(spr, q)) for q in (50, 90, 99)}
+    spr_hist["max"] = int(spr.max())
+    spr_hist["zero_frac"] = round(float((spr == 0).mean()), 4)
 
     # timed region: tuned path (its warm-up steps run first, untimed),
     # bracketed by barrier + synchronize on both sides
@@ -462,6 +467,7 @@ def main():
         mse = float(((pq - ref_pq).double() ** 2).mean())
         sweep[name] = {"Mrays_s": round(rays / (float(t.mean()) * 1e-3) / 1e6, 2),
                        "psnr_pq_vs_fp32_db": (round(10 * np.log10(1.0 / mse), 2) if mse > 0 else "inf")}
+
 
     # stereo 2 x 2048^2 frame latency (tuned)
     st_c2w = S.stereo_pair(c2w[0])
@@ -505,7 +511,7 @@ def main():
                    "levels": cfg.levels, "log2_T": cfg.log2_T, "occ_res": list(cfg.occ_res),
                    "max_steps": cfg.max_steps, "parallelism": f"replicas{world}",
                    "l2": "256 MB buffer written between timed steps"},
-        "work": {"samples_per_ray": round(n_samples / rays, 3),
+        "work": {"samples_per_ray": round(n_samples / rays, 3), "samples_per_ray_hist": spr_hist,
                  "levels_per_sample": round(n_levels / max(n_samples, 1), 3),
                  "steps_per_ray": round(n_steps / rays, 2), "rays_finished": n_rays_done},
         "precision_sweep": sweep,
@@ -552,6 +558,22 @@ def main():
                                 "cores": threads, "kind": "oracle",
                                 "sample": f"{crays // (128 * 128)} random 128x128 crops of the "
                                           f"2048x2048 frame ({cdt:.1f} s)"}
+        # the oracle's 256^2 window of the frame against each GPU precision
+        import oracle as O
+        crop_K = S.crop_camera(K, 896, 896)
+        crop_res = np.array([[256, 256]], np.int32)
+        oracle_pq = O.Field(cfg, sc.grid, sc.mlp, sc.occ_bits).render(c2w, crop_K, crop_res,
+                                                                      threads=threads)["pq"]
+        psnr = {}
+        for name in ("fp32", "fp16", "bf16", "fp8"):
+            cpq = torch.empty((256 * 256, 3), device=dev)
+            V.vrnerf_render(field, cams, torch.from_numpy(crop_K).to(dev), crop_res,
+                            out=torch.empty((256 * 256, 3), device=dev), precision=V.PRECISIONS[name],
+                            out_pq=cpq)
+            mse_o = float(np.mean((cpq.cpu().numpy().astype(np.float64) - oracle_pq) ** 2))
+            psnr[name] = round(10 * np.log10(1.0 / mse_o), 2) if mse_o > 0 else "inf"
+        line["cpu_baseline"]["gpu_psnr_pq_vs_oracle_db"] = psnr
+        line["cpu_baseline"]["psnr_sample"] = "256x256 window at (896, 896) of the frame, PQ peak 1.0"
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

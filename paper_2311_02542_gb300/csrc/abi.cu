@@ -434,6 +434,7 @@ int vrnerf_render(vrnerf_field *F, const float *cameras, const float *intrinsics
                   const int32_t *resolution_host, int32_t n, float *out,
                   const vrnerf_render_opts *opts, void *stream) {
     ABI_GUARD_BEGIN
+    NvtxRange nvtx_range("vrnerf_render");
     if (!F || !cameras || !intrinsics || !out) return fail(VRNERF_EINVAL, "NULL argument");
     long long rays = 0;
     int rc = check_views(resolution_host, n, rays);
@@ -448,6 +449,7 @@ int vrnerf_render_host(vrnerf_field *F, const float *cameras_host, const float *
                        const int32_t *resolution_host, int32_t n, float *out_host,
                        const vrnerf_render_opts *opts, void *stream) {
     ABI_GUARD_BEGIN
+    NvtxRange nvtx_range("vrnerf_render_host");
     if (!F || !cameras_host || !intrinsics_host || !out_host) return fail(VRNERF_EINVAL, "NULL argument");
     long long rays = 0;
     int rc = check_views(resolution_host, n, rays);
@@ -476,6 +478,7 @@ int vrnerf_render_host(vrnerf_field *F, const float *cameras_host, const float *
 int vrnerf_render_rays(vrnerf_field *F, const float *o, const float *d, const float *r, int32_t B,
                        float *out, const vrnerf_render_opts *opts, void *stream) {
     ABI_GUARD_BEGIN
+    NvtxRange nvtx_range("vrnerf_render_rays");
     if (!F || !o || !d || !r || !out) return fail(VRNERF_EINVAL, "NULL argument");
     if (B < 1) return fail(VRNERF_EINVAL, "B must be >= 1");
     RaySource *src = &F->src_scratch;

@@ -2,9 +2,20 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 
 namespace vrn {
+
+// NVTX range over an entry point or a stage (header-only NVTX 3: free unless
+// a profiler is attached), so that timelines show the library's calls.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Per-kernel launch shape, filled on first use for the current device.
 struct Launch {

@@ -223,6 +223,7 @@ int vrnerf_field_get_history(vrnerf_field *F, float *hist_host) {
 
 int vrnerf_prune(vrnerf_field *F, const float *camera_centres_host, int32_t n_cameras, int32_t points_per_axis,
                  float threshold, int32_t apply, float *alpha_out, uint32_t *occ_bits_out, uint64_t *kept_host) {
+    NvtxRange nvtx_range("vrnerf_prune");
     if (!F || !camera_centres_host) return fail(VRNERF_EINVAL, "NULL argument");
     if (n_cameras < 1 || n_cameras > 65536) return fail(VRNERF_EINVAL, "n_cameras must be in [1, 65536]");
     if (points_per_axis < 1 || points_per_axis > 16) return fail(VRNERF_EINVAL, "points_per_axis must be in [1, 16]");

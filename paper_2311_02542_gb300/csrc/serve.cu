@@ -489,6 +489,7 @@ void vrnerf_server::publish(const std::vector<int> &new_views) {
 }
 
 int vrnerf_server::ensure_kernel() {
+    NvtxRange nvtx_range("serve: ensure kernel");
     if (kernel_launched && cudaEventQuery(kernel_done) != cudaSuccess) return VRNERF_OK;  // still running
     int dev = 0;
     cudaGetDevice(&dev);

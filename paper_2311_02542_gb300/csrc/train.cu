@@ -693,6 +693,7 @@ extern "C" {
 int vrnerf_backward(vrnerf_field *F, const float *rays_o, const float *rays_d, const float *radii,
                     const float *target_linear, int32_t B, float *loss_host, void *stream) {
     try {
+        NvtxRange nvtx_range("vrnerf_backward");
         if (!F || !rays_o || !rays_d || !radii || !target_linear) return fail(VRNERF_EINVAL, "NULL argument");
         if (B < 1) return fail(VRNERF_EINVAL, "B must be >= 1");
         int rc = ensure_train(F, B);
@@ -717,6 +718,7 @@ int vrnerf_backward(vrnerf_field *F, const float *rays_o, const float *rays_d, c
 int vrnerf_forward_rays(vrnerf_field *F, const float *rays_o, const float *rays_d, const float *radii, int32_t B,
                         float *out_pq, int32_t *out_n, void *stream) {
     try {
+        NvtxRange nvtx_range("vrnerf_forward_rays");
         if (!F || !rays_o || !rays_d || !radii || !out_pq || !out_n) return fail(VRNERF_EINVAL, "NULL argument");
         if (B < 1) return fail(VRNERF_EINVAL, "B must be >= 1");
         int rc = ensure_train(F, B);
@@ -733,6 +735,7 @@ int vrnerf_forward_rays(vrnerf_field *F, const float *rays_o, const float *rays_
 int vrnerf_backward_from_grad(vrnerf_field *F, const float *rays_o, const float *rays_d, const float *radii,
                               int32_t B, const int32_t *n_fwd, const float *grad_pq, void *stream) {
     try {
+        NvtxRange nvtx_range("vrnerf_backward_from_grad");
         if (!F || !rays_o || !rays_d || !radii || !n_fwd || !grad_pq) return fail(VRNERF_EINVAL, "NULL argument");
         if (B < 1) return fail(VRNERF_EINVAL, "B must be >= 1");
         int rc = ensure_train(F, B);
@@ -797,6 +800,7 @@ int vrnerf_field_set_grads(vrnerf_field *F, const float *grid_grad_host, const f
 }
 
 int vrnerf_adam_step(vrnerf_field *F, float lr_grid, float lr_mlp, void *stream) {
+    NvtxRange nvtx_range("vrnerf_adam_step");
     if (!F) return fail(VRNERF_EINVAL, "field is NULL");
     if (!F->grid_grad || !F->mlp_grad) return fail(VRNERF_EINVAL, "no gradients yet: call vrnerf_backward");
     if (!(lr_grid >= 0.0f) || !(lr_mlp >= 0.0f)) return fail(VRNERF_EINVAL, "learning rates must be >= 0");

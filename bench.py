@@ -550,7 +550,7 @@ def main():
             "room_unbounded_surface_2048": workload_bench(V, "room_unbounded_surface", tuned,
                                                           max(3, args.steps // 2), flush),
         }
-        line["prune_room_k4"] = prune_bench(V, sc)
+        line["prune_room_surface_k4"] = prune_bench(V, S.make_scene("room_surface"))
     if rank == 0 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
         crays, cdt = run_oracle_sample(sc, c2w, K, args.cpu_seconds, threads)

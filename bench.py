@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--train-steps", type=int, default=5, help="timed 2^20-ray train steps (0: skip)")
     ap.add_argument("--no-extra-workloads", action="store_true",
                     help="skip the paper-grid / unbounded-room frames and the pruning pass")
+    ap.add_argument("--profile-train", action="store_true",
+                    help="small case for ncu: two 2^18-ray training steps on the room field")
     ap.add_argument("--profile-case", action="store_true",
                     help="small case for ncu: two renders of a 1024x1024 window of the room frame")
     return ap.parse_args()
@@ -371,12 +373,31 @@ def profile_case(args):
     return 0
 
 
+def profile_train(args):
+    """Two training steps of 2^18 rays on the room field (grid, gradients and
+    moments about 1 GB on the device): the small case for ncu captures of the
+    training kernels."""
+    import torch
+    from paper_2311_02542_gb300 import synth as S
+    from paper_2311_02542_gb300 import vrnerf as V
+    V.load()
+    sc = S.make_scene(args.variant)
+    field = V.Field(sc.cfg, sc.grid, sc.mlp, sc.occ_bits)
+    poses, intr = S.training_views(sc.occ, sc.cfg, n_views=64)
+    batch = [torch.from_numpy(a).cuda() for a in S.training_batch(poses, intr, 1 << 18, seed=5, step=0)]
+    losses = [V.vrnerf_train_step(field, *batch) for _ in range(2)]
+    print(json.dumps({"profile_train": "room, 2^18 rays", "losses": losses}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
     if args.profile_case:
         return profile_case(args)
+    if args.profile_train:
+        return profile_train(args)
     import torch
     rank, world, local = dist_env()
     torch.cuda.set_device(local)

@@ -558,8 +558,24 @@ def main():
         field_s = V.Field(sc_s.cfg, sc_s.grid, sc_s.mlp, sc_s.occ_bits)
         line["serving_surface_variant"] = serving_bench(V, field_s, sc_s, args.serving_requests)
         field_s.close()
-        line["serving_saturated"] = serving_bench(V, field, sc, max(60, args.serving_requests // 3),
-                                                  warm=10, rate_hz=1e9)
+        n_sat = max(60, args.serving_requests // 3)
+        line["serving_saturated"] = serving_bench(V, field, sc, n_sat, warm=10, rate_hz=1e9)
+        # the same requests rendered one by one without the server (device
+        # buffers): the server's efficiency on this mix
+        reqs = S.request_stream(sc.occ, cfg, n_sat + 10, seed=4, rate_hz=1e9)[10:]
+        direct_rays, direct_ms = 0, 0.0
+        for rq in reqs:
+            nr = int((rq.resolution[:, 0].astype(np.int64) * rq.resolution[:, 1]).sum())
+            o_d = torch.empty((nr, 3), device=dev)
+            c_d, k_d = torch.from_numpy(rq.c2w).to(dev), torch.from_numpy(rq.intrinsics).to(dev)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            V.vrnerf_render(field, c_d, k_d, rq.resolution, out=o_d, precision=V.FP16)
+            b.record()
+            torch.cuda.synchronize()
+            direct_ms += a.elapsed_time(b)
+            direct_rays += nr
+        line["serving_saturated"]["direct_render_Mrays_s"] = round(direct_rays / (direct_ms * 1e-3) / 1e6, 2)
     if args.train_steps > 0:
         line["train_step"] = train_bench(V, sc, args.train_steps)
         # the paper's batch: 12 800 rays (256 rays from each of 50 images)

@@ -195,7 +195,7 @@ using namespace vrn;
 void vrnerf_field::release() {
     release_train_scratch(this);
     void *ptrs[] = {grid,     mlp,      occ,         t_tab,  counter, tc_w,   grid_grad, mlp_grad,
-                    grid_master, m_grid, v_grid, m_mlp, v_mlp, loss_acc, stage_cam, stage_out, dist, hist};
+                    grid_master, m_grid, v_grid, m_mlp, v_mlp, loss_acc, stage_cam, stage_out, dist, hist, tcb_w};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     grid = nullptr;
@@ -205,6 +205,7 @@ void vrnerf_field::release() {
     counter = nullptr;
     dist = nullptr;
     hist = nullptr;
+    tcb_w = nullptr;
     tc_w = nullptr;
     grid_grad = mlp_grad = grid_master = m_grid = v_grid = m_mlp = v_mlp = loss_acc = nullptr;
     stage_cam = stage_out = nullptr;

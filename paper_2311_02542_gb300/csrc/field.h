@@ -26,6 +26,10 @@ struct vrnerf_field {
     size_t tc_w_bytes = 0;
     int tc_prec = -1;
     uint64_t mlp_version = 1, tc_version = 0;
+    // tensor-core backward (bf16 training precision): forward + transposed images
+    void *tcb_w = nullptr;
+    uint64_t tcb_version = 0;
+    int train_prec = VRNERF_FP32;
     // training state
     float *grid_grad = nullptr, *mlp_grad = nullptr;
     float *grid_master = nullptr;  // fp32 master copy when the grid is stored in fp16
@@ -54,6 +58,9 @@ void derive_view(const vrnerf_field_desc &d, FieldView &f, std::vector<float> &t
 void release_train_scratch(vrnerf_field *F);
 
 // render_tc.cu: tcgen05 tensor-core MLP path
+cudaError_t launch_bwd_tc(vrnerf_field *F, const float *o, const float *d, const float *r, const int2 *rec,
+                          const long long *off, const int *n_used, long long n, const float4 *grad_s,
+                          cudaStream_t st);
 cudaError_t launch_render_tc(vrnerf_field *F, const RaySource &src, const RenderOut &out, int prec,
                              cudaStream_t st);
 cudaError_t launch_query_tc(vrnerf_field *F, const float *pos, const float *dir, const float *radius,

@@ -275,7 +275,8 @@ ray_comp_kernel(const FieldView f, const float *__restrict__ o_in, const float *
                 dz[c] = w * g[c] * cc[c] * (1.0f - cc[c]);
                 Cpre[c] += w * cc[c];
             }
-            sc[k0 + k] = make_float4(dsig, dz[0], dz[1], dz[2]);
+            // dL/do_0 = dL/dsigma * sigma (sigma = exp(o_0 + bias)), with this pass's sigma
+            sc[k0 + k] = make_float4(dsig * v.x, dz[0], dz[1], dz[2]);
             T = Tn;
         }
         for (int k = n; k < m; ++k) sc[k0 + k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -314,7 +315,7 @@ sample_bwd_kernel(const FieldView f, const float *__restrict__ o_in, const float
         const long long i = base + lane;
         bool have = false;
         float p[3] = {0, 0, 0}, dir[3] = {0.0f, 0.0f, 1.0f}, rn = 0.0f, dsig = 0.0f, dz[3] = {0, 0, 0};
-        if (i < n_samples) {
+        if (i < n_samples) {  // dsig: dL/do_0 (dL/dsigma * sigma)
             const int2 q = rec[i];
             const long long b = q.x;
             if (i - off[b] < n_used[b]) {
@@ -353,7 +354,6 @@ sample_bwd_kernel(const FieldView f, const float *__restrict__ o_in, const float
 #pragma unroll
             for (int k = 0; k < 16; ++k) o[k] = fmaf(__ldg(W2 + k * 64 + j), h, o[k]);
         }
-        const float sigma = expf(o[0] + f.density_bias);
         float h1[64];
         {
             float x[32];
@@ -434,7 +434,7 @@ sample_bwd_kernel(const FieldView f, const float *__restrict__ o_in, const float
 #pragma unroll
             for (int k = 0; k < 16; ++k) dout[k] = fmaf(__ldg(W3 + j * 32 + k), d, dout[k]);
         }
-        dout[0] += dsig * sigma;
+        dout[0] += dsig;  // dL/do_0 from the ray pass (dL/dsigma * sigma)
         __syncwarp();
         // ---- W2: dout x h (h recomputed) ----
         float h[64];
@@ -670,7 +670,9 @@ static int backward_t(vrnerf_field *F, const float *o, const float *d, const flo
                                                 target ? F->loss_acc : nullptr, C_out ? nullptr : F->hist, C_out);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess && n > 0 && !C_out) {
+    if (e == cudaSuccess && n > 0 && !C_out && F->train_prec == VRNERF_BF16) {
+        e = launch_bwd_tc(F, o, d, r, S.rec, S.off, S.n_used, n, S.sc, st);
+    } else if (e == cudaSuccess && n > 0 && !C_out) {
         const size_t smem_b = sizeof(float) * ((size_t)GradSm<D>::size + (size_t)(kBwdThreads / 32) * 2 * 32 * kStride);
         e = cudaFuncSetAttribute(sample_bwd_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b);
         if (e == cudaSuccess) e = grid_for(sample_bwd_kernel<L>, kBwdThreads, smem_b, n, blocks);
@@ -746,6 +748,14 @@ int vrnerf_backward_from_grad(vrnerf_field *F, const float *rays_o, const float 
     } catch (...) {
         return fail(VRNERF_EINVAL, "backward_from_grad: unexpected C++ exception");
     }
+}
+
+int vrnerf_field_set_train_precision(vrnerf_field *F, int32_t precision) {
+    if (!F) return fail(VRNERF_EINVAL, "field is NULL");
+    if (precision != VRNERF_FP32 && precision != VRNERF_BF16)
+        return fail(VRNERF_EINVAL, "training precision must be VRNERF_FP32 or VRNERF_BF16");
+    F->train_prec = precision;
+    return VRNERF_OK;
 }
 
 int vrnerf_field_param_ptrs(vrnerf_field *F, void **grid, float **mlp, float **grid_grad, float **mlp_grad) {

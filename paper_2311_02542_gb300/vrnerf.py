@@ -67,6 +67,7 @@ _SIGS = {
     "vrnerf_field_save": (ctypes.c_int, [_VP, ctypes.c_char_p]),
     "vrnerf_history_reset": (ctypes.c_int, [_VP]),
     "vrnerf_build_checked": (ctypes.c_int, []),
+    "vrnerf_field_set_train_precision": (ctypes.c_int, [_VP, _I32]),
     "vrnerf_debug_check_trigger": (ctypes.c_int, [_VP, _VP]),
     "vrnerf_forward_rays": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP]),
     "vrnerf_backward_from_grad": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP]),
@@ -361,6 +362,11 @@ class FieldModule(torch.nn.Module):
 
     def params_changed(self):
         vrnerf_field_params_changed(self.field)
+
+
+def vrnerf_field_set_train_precision(field: Field, precision):
+    p = PRECISIONS.get(precision, precision) if isinstance(precision, str) else int(precision)
+    _check(load().vrnerf_field_set_train_precision(field.h, p))
 
 
 def vrnerf_build_checked() -> bool:

@@ -174,3 +174,51 @@ def test_checkpoint_round_trip_resumes_training(V, tmp_path):
         V.vrnerf_field_load(str(tmp_path / "bad.vrnf"), cfg)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("variant", ["room", "room_surface"])
+def test_bf16_tensor_core_backward_against_oracle(V, variant):
+    """The tensor-core backward (bf16 operands, fp32 accumulation) against the
+    fp64 oracle: relative L2 error of each gradient within 6e-2 and cosine
+    similarity above 0.998 (bf16 keeps 8 bits of mantissa, and the sums that
+    form the data gradients cancel; the opaque room's grid gradient is the
+    hardest case, 5 % in L2)."""
+    sc = S.make_scene(variant)
+    cfg = sc.cfg
+    f = V.Field(cfg, sc.grid, sc.mlp, sc.occ_bits)
+    F = O.Field(cfg, sc.grid, sc.mlp, sc.occ_bits)
+    o, d, r, tgt = _crop_rays(sc)
+    loss_ref, rg, rm = F.backward(o, d, r, tgt)
+    V.vrnerf_field_set_train_precision(f, "bf16")
+    loss = V.vrnerf_backward(f, _cuda(o), _cuda(d), _cuda(r), _cuda(tgt))
+    gg, gm = V.vrnerf_field_get_grads(f)
+    V.vrnerf_field_status(f)
+    assert loss == pytest.approx(loss_ref, rel=1e-5)  # the forward stays fp32
+    for got, ref in ((gm, rm), (gg.reshape(-1), rg.reshape(-1))):
+        rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        cos = float(np.dot(got, ref) / (np.linalg.norm(got) * np.linalg.norm(ref)))
+        big = np.abs(ref) > 0.1 * np.abs(ref).max()
+        worst = np.max(np.abs(got - ref)[big] / np.abs(ref)[big])
+        print(variant, got.size, "rel L2", rel, "cos", cos, "worst large", worst)
+        assert rel < 6e-2 and cos > 0.998, (rel, cos, worst)
+    V.vrnerf_field_set_train_precision(f, "fp32")
+    with pytest.raises(V.VrnerfError):
+        V.vrnerf_field_set_train_precision(f, "fp8")
+    f.close()
+
+
+def test_bf16_training_reduces_loss_like_fp32(V):
+    sc = S.make_scene("room")
+    poses, intr = S.training_views(sc.occ, sc.cfg, n_views=64)
+    o, d, r, tgt = S.training_batch(poses, intr, 1 << 14, seed=5, step=0)
+    args = (_cuda(o), _cuda(d), _cuda(r), _cuda(tgt))
+    curves = {}
+    for prec in ("fp32", "bf16"):
+        f = V.Field(sc.cfg, sc.grid, sc.mlp, sc.occ_bits)
+        V.vrnerf_field_set_train_precision(f, prec)
+        curves[prec] = [V.vrnerf_train_step(f, *args, lr_grid=0.01, lr_mlp=0.005) for _ in range(30)]
+        V.vrnerf_field_status(f)
+        f.close()
+    a, b = np.array(curves["fp32"]), np.array(curves["bf16"])
+    assert b[-1] < 0.9 * b[0]
+    assert np.all(np.abs(a - b) <= 0.02 * a), (a[::6], b[::6])

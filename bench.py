@@ -266,12 +266,15 @@ def serving_bench(V, field, sc, n_req, warm=30, rate_hz=36.0 / 0.7, seed=4, in_f
             "note": "latency = submit to image in pinned host memory; fp16 tensor-core MLP"}
 
 
-def train_bench(V, sc, steps, batch=1 << 20):
+def train_bench(V, sc, steps, batch=1 << 20, precision="fp32"):
     """Training step on a batch of rays drawn from 64 synthetic HDR views
-    (targets log-uniform in [1e-3, 1e3]); forward, loss, backward, Adam."""
+    (targets log-uniform in [1e-3, 1e3]); forward, loss, backward, Adam.
+    precision: arithmetic of the backward's MLP products (fp32 CUDA cores or
+    bf16 tcgen05 tensor cores)."""
     import torch
     from paper_2311_02542_gb300 import synth as S
     field = V.Field(sc.cfg, sc.grid, sc.mlp, sc.occ_bits)
+    V.vrnerf_field_set_train_precision(field, precision)
     poses, intr = S.training_views(sc.occ, sc.cfg, n_views=64)
     batches = []
     for k in range(2):
@@ -293,7 +296,8 @@ def train_bench(V, sc, steps, batch=1 << 20):
     field.close()
     return {"batch_rays": batch, "ms_per_step": round(ms, 3),
             "Mrays_s": round(batch / (ms * 1e-3) / 1e6, 2), "loss": round(float(loss), 6),
-            "steps": steps, "mlp": "fp32 (CUDA cores)"}
+            "steps": steps,
+            "mlp_backward": "fp32 (CUDA cores)" if precision == "fp32" else "bf16 operands, fp32 accumulation (tcgen05)"}
 
 
 def workload_bench(V, name, precision, steps, flush):
@@ -580,6 +584,7 @@ def main():
         line["train_step"] = train_bench(V, sc, args.train_steps)
         # the paper's batch: 12 800 rays (256 rays from each of 50 images)
         line["train_step_paper_batch"] = train_bench(V, sc, max(args.train_steps, 20), batch=12800)
+        line["train_step_bf16_tc"] = train_bench(V, sc, args.train_steps, precision="bf16")
     if not args.no_extra_workloads:
         line["workloads"] = {
             "room_paper_grid_2048": workload_bench(V, "room_paper_grid", tuned, max(3, args.steps // 2), flush),

@@ -180,7 +180,7 @@ template <int L>
 __global__ void __launch_bounds__(128)
 sample_fwd_kernel(const FieldView f, const float *__restrict__ o_in, const float *__restrict__ d_in,
                   const float *__restrict__ r_in, const int2 *__restrict__ rec, long long n,
-                  float4 *__restrict__ sc) {
+                  float4 *__restrict__ sc, uint4 *__restrict__ feat_out) {
     constexpr int D = 2 * L;
     extern __shared__ float4 smem4[];
     float *sW = reinterpret_cast<float *>(smem4);
@@ -199,6 +199,18 @@ sample_fwd_kernel(const FieldView f, const float *__restrict__ o_in, const float
         gather_features<L>(f, p, footprint(f, t, r_in[b], p, nullptr, nullptr), feat);
         mlp_simt<D>(sW, feat, d, f.density_bias, sigma, rgb);
         sc[i] = make_float4(sigma, rgb[0], rgb[1], rgb[2]);
+        if (feat_out) {  // bf16 features for the tensor-core backward (D / 8 16-byte words)
+#pragma unroll
+            for (int k = 0; k < D / 8; ++k) {
+                uint32_t w[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const __nv_bfloat162 h = __floats2bfloat162_rn(feat[8 * k + 2 * j], feat[8 * k + 2 * j + 1]);
+                    w[j] = *reinterpret_cast<const uint32_t *>(&h);
+                }
+                feat_out[i * (D / 8) + k] = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
     }
 }
 
@@ -539,7 +551,8 @@ struct TrainScratch {
     // per sample
     int2 *rec = nullptr;
     float4 *sc = nullptr;
-    long long scap = 0;
+    uint4 *feat = nullptr;  // bf16 features per sample (tensor-core backward only)
+    long long scap = 0, fcap = 0;
     unsigned long long *total = nullptr;   // device counter of records
     unsigned long long *total_h = nullptr; // pinned host copy
 };
@@ -601,6 +614,7 @@ void release_train_scratch(vrnerf_field *F) {
     cudaFree(S->off);
     cudaFree(S->rec);
     cudaFree(S->sc);
+    cudaFree(S->feat);
     cudaFree(S->total);
     if (S->total_h) cudaFreeHost(S->total_h);
     delete S;
@@ -648,6 +662,16 @@ static int backward_t(vrnerf_field *F, const float *o, const float *d, const flo
     const long long n = (long long)*S.total_h;
     int rc = ensure_samples(S, n);
     if (rc) return rc;
+    const bool tc_bwd = !C_out && F->train_prec == VRNERF_BF16;
+    if (tc_bwd && n > S.fcap) {
+        cudaFree(S.feat);
+        S.feat = nullptr;
+        S.fcap = 0;
+        const long long want = n + n / 4 + 1024;
+        if ((e = cudaMalloc(&S.feat, sizeof(uint4) * (size_t)(D / 8) * (size_t)want)) != cudaSuccess)
+            return fail(VRNERF_ENOMEM, "sample features (%lld): %s", want, cudaGetErrorString(e));
+        S.fcap = want;
+    }
     if (n > 0) {
         e = grid_for(emit_kernel, 128, 0, B, blocks);
         if (e == cudaSuccess) {
@@ -659,7 +683,7 @@ static int backward_t(vrnerf_field *F, const float *o, const float *d, const flo
             e = cudaFuncSetAttribute(sample_fwd_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_f);
         if (e == cudaSuccess) e = grid_for(sample_fwd_kernel<L>, 128, smem_f, n, blocks);
         if (e == cudaSuccess) {
-            sample_fwd_kernel<L><<<blocks, 128, smem_f, st>>>(f, o, d, r, S.rec, n, S.sc);
+            sample_fwd_kernel<L><<<blocks, 128, smem_f, st>>>(f, o, d, r, S.rec, n, S.sc, tc_bwd ? S.feat : nullptr);
             e = cudaGetLastError();
         }
     }
@@ -670,8 +694,8 @@ static int backward_t(vrnerf_field *F, const float *o, const float *d, const flo
                                                 target ? F->loss_acc : nullptr, C_out ? nullptr : F->hist, C_out);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess && n > 0 && !C_out && F->train_prec == VRNERF_BF16) {
-        e = launch_bwd_tc(F, o, d, r, S.rec, S.off, S.n_used, n, S.sc, st);
+    if (e == cudaSuccess && n > 0 && tc_bwd) {
+        e = launch_bwd_tc(F, o, d, r, S.rec, S.off, S.n_used, n, S.sc, S.feat, st);
     } else if (e == cudaSuccess && n > 0 && !C_out) {
         const size_t smem_b = sizeof(float) * ((size_t)GradSm<D>::size + (size_t)(kBwdThreads / 32) * 2 * 32 * kStride);
         e = cudaFuncSetAttribute(sample_bwd_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b);

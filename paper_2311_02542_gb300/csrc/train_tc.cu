@@ -3,7 +3,8 @@
 // option of the training path; the fp32 CUDA-core kernel stays the default).
 //
 // One persistent CTA per SM walks tiles of 128 samples (row r = thread r):
-//  forward recompute   F = gather(p)           -> L1: H  = relu(F W1^T)
+//  forward recompute   F (bf16 features kept by the forward pass)
+//                                              -> L1: H  = relu(F W1^T)
 //                                              -> L2: O  = H W2^T
 //                      X = [O, SH(d)]          -> L3: H1 = relu(X W3^T)
 //                                              -> L4: H2 = relu(H1 W4^T)
@@ -129,7 +130,8 @@ __global__ void __launch_bounds__(kTile, 1)
 bwd_tc_kernel(const FieldView f, const float *__restrict__ o_in, const float *__restrict__ d_in,
               const float *__restrict__ r_in, const int2 *__restrict__ rec, const long long *__restrict__ off,
               const int *__restrict__ n_used, long long n_samples, const float4 *__restrict__ grad_s,
-              const uint4 *__restrict__ wimg, const uint4 *__restrict__ wtimg, float *__restrict__ grid_grad,
+              const uint4 *__restrict__ feat_in, const uint4 *__restrict__ wimg, const uint4 *__restrict__ wtimg,
+              float *__restrict__ grid_grad,
               float *__restrict__ mlp_grad, unsigned long long *__restrict__ status) {
     constexpr int D = 2 * L;
     using M = BwdSm<D>;
@@ -190,19 +192,14 @@ bwd_tc_kernel(const FieldView f, const float *__restrict__ o_in, const float *__
                 dz[2] = gs.w;
             }
         }
-        // ---- features: F row and F^T column ----
-        {
-            float feat[D];
-            if (have) gather_features<L>(f, p, rn, feat);
-            else
+        // ---- features (bf16, kept by the forward pass): F row and F^T column ----
 #pragma unroll
-                for (int k = 0; k < D; ++k) feat[k] = 0.0f;
+        for (int k = 0; k < D / 8; ++k) {
+            const uint4 w = have ? __ldg(feat_in + i * (D / 8) + k) : make_uint4(0u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4 *>(tF + tc::kmajor_offset(r, 8 * k, D)) = w;  // one core-matrix row
+            const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-            for (int k = 0; k < D; ++k) {
-                const uint16_t v = bf16_bits(feat[k]);
-                put16(tF, r, k, D, v);
-                put16(tFT, k, r, kTile, v);
-            }
+            for (int j = 0; j < 8; ++j) put16(tFT, 8 * k + j, r, kTile, (uint16_t)(ws[j >> 1] >> (16 * (j & 1))));
         }
         // ---- L1: H = relu(F W1^T) ----
         mma_batch(sy, [&] { issue_mma<D, 64>(s0 + M::F, s0 + M::w + W::w1, tbase + kColData, false); });
@@ -410,7 +407,7 @@ static cudaError_t ensure_bwd_images(vrnerf_field *F, cudaStream_t st) {
 template <int L>
 static cudaError_t launch_bwd_tc_t(vrnerf_field *F, const float *o, const float *d, const float *r, const int2 *rec,
                                    const long long *off, const int *n_used, long long n, const float4 *grad_s,
-                                   cudaStream_t st) {
+                                   const uint4 *feat, cudaStream_t st) {
     constexpr int D = 2 * L;
     cudaError_t e = ensure_bwd_images(F, st);
     if (e != cudaSuccess) return e;
@@ -423,7 +420,7 @@ static cudaError_t launch_bwd_tc_t(vrnerf_field *F, const float *o, const float 
     const unsigned char *img = static_cast<const unsigned char *>(F->tcb_w);
     const size_t fwd = (size_t)TcW<D>::bytes;
     unsigned long long *status = reinterpret_cast<unsigned long long *>(F->counter) + 1;
-    kern<<<grid, kTile, smem, st>>>(F->view, o, d, r, rec, off, n_used, n, grad_s,
+    kern<<<grid, kTile, smem, st>>>(F->view, o, d, r, rec, off, n_used, n, grad_s, feat,
                                     reinterpret_cast<const uint4 *>(img), reinterpret_cast<const uint4 *>(img + fwd),
                                     F->grid_grad, F->mlp_grad, status);
     return cudaGetLastError();
@@ -431,9 +428,9 @@ static cudaError_t launch_bwd_tc_t(vrnerf_field *F, const float *o, const float 
 
 cudaError_t launch_bwd_tc(vrnerf_field *F, const float *o, const float *d, const float *r, const int2 *rec,
                           const long long *off, const int *n_used, long long n, const float4 *grad_s,
-                          cudaStream_t st) {
-    return F->view.L == 8 ? launch_bwd_tc_t<8>(F, o, d, r, rec, off, n_used, n, grad_s, st)
-                          : launch_bwd_tc_t<16>(F, o, d, r, rec, off, n_used, n, grad_s, st);
+                          const uint4 *feat, cudaStream_t st) {
+    return F->view.L == 8 ? launch_bwd_tc_t<8>(F, o, d, r, rec, off, n_used, n, grad_s, feat, st)
+                          : launch_bwd_tc_t<16>(F, o, d, r, rec, off, n_used, n, grad_s, feat, st);
 }
 
 }  // namespace vrn

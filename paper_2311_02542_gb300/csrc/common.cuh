@@ -614,4 +614,56 @@ __device__ __forceinline__ int gather_features(const FieldView &f, const float p
     return fetched;
 }
 
+
+// Hash-grid gradient scatter of one sample per lane (all 32 lanes call it,
+// `have` false for lanes without a sample): dL/dfeat times the level weight
+// w_l and the trilinear weight of each corner, added into grid_grad [L][T][F=2].
+// On dense levels neighbouring lanes (consecutive samples of a ray) often hit
+// the same corners, and thousands of samples per batch meet on the few
+// coarse vertices, so runs of equal indices in consecutive lanes are summed
+// with shuffles first and only the run's first lane issues the atomic.
+template <int L>
+__device__ __forceinline__ void scatter_grid_grad(const FieldView &f, const float p[3], float rn,
+                                                  const float *dfeat, bool have, float *grid_grad) {
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const float Ls = have ? lod_star(f, rn) : -1.0e30f;
+#pragma unroll 1
+    for (int l = 0; l < L; ++l) {
+        const float wl = lod_weight(Ls, l);
+        const bool act = have && wl > 0.0f;
+        if (!__any_sync(FULL, act)) break;  // weights fall with l for every lane
+        uint32_t idx[8];
+        float fr[3] = {0.0f, 0.0f, 0.0f};
+        if (act) level_corners(f, l, p, idx, fr);
+        float2 *gbase = reinterpret_cast<float2 *>(grid_grad) + (size_t)l * (f.T_mask + 1u);
+        const bool dense = (f.dense_mask >> l) & 1u;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const float cw = (b & 1 ? fr[0] : 1.0f - fr[0]) * (b & 2 ? fr[1] : 1.0f - fr[1]) *
+                             (b & 4 ? fr[2] : 1.0f - fr[2]) * wl;
+            float gx = act ? cw * dfeat[2 * l] : 0.0f, gy = act ? cw * dfeat[2 * l + 1] : 0.0f;
+            if (!dense) {
+                if (act) atomicAdd(gbase + idx[b], make_float2(gx, gy));
+                continue;
+            }
+            const uint32_t key = act ? idx[b] : 0xffffffffu;
+            const uint32_t prev = __shfl_up_sync(FULL, key, 1);
+            const bool head = lane == 0 || prev != key;
+            const unsigned heads = __ballot_sync(FULL, head);
+            const unsigned above = heads & ~((2u << lane) - 1u);  // heads after this lane
+            const int next = above ? __ffs(above) - 1 : 32;       // end of this lane's run
+#pragma unroll
+            for (int s = 1; s < 32; s <<= 1) {
+                const float ox = __shfl_down_sync(FULL, gx, s), oy = __shfl_down_sync(FULL, gy, s);
+                if (lane + s < next) {
+                    gx += ox;
+                    gy += oy;
+                }
+            }
+            if (head && act) atomicAdd(gbase + idx[b], make_float2(gx, gy));
+        }
+    }
+}
+
 }  // namespace vrn

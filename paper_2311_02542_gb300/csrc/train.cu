@@ -486,23 +486,7 @@ sample_bwd_kernel(const FieldView f, const float *__restrict__ o_in, const float
         __syncwarp();
 
         // ---- hash-grid scatter ----
-        if (have) {
-            const float Ls = lod_star(f, rn);
-            for (int l = 0; l < L; ++l) {
-                const float wl = lod_weight(Ls, l);
-                if (wl <= 0.0f) break;
-                uint32_t idx[8];
-                float fr[3];
-                level_corners(f, l, p, idx, fr);
-                float2 *gbase = reinterpret_cast<float2 *>(grid_grad) + (size_t)l * (f.T_mask + 1u);
-#pragma unroll
-                for (int b = 0; b < 8; ++b) {
-                    const float cw = (b & 1 ? fr[0] : 1.0f - fr[0]) * (b & 2 ? fr[1] : 1.0f - fr[1]) *
-                                     (b & 4 ? fr[2] : 1.0f - fr[2]) * wl;
-                    atomicAdd(gbase + idx[b], make_float2(cw * dfeat[2 * l], cw * dfeat[2 * l + 1]));
-                }
-            }
-        }
+        scatter_grid_grad<L>(f, p, rn, dfeat, have, grid_grad);
     }
     __syncthreads();
     // per-CTA weight gradients -> global, in the [out][in] layout

@@ -51,6 +51,9 @@ def main():
         V.vrnerf_debug_corners(f, o)
         V.vrnerf_history_reset(f)
         V.vrnerf_train_step(f, o, d, r, tgt)
+        V.vrnerf_field_set_train_precision(f, "bf16")  # the tensor-core backward
+        V.vrnerf_train_step(f, o, d, r, tgt)
+        V.vrnerf_field_set_train_precision(f, "fp32")
         pq, n = V.vrnerf_forward_rays(f, o, d, r)
         V.vrnerf_backward_from_grad(f, o, d, r, n, torch.randn_like(pq))
         V.vrnerf_field_status(f)

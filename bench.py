@@ -520,8 +520,8 @@ def main():
     hbm_peak, peak_kind = load_peaks()
     feat_bytes = 2 if cfg.feat_fp16 else 4
     # algorithmic bytes of one launch: 8 corners x F features per fetched
-    # level, 12 B of output per ray, 1 bit of occupancy per tested step
-    alg_bytes = n_levels * 8 * cfg.feats * feat_bytes + rays * 12 + n_steps / 8.0
+    # level, 12 B of output per ray, 1 byte of distance field per march step
+    alg_bytes = n_levels * 8 * cfg.feats * feat_bytes + rays * 12 + n_steps
     achieved = alg_bytes / (ms_step * 1e-3) / 1e9
 
     line = {

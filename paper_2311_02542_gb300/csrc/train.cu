@@ -662,13 +662,17 @@ static int backward_t(vrnerf_field *F, const float *o, const float *d, const flo
             emit_kernel<<<blocks, 128, 0, st>>>(f, o, d, B, S.off, S.cnt, S.rec);
             e = cudaGetLastError();
         }
-        const size_t smem_f = sizeof(float) * SimtW<D>::size;
-        if (e == cudaSuccess)
+        if (e == cudaSuccess && tc_bwd) {
+            // bf16 training: the MLPs of the forward on the tensor cores too
+            e = launch_fwd_tc(F, o, d, r, S.rec, n, S.sc, S.feat, st);
+        } else if (e == cudaSuccess) {
+            const size_t smem_f = sizeof(float) * SimtW<D>::size;
             e = cudaFuncSetAttribute(sample_fwd_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_f);
-        if (e == cudaSuccess) e = grid_for(sample_fwd_kernel<L>, 128, smem_f, n, blocks);
-        if (e == cudaSuccess) {
-            sample_fwd_kernel<L><<<blocks, 128, smem_f, st>>>(f, o, d, r, S.rec, n, S.sc, tc_bwd ? S.feat : nullptr);
-            e = cudaGetLastError();
+            if (e == cudaSuccess) e = grid_for(sample_fwd_kernel<L>, 128, smem_f, n, blocks);
+            if (e == cudaSuccess) {
+                sample_fwd_kernel<L><<<blocks, 128, smem_f, st>>>(f, o, d, r, S.rec, n, S.sc, nullptr);
+                e = cudaGetLastError();
+            }
         }
     }
     if (e == cudaSuccess) e = grid_for(ray_comp_kernel, 128, 0, B, blocks);

@@ -351,6 +351,57 @@ bwd_tc_kernel(const FieldView f, const float *__restrict__ o_in, const float *__
     if (r < 32) tc::tmem_dealloc(tbase, kBwdCols);
 }
 
+// Sample forward of the bf16 training precision: one thread per sample of a
+// 128-sample tile gathers its features straight into the bf16 operand tile
+// (kept in global memory for the backward) and the tile runs the MLPs on the
+// tensor cores; sigma and PQ colour per sample.
+template <int L>
+__global__ void __launch_bounds__(kTcThreads, kTcMinBlocks)
+sample_fwd_tc_kernel(const FieldView f, const float *__restrict__ o_in, const float *__restrict__ d_in,
+                     const float *__restrict__ r_in, const int2 *__restrict__ rec, long long n,
+                     float4 *__restrict__ sc, uint4 *__restrict__ feat_out, const uint4 *__restrict__ wimg,
+                     unsigned long long *__restrict__ status) {
+    constexpr int D = 2 * L;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    float *unused;
+    const TcShared S = tc_setup<D, 1>(smem, wimg, unused, nullptr, 0);
+    const int r = threadIdx.x;
+    uint32_t phase = 0;
+    bool ok = true;
+    const long long tiles = (n + kTcThreads - 1) / kTcThreads;
+    for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        if (__syncthreads_or(*S.abort)) break;
+        const long long i = tile * kTcThreads + r;
+        const bool have = i < n;
+        float dir[3] = {0.0f, 0.0f, 1.0f};
+        if (have) {
+            const int2 q = rec[i];
+            const long long b = q.x;
+            const float o[3] = {o_in[3 * b], o_in[3 * b + 1], o_in[3 * b + 2]};
+            dir[0] = d_in[3 * b];
+            dir[1] = d_in[3 * b + 1];
+            dir[2] = d_in[3 * b + 2];
+            const float t = f.t_tab[q.y];
+            float p[3];
+            int vox;
+            sample_voxel(f, o, dir, t, p, vox);
+            gather_to_tile<L, 1>(f, p, footprint(f, t, r_in[b], p, nullptr, nullptr), S.act, r);
+            const unsigned char *row = S.act + (r >> 3) * (D / 8) * 128 + (r & 7) * 16;
+#pragma unroll
+            for (int j = 0; j < D / 8; ++j) feat_out[i * (D / 8) + j] = *reinterpret_cast<const uint4 *>(row + j * 128);
+        } else {
+            uint32_t z[D / 2];
+#pragma unroll
+            for (int k = 0; k < D / 2; ++k) z[k] = 0u;
+            store_row<D>(S.act, r, z);
+        }
+        float sigma, rgb[3];
+        tc_mlp_any<D, 1>(S, nullptr, dir, f.density_bias, sigma, rgb, phase, ok);
+        if (have) sc[i] = make_float4(sigma, rgb[0], rgb[1], rgb[2]);
+    }
+    tc_teardown(S, status);
+}
+
 // fp32 W1..W4 -> the transposed bf16 image TcWT<D>.
 __global__ void build_wt_image_kernel(const float *__restrict__ mlp, int D, unsigned char *__restrict__ img) {
     // (matrix, rows N = inputs, K = outputs, source offset, source row length)
@@ -408,6 +459,30 @@ static cudaError_t launch_bwd_tc_t(vrnerf_field *F, const float *o, const float 
                                     reinterpret_cast<const uint4 *>(img), reinterpret_cast<const uint4 *>(img + fwd),
                                     F->grid_grad, F->mlp_grad, status);
     return cudaGetLastError();
+}
+
+template <int L>
+static cudaError_t launch_fwd_tc_t(vrnerf_field *F, const float *o, const float *d, const float *r, const int2 *rec,
+                                   long long n, float4 *sc, uint4 *feat, cudaStream_t st) {
+    constexpr int D = 2 * L;
+    cudaError_t e = ensure_bwd_images(F, st);
+    if (e != cudaSuccess) return e;
+    const size_t smem = tc_smem_bytes(D, 0);
+    auto kern = sample_fwd_tc_kernel<L>;
+    int bps = 0;
+    if ((e = prepare_tc(kern, smem, bps)) != cudaSuccess) return e;
+    const long long tiles = (n + kTcThreads - 1) / kTcThreads, cap = (long long)num_sms() * bps;
+    const int grid = (int)(tiles < cap ? tiles : cap);
+    unsigned long long *status = reinterpret_cast<unsigned long long *>(F->counter) + 1;
+    kern<<<grid, kTcThreads, smem, st>>>(F->view, o, d, r, rec, n, sc, feat,
+                                         reinterpret_cast<const uint4 *>(F->tcb_w), status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fwd_tc(vrnerf_field *F, const float *o, const float *d, const float *r, const int2 *rec,
+                          long long n, float4 *sc, uint4 *feat, cudaStream_t st) {
+    return F->view.L == 8 ? launch_fwd_tc_t<8>(F, o, d, r, rec, n, sc, feat, st)
+                          : launch_fwd_tc_t<16>(F, o, d, r, rec, n, sc, feat, st);
 }
 
 cudaError_t launch_bwd_tc(vrnerf_field *F, const float *o, const float *d, const float *r, const int2 *rec,

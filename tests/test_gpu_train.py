@@ -178,10 +178,10 @@ def test_checkpoint_round_trip_resumes_training(V, tmp_path):
 
 @pytest.mark.parametrize("variant", ["room", "room_surface"])
 def test_bf16_tensor_core_backward_against_oracle(V, variant):
-    """The tensor-core backward (bf16 operands, fp32 accumulation) against the
-    fp64 oracle: relative L2 error of each gradient within 6e-2 and cosine
+    """The bf16 training precision (sample forward and backward on the tensor
+    cores, bf16 operands, fp32 accumulation) against the fp64 oracle: relative L2 error of each gradient within 6e-2 and cosine
     similarity above 0.998 (bf16 keeps 8 bits of mantissa, and the sums that
-    form the data gradients cancel; the opaque room's grid gradient is the
+    form the data gradients cancel; the surface room's grid gradient is the
     hardest case, 5 % in L2)."""
     sc = S.make_scene(variant)
     cfg = sc.cfg
@@ -193,7 +193,10 @@ def test_bf16_tensor_core_backward_against_oracle(V, variant):
     loss = V.vrnerf_backward(f, _cuda(o), _cuda(d), _cuda(r), _cuda(tgt))
     gg, gm = V.vrnerf_field_get_grads(f)
     V.vrnerf_field_status(f)
-    assert loss == pytest.approx(loss_ref, rel=1e-5)  # the forward stays fp32
+    # the forward's MLPs run in bf16 too; the loss is a mean over many samples
+    # whose bf16 rounding errors (2^-9 relative) mostly cancel: within 5e-4
+    print(variant, "loss rel err", abs(loss - loss_ref) / loss_ref)
+    assert loss == pytest.approx(loss_ref, rel=5e-4)
     for got, ref in ((gm, rm), (gg.reshape(-1), rg.reshape(-1))):
         rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
         cos = float(np.dot(got, ref) / (np.linalg.norm(got) * np.linalg.norm(ref)))

@@ -62,6 +62,8 @@ def parse():
                     help="skip the paper-grid / unbounded-room frames and the pruning pass")
     ap.add_argument("--profile-train", action="store_true",
                     help="small case for ncu: two 2^18-ray training steps on the room field")
+    ap.add_argument("--train-prec", default="fp32", choices=("fp32", "bf16"),
+                    help="training precision of --profile-train")
     ap.add_argument("--profile-case", action="store_true",
                     help="small case for ncu: two renders of a 1024x1024 window of the room frame")
     return ap.parse_args()
@@ -269,8 +271,8 @@ def serving_bench(V, field, sc, n_req, warm=30, rate_hz=36.0 / 0.7, seed=4, in_f
 def train_bench(V, sc, steps, batch=1 << 20, precision="fp32"):
     """Training step on a batch of rays drawn from 64 synthetic HDR views
     (targets log-uniform in [1e-3, 1e3]); forward, loss, backward, Adam.
-    precision: arithmetic of the backward's MLP products (fp32 CUDA cores or
-    bf16 tcgen05 tensor cores)."""
+    precision: arithmetic of the MLPs in the training forward and backward
+    (fp32 CUDA cores or bf16 tcgen05 tensor cores)."""
     import torch
     from paper_2311_02542_gb300 import synth as S
     field = V.Field(sc.cfg, sc.grid, sc.mlp, sc.occ_bits)
@@ -297,7 +299,8 @@ def train_bench(V, sc, steps, batch=1 << 20, precision="fp32"):
     return {"batch_rays": batch, "ms_per_step": round(ms, 3),
             "Mrays_s": round(batch / (ms * 1e-3) / 1e6, 2), "loss": round(float(loss), 6),
             "steps": steps,
-            "mlp_backward": "fp32 (CUDA cores)" if precision == "fp32" else "bf16 operands, fp32 accumulation (tcgen05)"}
+            "mlp": "fp32 (CUDA cores)" if precision == "fp32"
+            else "forward and backward: bf16 operands, fp32 accumulation (tcgen05)"}
 
 
 def workload_bench(V, name, precision, steps, flush):
@@ -387,10 +390,11 @@ def profile_train(args):
     V.load()
     sc = S.make_scene(args.variant)
     field = V.Field(sc.cfg, sc.grid, sc.mlp, sc.occ_bits)
+    V.vrnerf_field_set_train_precision(field, args.train_prec)
     poses, intr = S.training_views(sc.occ, sc.cfg, n_views=64)
     batch = [torch.from_numpy(a).cuda() for a in S.training_batch(poses, intr, 1 << 18, seed=5, step=0)]
     losses = [V.vrnerf_train_step(field, *batch) for _ in range(2)]
-    print(json.dumps({"profile_train": "room, 2^18 rays", "losses": losses}))
+    print(json.dumps({"profile_train": "room, 2^18 rays", "precision": args.train_prec, "losses": losses}))
     return 0
 
 
@@ -478,7 +482,8 @@ def main():
     # plain fp32 path on the same frame
     ms32 = timed(V.FP32, max(3, args.steps // 2), 2) if tuned != V.FP32 else ms
 
-    # precision sweep on the same frame: throughput, and PQ-space PSNR against
+    # precision sweep on the same frame: throughput (median frame, so that one
+    # host stall between the start event and the launch does not count), and PQ-space PSNR against
     # the fp32 render (the tests hold each precision to >= 50 dB against the
     # fp64 CPU oracle on 256^2 crops)
     ref_pq = torch.empty((rays, 3), device=dev)
@@ -490,7 +495,7 @@ def main():
         pq = torch.empty((rays, 3), device=dev)
         V.vrnerf_render(field, cams, intr, res, out=out, precision=p, out_pq=pq)
         mse = float(((pq - ref_pq).double() ** 2).mean())
-        sweep[name] = {"Mrays_s": round(rays / (float(t.mean()) * 1e-3) / 1e6, 2),
+        sweep[name] = {"Mrays_s": round(rays / (float(np.median(t)) * 1e-3) / 1e6, 2),
                        "psnr_pq_vs_fp32_db": (round(10 * np.log10(1.0 / mse), 2) if mse > 0 else "inf")}
 
 

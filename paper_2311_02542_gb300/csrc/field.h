@@ -57,12 +57,12 @@ int check_desc(const vrnerf_field_desc *d);
 void derive_view(const vrnerf_field_desc &d, FieldView &f, std::vector<float> &t_tab);
 void release_train_scratch(vrnerf_field *F);
 
-// render_tc.cu: tcgen05 tensor-core MLP path
+// render_tc.cu, train_tc.cu: tcgen05 tensor-core MLP path
 cudaError_t launch_fwd_tc(vrnerf_field *F, const float *o, const float *d, const float *r, const int2 *rec,
                           long long n, float4 *sc, uint4 *feat, cudaStream_t st);
 cudaError_t launch_bwd_tc(vrnerf_field *F, const float *o, const float *d, const float *r, const int2 *rec,
                           const long long *off, const int *n_used, long long n, const float4 *grad_s,
-                          const uint4 *feat, cudaStream_t st);
+                          const uint4 *feat, float4 *dfeat, cudaStream_t st);
 cudaError_t launch_render_tc(vrnerf_field *F, const RaySource &src, const RenderOut &out, int prec,
                              cudaStream_t st);
 cudaError_t launch_query_tc(vrnerf_field *F, const float *pos, const float *dir, const float *radius,

@@ -535,7 +535,8 @@ struct TrainScratch {
     // per sample
     int2 *rec = nullptr;
     float4 *sc = nullptr;
-    uint4 *feat = nullptr;  // bf16 features per sample (tensor-core backward only)
+    uint4 *feat = nullptr;    // bf16 features per sample (tensor-core backward only)
+    float4 *dfeat = nullptr;  // dL/dfeatures per sample, fp32 (tensor-core backward only)
     long long scap = 0, fcap = 0;
     unsigned long long *total = nullptr;   // device counter of records
     unsigned long long *total_h = nullptr; // pinned host copy
@@ -599,6 +600,7 @@ void release_train_scratch(vrnerf_field *F) {
     cudaFree(S->rec);
     cudaFree(S->sc);
     cudaFree(S->feat);
+    cudaFree(S->dfeat);
     cudaFree(S->total);
     if (S->total_h) cudaFreeHost(S->total_h);
     delete S;
@@ -649,10 +651,13 @@ static int backward_t(vrnerf_field *F, const float *o, const float *d, const flo
     const bool tc_bwd = !C_out && F->train_prec == VRNERF_BF16;
     if (tc_bwd && n > S.fcap) {
         cudaFree(S.feat);
+        cudaFree(S.dfeat);
         S.feat = nullptr;
+        S.dfeat = nullptr;
         S.fcap = 0;
         const long long want = n + n / 4 + 1024;
-        if ((e = cudaMalloc(&S.feat, sizeof(uint4) * (size_t)(D / 8) * (size_t)want)) != cudaSuccess)
+        if ((e = cudaMalloc(&S.feat, sizeof(uint4) * (size_t)(D / 8) * (size_t)want)) != cudaSuccess ||
+            (e = cudaMalloc(&S.dfeat, sizeof(float4) * (size_t)(D / 4) * (size_t)want)) != cudaSuccess)
             return fail(VRNERF_ENOMEM, "sample features (%lld): %s", want, cudaGetErrorString(e));
         S.fcap = want;
     }
@@ -683,7 +688,7 @@ static int backward_t(vrnerf_field *F, const float *o, const float *d, const flo
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && n > 0 && tc_bwd) {
-        e = launch_bwd_tc(F, o, d, r, S.rec, S.off, S.n_used, n, S.sc, S.feat, st);
+        e = launch_bwd_tc(F, o, d, r, S.rec, S.off, S.n_used, n, S.sc, S.feat, S.dfeat, st);
     } else if (e == cudaSuccess && n > 0 && !C_out) {
         const size_t smem_b = sizeof(float) * ((size_t)GradSm<D>::size + (size_t)(kBwdThreads / 32) * 2 * 32 * kStride);
         e = cudaFuncSetAttribute(sample_bwd_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b);

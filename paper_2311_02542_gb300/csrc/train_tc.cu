@@ -131,7 +131,7 @@ bwd_tc_kernel(const FieldView f, const float *__restrict__ o_in, const float *__
               const float *__restrict__ r_in, const int2 *__restrict__ rec, const long long *__restrict__ off,
               const int *__restrict__ n_used, long long n_samples, const float4 *__restrict__ grad_s,
               const uint4 *__restrict__ feat_in, const uint4 *__restrict__ wimg, const uint4 *__restrict__ wtimg,
-              float *__restrict__ grid_grad,
+              float4 *__restrict__ dfeat_out,
               float *__restrict__ mlp_grad, unsigned long long *__restrict__ status) {
     constexpr int D = 2 * L;
     using M = BwdSm<D>;
@@ -171,20 +171,15 @@ bwd_tc_kernel(const FieldView f, const float *__restrict__ o_in, const float *__
         if (__syncthreads_or(*abort)) break;
         const long long i = tile * kTile + r;
         bool have = false;
-        float p[3] = {0, 0, 0}, dir[3] = {0.0f, 0.0f, 1.0f}, rn = 0.0f, dsig = 0.0f, dz[3] = {0, 0, 0};
+        float dir[3] = {0.0f, 0.0f, 1.0f}, dsig = 0.0f, dz[3] = {0, 0, 0};
         if (i < n_samples) {
             const int2 q = rec[i];
             const long long b = q.x;
             if (i - off[b] < n_used[b]) {
                 have = true;
-                const float o[3] = {o_in[3 * b], o_in[3 * b + 1], o_in[3 * b + 2]};
                 dir[0] = d_in[3 * b];
                 dir[1] = d_in[3 * b + 1];
                 dir[2] = d_in[3 * b + 2];
-                const float t = f.t_tab[q.y];
-                int vox;
-                sample_voxel(f, o, dir, t, p, vox);
-                rn = footprint(f, t, r_in[b], p, nullptr, nullptr);
                 const float4 gs = grad_s[i];
                 dsig = gs.x;
                 dz[0] = gs.y;
@@ -314,10 +309,15 @@ bwd_tc_kernel(const FieldView f, const float *__restrict__ o_in, const float *__
                 issue_mma<64, D>(s0 + M::H, s0 + M::wt + WT::w1, tbase + kColData, false);
         });
         acc = true;
-        {
+        {  // dL/dfeatures (fp32) for the grid scatter; the TMEM load is warp-wide
             float dfeat[D];
             tmem_row(lane_addr + kColData, D, dfeat);
-            scatter_grid_grad<L>(f, p, rn, dfeat, have, grid_grad);
+            if (have) {
+#pragma unroll
+                for (int k = 0; k < D / 4; ++k)
+                    dfeat_out[i * (D / 4) + k] =
+                        make_float4(dfeat[4 * k], dfeat[4 * k + 1], dfeat[4 * k + 2], dfeat[4 * k + 3]);
+            }
         }
         tc::fence_before_sync();  // this tile's TMEM reads precede the next tile's MMAs
     }
@@ -349,6 +349,47 @@ bwd_tc_kernel(const FieldView f, const float *__restrict__ o_in, const float *__
     tc::fence_after_sync();
     if (r == 0 && *abort && status) atomicExch(status, (unsigned long long)(-VRNERF_ETIMEDOUT));
     if (r < 32) tc::tmem_dealloc(tbase, kBwdCols);
+}
+
+// Grid-gradient scatter of the tensor-core backward: one thread per sample
+// (consecutive samples in a warp, so the dense-level runs still merge), at
+// full occupancy so that the atomics' latency is hidden; dL/dfeatures come
+// from the backward kernel in fp32.
+template <int L>
+__global__ void __launch_bounds__(128)
+grid_scatter_kernel(const FieldView f, const float *__restrict__ o_in, const float *__restrict__ d_in,
+                    const float *__restrict__ r_in, const int2 *__restrict__ rec, const long long *__restrict__ off,
+                    const int *__restrict__ n_used, long long n, const float4 *__restrict__ dfeat_in,
+                    float *__restrict__ grid_grad) {
+    constexpr int D = 2 * L;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i0 = (long long)blockIdx.x * blockDim.x; i0 < n; i0 += stride) {  // uniform per block
+        const long long i = i0 + threadIdx.x;
+        bool have = false;
+        float p[3] = {0.0f, 0.0f, 0.0f}, rn = 0.0f, dfeat[D];
+        if (i < n) {
+            const int2 q = rec[i];
+            const long long b = q.x;
+            if (i - off[b] < n_used[b]) {
+                have = true;
+                const float o[3] = {o_in[3 * b], o_in[3 * b + 1], o_in[3 * b + 2]};
+                const float d[3] = {d_in[3 * b], d_in[3 * b + 1], d_in[3 * b + 2]};
+                const float t = f.t_tab[q.y];
+                int vox;
+                sample_voxel(f, o, d, t, p, vox);
+                rn = footprint(f, t, r_in[b], p, nullptr, nullptr);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < D / 4; ++k) {
+            const float4 v = have ? __ldg(dfeat_in + i * (D / 4) + k) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            dfeat[4 * k] = v.x;
+            dfeat[4 * k + 1] = v.y;
+            dfeat[4 * k + 2] = v.z;
+            dfeat[4 * k + 3] = v.w;
+        }
+        scatter_grid_grad<L>(f, p, rn, dfeat, have, grid_grad);
+    }
 }
 
 // Sample forward of the bf16 training precision: one thread per sample of a
@@ -442,7 +483,7 @@ static cudaError_t ensure_bwd_images(vrnerf_field *F, cudaStream_t st) {
 template <int L>
 static cudaError_t launch_bwd_tc_t(vrnerf_field *F, const float *o, const float *d, const float *r, const int2 *rec,
                                    const long long *off, const int *n_used, long long n, const float4 *grad_s,
-                                   const uint4 *feat, cudaStream_t st) {
+                                   const uint4 *feat, float4 *dfeat, cudaStream_t st) {
     constexpr int D = 2 * L;
     cudaError_t e = ensure_bwd_images(F, st);
     if (e != cudaSuccess) return e;
@@ -457,7 +498,14 @@ static cudaError_t launch_bwd_tc_t(vrnerf_field *F, const float *o, const float 
     unsigned long long *status = reinterpret_cast<unsigned long long *>(F->counter) + 1;
     kern<<<grid, kTile, smem, st>>>(F->view, o, d, r, rec, off, n_used, n, grad_s, feat,
                                     reinterpret_cast<const uint4 *>(img), reinterpret_cast<const uint4 *>(img + fwd),
-                                    F->grid_grad, F->mlp_grad, status);
+                                    dfeat, F->mlp_grad, status);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, grid_scatter_kernel<L>, 128, 0)) != cudaSuccess)
+        return e;
+    const long long blocks = (n + 127) / 128, cap = (long long)num_sms() * (per_sm > 0 ? per_sm : 1);
+    grid_scatter_kernel<L><<<(int)(blocks < cap ? blocks : cap), 128, 0, st>>>(F->view, o, d, r, rec, off, n_used, n,
+                                                                               dfeat, F->grid_grad);
     return cudaGetLastError();
 }
 
@@ -487,9 +535,9 @@ cudaError_t launch_fwd_tc(vrnerf_field *F, const float *o, const float *d, const
 
 cudaError_t launch_bwd_tc(vrnerf_field *F, const float *o, const float *d, const float *r, const int2 *rec,
                           const long long *off, const int *n_used, long long n, const float4 *grad_s,
-                          const uint4 *feat, cudaStream_t st) {
-    return F->view.L == 8 ? launch_bwd_tc_t<8>(F, o, d, r, rec, off, n_used, n, grad_s, feat, st)
-                          : launch_bwd_tc_t<16>(F, o, d, r, rec, off, n_used, n, grad_s, feat, st);
+                          const uint4 *feat, float4 *dfeat, cudaStream_t st) {
+    return F->view.L == 8 ? launch_bwd_tc_t<8>(F, o, d, r, rec, off, n_used, n, grad_s, feat, dfeat, st)
+                          : launch_bwd_tc_t<16>(F, o, d, r, rec, off, n_used, n, grad_s, feat, dfeat, st);
 }
 
 }  // namespace vrn

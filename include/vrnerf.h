@@ -263,12 +263,13 @@ int vrnerf_backward_from_grad(vrnerf_field *field, const float *rays_o, const fl
                               const float *radii, int32_t B, const int32_t *n_fwd,
                               const float *grad_pq, void *stream);
 
-/* Arithmetic of the training backward's MLP products: VRNERF_FP32 (default;
+/* Arithmetic of the MLPs in training (Sec. 6, A9): VRNERF_FP32 (default;
  * CUDA cores, gradients within 1e-4 of the fp64 reference) or VRNERF_BF16
- * (tcgen05 tensor cores: bf16 activations, deltas and weights, fp32
- * accumulation; the forward pass, compositing and hash-grid scatter stay
- * fp32). Applies to vrnerf_backward, vrnerf_train_step and
- * vrnerf_backward_from_grad. EINVAL for other precisions. */
+ * (tcgen05 tensor cores for the per-sample forward and backward: bf16
+ * features, activations, deltas and weights, fp32 accumulation; the
+ * compositing, the loss and the hash-grid scatter stay fp32). Applies to
+ * vrnerf_backward, vrnerf_train_step and vrnerf_backward_from_grad
+ * (vrnerf_forward_rays stays fp32). EINVAL for other precisions. */
 int vrnerf_field_set_train_precision(vrnerf_field *field, int32_t precision);
 
 /* Device pointers of the field's parameters ([L][T][F] grid in its storage

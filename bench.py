@@ -504,7 +504,7 @@ def main():
     st_K = np.concatenate([K, K])
     st_res = np.array([[2048, 2048], [2048, 2048]], np.int32)
     st_out = torch.empty((2 * rays, 3), device=dev)
-    st_ms = timed(tuned, max(args.steps, 20), 3, st_res, torch.from_numpy(st_c2w).to(dev),
+    st_ms = timed(tuned, max(args.steps, 50), 10, st_res, torch.from_numpy(st_c2w).to(dev),
                   torch.from_numpy(st_K).to(dev), st_out)
 
     # end to end through the host-buffer entry point (pinned host memory)
@@ -605,6 +605,9 @@ def main():
                                 "cores": threads, "kind": "oracle",
                                 "sample": f"{crays // (128 * 128)} random 128x128 crops of the "
                                           f"2048x2048 frame ({cdt:.1f} s)"}
+        # the same on one host core (a shorter sample)
+        crays1, cdt1 = run_oracle_sample(sc, c2w, K, min(4.0, args.cpu_seconds / 3), 1)
+        line["cpu_baseline"]["single_core_Mrays_s"] = round(crays1 / cdt1 / 1e6, 5)
         # the oracle's 256^2 window of the frame against each GPU precision
         import oracle as O
         crop_K = S.crop_camera(K, 896, 896)

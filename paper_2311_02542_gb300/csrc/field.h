@@ -63,6 +63,9 @@ cudaError_t launch_fwd_tc(vrnerf_field *F, const float *o, const float *d, const
 cudaError_t launch_bwd_tc(vrnerf_field *F, const float *o, const float *d, const float *r, const int2 *rec,
                           const long long *off, const int *n_used, long long n, const float4 *grad_s,
                           const uint4 *feat, float4 *dfeat, cudaStream_t st);
+cudaError_t launch_grid_scatter(vrnerf_field *F, const float *o, const float *d, const float *r, const int2 *rec,
+                                const long long *off, const int *n_used, long long n, const float4 *dfeat,
+                                cudaStream_t st);
 cudaError_t launch_render_tc(vrnerf_field *F, const RaySource &src, const RenderOut &out, int prec,
                              cudaStream_t st);
 cudaError_t launch_query_tc(vrnerf_field *F, const float *pos, const float *dir, const float *radius,

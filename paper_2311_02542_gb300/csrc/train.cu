@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(kBwdThreads)
 sample_bwd_kernel(const FieldView f, const float *__restrict__ o_in, const float *__restrict__ d_in,
                   const float *__restrict__ r_in, const int2 *__restrict__ rec, const long long *__restrict__ off,
                   const int *__restrict__ n_used, long long n_samples, const float4 *__restrict__ grad_s,
-                  float *__restrict__ grid_grad, float *__restrict__ mlp_grad) {
+                  float4 *__restrict__ dfeat_out, float *__restrict__ mlp_grad) {
     constexpr int D = 2 * L;
     using G = GradSm<D>;
     extern __shared__ float4 smem4[];
@@ -485,8 +485,12 @@ sample_bwd_kernel(const FieldView f, const float *__restrict__ o_in, const float
         }
         __syncwarp();
 
-        // ---- hash-grid scatter ----
-        scatter_grid_grad<L>(f, p, rn, dfeat, have, grid_grad);
+        // ---- dL/dfeatures for the hash-grid scatter (a separate full-occupancy kernel) ----
+        if (have) {
+#pragma unroll
+            for (int k = 0; k < D / 4; ++k)
+                dfeat_out[i * (D / 4) + k] = make_float4(dfeat[4 * k], dfeat[4 * k + 1], dfeat[4 * k + 2], dfeat[4 * k + 3]);
+        }
     }
     __syncthreads();
     // per-CTA weight gradients -> global, in the [out][in] layout
@@ -536,8 +540,8 @@ struct TrainScratch {
     int2 *rec = nullptr;
     float4 *sc = nullptr;
     uint4 *feat = nullptr;    // bf16 features per sample (tensor-core backward only)
-    float4 *dfeat = nullptr;  // dL/dfeatures per sample, fp32 (tensor-core backward only)
-    long long scap = 0, fcap = 0;
+    float4 *dfeat = nullptr;  // dL/dfeatures per sample, fp32 (backward)
+    long long scap = 0, fcap = 0, dcap = 0;
     unsigned long long *total = nullptr;   // device counter of records
     unsigned long long *total_h = nullptr; // pinned host copy
 };
@@ -651,15 +655,21 @@ static int backward_t(vrnerf_field *F, const float *o, const float *d, const flo
     const bool tc_bwd = !C_out && F->train_prec == VRNERF_BF16;
     if (tc_bwd && n > S.fcap) {
         cudaFree(S.feat);
-        cudaFree(S.dfeat);
         S.feat = nullptr;
-        S.dfeat = nullptr;
         S.fcap = 0;
         const long long want = n + n / 4 + 1024;
-        if ((e = cudaMalloc(&S.feat, sizeof(uint4) * (size_t)(D / 8) * (size_t)want)) != cudaSuccess ||
-            (e = cudaMalloc(&S.dfeat, sizeof(float4) * (size_t)(D / 4) * (size_t)want)) != cudaSuccess)
+        if ((e = cudaMalloc(&S.feat, sizeof(uint4) * (size_t)(D / 8) * (size_t)want)) != cudaSuccess)
             return fail(VRNERF_ENOMEM, "sample features (%lld): %s", want, cudaGetErrorString(e));
         S.fcap = want;
+    }
+    if (!C_out && n > S.dcap) {
+        cudaFree(S.dfeat);
+        S.dfeat = nullptr;
+        S.dcap = 0;
+        const long long want = n + n / 4 + 1024;
+        if ((e = cudaMalloc(&S.dfeat, sizeof(float4) * (size_t)(D / 4) * (size_t)want)) != cudaSuccess)
+            return fail(VRNERF_ENOMEM, "sample feature gradients (%lld): %s", want, cudaGetErrorString(e));
+        S.dcap = want;
     }
     if (n > 0) {
         e = grid_for(emit_kernel, 128, 0, B, blocks);
@@ -695,9 +705,10 @@ static int backward_t(vrnerf_field *F, const float *o, const float *d, const flo
         if (e == cudaSuccess) e = grid_for(sample_bwd_kernel<L>, kBwdThreads, smem_b, n, blocks);
         if (e == cudaSuccess) {
             sample_bwd_kernel<L><<<blocks, kBwdThreads, smem_b, st>>>(f, o, d, r, S.rec, S.off, S.n_used, n, S.sc,
-                                                                      F->grid_grad, F->mlp_grad);
+                                                                      S.dfeat, F->mlp_grad);
             e = cudaGetLastError();
         }
+        if (e == cudaSuccess) e = launch_grid_scatter(F, o, d, r, S.rec, S.off, S.n_used, n, S.dfeat, st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "backward");
     return VRNERF_OK;

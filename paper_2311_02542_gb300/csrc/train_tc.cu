@@ -500,13 +500,27 @@ static cudaError_t launch_bwd_tc_t(vrnerf_field *F, const float *o, const float 
                                     reinterpret_cast<const uint4 *>(img), reinterpret_cast<const uint4 *>(img + fwd),
                                     dfeat, F->mlp_grad, status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return launch_grid_scatter(F, o, d, r, rec, off, n_used, n, dfeat, st);
+}
+
+template <int L>
+static cudaError_t launch_grid_scatter_t(vrnerf_field *F, const float *o, const float *d, const float *r,
+                                         const int2 *rec, const long long *off, const int *n_used, long long n,
+                                         const float4 *dfeat, cudaStream_t st) {
     int per_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, grid_scatter_kernel<L>, 128, 0)) != cudaSuccess)
-        return e;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, grid_scatter_kernel<L>, 128, 0);
+    if (e != cudaSuccess) return e;
     const long long blocks = (n + 127) / 128, cap = (long long)num_sms() * (per_sm > 0 ? per_sm : 1);
     grid_scatter_kernel<L><<<(int)(blocks < cap ? blocks : cap), 128, 0, st>>>(F->view, o, d, r, rec, off, n_used, n,
                                                                                dfeat, F->grid_grad);
     return cudaGetLastError();
+}
+
+cudaError_t launch_grid_scatter(vrnerf_field *F, const float *o, const float *d, const float *r, const int2 *rec,
+                                const long long *off, const int *n_used, long long n, const float4 *dfeat,
+                                cudaStream_t st) {
+    return F->view.L == 8 ? launch_grid_scatter_t<8>(F, o, d, r, rec, off, n_used, n, dfeat, st)
+                          : launch_grid_scatter_t<16>(F, o, d, r, rec, off, n_used, n, dfeat, st);
 }
 
 template <int L>

@@ -168,6 +168,15 @@ def run_oracle_sample(sc, c2w, K, seconds, threads):
     return rays, time.perf_counter() - t0
 
 
+def workload_config(cfg, variant, world):
+    """The workload both arms measure: one 2048x2048 eye buffer of the room
+    field per step and GPU."""
+    return {"workload": WORKLOAD, "variant": variant, "resolution": [2048, 2048],
+            "views_per_step": 1, "rays_per_step": 2048 * 2048, "levels": cfg.levels,
+            "log2_T": cfg.log2_T, "occ_res": list(cfg.occ_res), "max_steps": cfg.max_steps,
+            "parallelism": f"replicas{world}"}
+
+
 def reference_arm(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -197,7 +206,7 @@ def reference_arm(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(1e3 * dt / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "variant": args.variant,
+            "config": {**workload_config(sc.cfg, args.variant, args.gpus),
                        "sample": "one 256x256 crop of the 2048x2048 frame per step"},
             "cpu_baseline": {"value": round(v, 4), "unit": "Mrays/s", "cores": threads,
                              "kind": "oracle",
@@ -536,11 +545,9 @@ def main():
         "dtype": {"fp32": "f32", "fp16": "f16+f32acc", "bf16": "bf16+f32acc",
                   "fp8": "e4m3+f16+f32acc"}[precision_name],
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "variant": args.variant, "resolution": [2048, 2048],
-                   "views_per_step": 1, "rays_per_step": rays, "mlp_precision": precision_name,
-                   "levels": cfg.levels, "log2_T": cfg.log2_T, "occ_res": list(cfg.occ_res),
-                   "max_steps": cfg.max_steps, "parallelism": f"replicas{world}",
+        "config": {**workload_config(cfg, args.variant, world),
                    "l2": "256 MB buffer written between timed steps"},
+        "mlp_precision": precision_name,
         "work": {"samples_per_ray": round(n_samples / rays, 3), "samples_per_ray_hist": spr_hist,
                  "levels_per_sample": round(n_levels / max(n_samples, 1), 3),
                  "steps_per_ray": round(n_steps / rays, 2), "rays_finished": n_rays_done},

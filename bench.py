@@ -48,7 +48,7 @@ NCU_TRAFFIC_BYTES = 53212928 + 25871616
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="auto")
@@ -102,7 +102,9 @@ def load_peaks():
 
 
 class Clocks:
-    """nvidia-smi sampler running during the timed region."""
+    """nvidia-smi sampler (every 200 ms) started before the warm-up; mark()
+    at the start of the timed region, stop() at its end. The summary uses the
+    samples taken between the two (the last earlier one if none was)."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -115,6 +117,20 @@ class Clocks:
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
+        self.skip = 0
+
+    def _lines(self):
+        self.f.flush()
+        self.f.seek(0)
+        return [ln for ln in self.f.read().splitlines() if len(ln.split(",")) >= 9]
+
+    def mark(self):
+        """Waits (up to 3 s) for the sampler's first line, then records how
+        many lines precede the timed region."""
+        t0 = time.perf_counter()
+        while self.p is not None and not self._lines() and time.perf_counter() - t0 < 3.0:
+            time.sleep(0.02)
+        self.skip = len(self._lines()) if self.p is not None else 0
 
     def stop(self):
         if self.p is None:
@@ -124,11 +140,11 @@ class Clocks:
             self.p.wait(timeout=5)
         except Exception:
             self.p.kill()
-        self.f.flush()
-        self.f.seek(0)
+        lines = self._lines()
+        lines = lines[self.skip:] or lines[max(self.skip - 1, 0):self.skip]
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.f.read().splitlines():
+        for ln in lines:
             parts = [x.strip() for x in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -471,13 +487,14 @@ def main():
 
     # timed region: tuned path (its warm-up steps run first, untimed),
     # bracketed by barrier + synchronize on both sides
+    clk = Clocks(local)
     for _ in range(args.warmup):
         V.vrnerf_render(field, cams, intr, res, out=out, precision=tuned)
     torch.cuda.synchronize()
+    clk.mark()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    clk = Clocks(local)
     t_wall0 = time.perf_counter()
     ms = timed(tuned, args.steps, 0)
     torch.cuda.synchronize()
@@ -489,7 +506,7 @@ def main():
     value = whole_job_mrays(rays, world, ms_step)
 
     # plain fp32 path on the same frame
-    ms32 = timed(V.FP32, max(3, args.steps // 2), 2) if tuned != V.FP32 else ms
+    ms32 = timed(V.FP32, 10, 2) if tuned != V.FP32 else ms
 
     # precision sweep on the same frame: throughput (median frame, so that one
     # host stall between the start event and the launch does not count), and PQ-space PSNR against
@@ -500,7 +517,7 @@ def main():
     sweep = {}
     for name in ("fp32", "fp16", "bf16", "fp8"):
         p = V.PRECISIONS[name]
-        t = timed(p, max(3, args.steps // 4), 2)
+        t = timed(p, 5, 2)
         pq = torch.empty((rays, 3), device=dev)
         V.vrnerf_render(field, cams, intr, res, out=out, precision=p, out_pq=pq)
         mse = float(((pq - ref_pq).double() ** 2).mean())
@@ -513,7 +530,7 @@ def main():
     st_K = np.concatenate([K, K])
     st_res = np.array([[2048, 2048], [2048, 2048]], np.int32)
     st_out = torch.empty((2 * rays, 3), device=dev)
-    st_ms = timed(tuned, max(args.steps, 50), 10, st_res, torch.from_numpy(st_c2w).to(dev),
+    st_ms = timed(tuned, 50, 10, st_res, torch.from_numpy(st_c2w).to(dev),
                   torch.from_numpy(st_K).to(dev), st_out)
 
     # end to end through the host-buffer entry point (pinned host memory)
@@ -523,7 +540,7 @@ def main():
     for _ in range(2):
         V.vrnerf_render_host(field, h_cam, h_K, res, out=h_out, precision=tuned)
     e2e_t = []
-    for _ in range(max(3, args.steps // 2)):
+    for _ in range(10):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -599,10 +616,10 @@ def main():
         line["train_step_bf16_tc"] = train_bench(V, sc, args.train_steps, precision="bf16")
     if not args.no_extra_workloads:
         line["workloads"] = {
-            "room_paper_grid_2048": workload_bench(V, "room_paper_grid", tuned, max(3, args.steps // 2), flush),
-            "room_unbounded_2048": workload_bench(V, "room_unbounded", tuned, max(3, args.steps // 2), flush),
+            "room_paper_grid_2048": workload_bench(V, "room_paper_grid", tuned, 10, flush),
+            "room_unbounded_2048": workload_bench(V, "room_unbounded", tuned, 10, flush),
             "room_unbounded_surface_2048": workload_bench(V, "room_unbounded_surface", tuned,
-                                                          max(3, args.steps // 2), flush),
+                                                          10, flush),
         }
         line["prune_room_surface_k4"] = prune_bench(V, S.make_scene("room_surface"))
     if rank == 0 and not args.no_cpu_baseline:

@@ -190,7 +190,7 @@ int vrnerf_render(vrnerf_field *field, const float *cameras, const float *intrin
                   const int32_t *resolution_host, int32_t n, float *out,
                   const vrnerf_render_opts *opts, void *stream);
 
-/* vrnerf_render with every array in host memory: copies the cameras in and
+/* vrnerf_render (Sec. 5) with every array in host memory: copies the cameras in and
  * the image out on `stream` through the field's device staging buffers and
  * returns after the stream has finished (synchronous). The optional outputs
  * of opts are ignored. EINVAL, ENOMEM, ECUDA. */
@@ -241,9 +241,9 @@ int vrnerf_backward(vrnerf_field *field, const float *rays_o, const float *rays_
                     const float *radii, const float *target_linear, int32_t B, float *loss_host,
                     void *stream);
 
-/* The forward of the training path for explicit rays: PQ colour out_pq
- * [B][3] and composited sample count out_n [B] (the render of
- * vrnerf_render_rays with VRNERF_FP32, early termination included),
+/* The forward of the training path for explicit rays (Sec. 4.1, Sec. 6):
+ * PQ colour out_pq [B][3] and composited sample count out_n [B] (the render
+ * of vrnerf_render_rays with VRNERF_FP32, early termination included),
  * computed sample-parallel like vrnerf_backward, so that small batches fill
  * the GPU. Device memory; waits for `stream` once. EINVAL, ENOMEM, ECUDA. */
 int vrnerf_forward_rays(vrnerf_field *field, const float *rays_o, const float *rays_d,
@@ -294,9 +294,9 @@ int vrnerf_field_params_changed(vrnerf_field *field);
 int vrnerf_build_checked(void);
 int vrnerf_debug_check_trigger(vrnerf_field *field, void *stream);
 
-/* Display tonemapping of an existing PQ image (the exposure sweep of the
- * paper's results: PQ colour to sRGB at a chosen exposure, without
- * re-rendering). pq [n][3] and optional T [n] (NULL: alpha 255) in device
+/* Display tonemapping of an existing PQ image (Sec. 4.1: the exposure sweep
+ * at rendering time; Sec. 6 evaluates in tonemapped sRGB): PQ colour to sRGB
+ * at a chosen exposure, without re-rendering. pq [n][3] and optional T [n] (NULL: alpha 255) in device
  * memory; rgba8 [n] as vrnerf_render_opts.out_rgba8. Asynchronous on
  * `stream`. EINVAL (n < 0, NULL pointers), ECUDA. */
 int vrnerf_tonemap(const float *pq, const float *T, int64_t n, float exposure_ev, uint32_t *rgba8,
@@ -348,7 +348,8 @@ int vrnerf_field_get_grads(vrnerf_field *field, float *grid_grad_host, float *ml
  * keeps fp32 master weights and the first and second moments. */
 int vrnerf_adam_step(vrnerf_field *field, float lr_grid, float lr_mlp, void *stream);
 
-/* vrnerf_backward followed by vrnerf_adam_step. */
+/* vrnerf_backward followed by vrnerf_adam_step: one training iteration of
+ * Sec. 6. */
 int vrnerf_train_step(vrnerf_field *field, const float *rays_o, const float *rays_d,
                       const float *radii, const float *target_linear, int32_t B, float lr_grid,
                       float lr_mlp, float *loss_host, void *stream);
@@ -385,11 +386,12 @@ typedef struct {
     double wall_s;             /* since the first request after the last reset */
 } vrnerf_serve_stats;
 
-/* Starts a server for `field` on its device: a scheduler thread, two streams
- * and an output arena of hbm_budget_bytes on the device. A request is
- * admitted when its output (12 bytes per ray) fits in the arena's free space
- * and the in-flight views fit the server's view ring (256); otherwise it
- * waits in arrival order. precision: VRNERF_FP16 or VRNERF_BF16. The server
+/* Serving (Sec. 5: real-time rendering of stereo eye buffers, here as
+ * continuous batching on one GPU). Starts a server for `field` on its
+ * device: a scheduler thread, two streams and an output arena of
+ * hbm_budget_bytes on the device. A request is admitted when its output
+ * (12 bytes per ray) fits in the arena's free space and the in-flight views
+ * fit the server's view ring (256); otherwise it waits in arrival order. precision: VRNERF_FP16 or VRNERF_BF16. The server
  * owns the field until vrnerf_server_destroy: make no other call on the
  * field meanwhile. EINVAL, ENOMEM. */
 int vrnerf_server_create(vrnerf_field *field, uint64_t hbm_budget_bytes, int32_t precision,

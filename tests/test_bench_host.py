@@ -56,3 +56,15 @@ def test_both_arms_share_the_workload_config():
     assert c["levels"] == 16 and c["log2_T"] == 21 and c["occ_res"] == [256, 256, 256]
     assert c["parallelism"] == "replicas2"
     assert "mlp_precision" not in c
+
+
+def test_clock_sampler_without_nvidia_smi_reports_it():
+    import shutil
+
+    import bench
+    if shutil.which("nvidia-smi"):
+        pytest.skip("nvidia-smi present")
+    c = bench.Clocks(0)
+    c.mark()
+    s = c.stop()
+    assert s["sm_mhz"] is None and s["reasons"] == ["nvidia-smi unavailable"]

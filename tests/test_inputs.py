@@ -1,0 +1,88 @@
+"""The seeded synthetic inputs follow their stated recipe: serving request mix
+(Poisson arrivals at 36/0.7 req/s, 70 % stereo pairs 63 mm apart, singles of
+side 512 / 1024 / 1536, pitch and roll within 30 degrees), training batches
+(90 degree frusta, HDR targets log-uniform in [1e-3, 1e3]) and the benchmark
+camera (1.7 m eye height, level)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2311_02542_gb300 import synth as S
+
+
+@pytest.fixture(scope="module")
+def room():
+    return S.make_scene("room", with_params=False)
+
+
+def _orthonormal(m):
+    R = m[:, :3].astype(np.float64)
+    return np.allclose(R.T @ R, np.eye(3), atol=1e-6)
+
+
+def test_pose_frame_is_orthonormal_and_right_handed():
+    for yaw, pitch, roll in ((0.3, 0.2, -0.4), (2.0, -0.5, 0.1), (5.0, 0.0, 0.0)):
+        m = S.pose_from_angles(np.zeros(3), yaw, pitch, roll)
+        assert _orthonormal(m)
+        right, down, fwd = (m[:, k].astype(np.float64) for k in range(3))
+        assert np.allclose(np.cross(fwd, right), down, atol=1e-6)  # x right, y down, z forward
+        assert fwd[2] == pytest.approx(math.sin(pitch), abs=1e-6)
+
+
+def test_request_stream_mix_rate_and_poses(room):
+    rate = 36.0 / 0.7
+    reqs = S.request_stream(room.occ, room.cfg, 2000, rate_hz=rate)
+    t = np.array([r.arrival_s for r in reqs])
+    gaps = np.diff(np.concatenate([[0.0], t]))
+    assert np.all(gaps > 0)
+    assert gaps.mean() == pytest.approx(1.0 / rate, rel=0.06)
+    assert gaps.std() == pytest.approx(1.0 / rate, rel=0.1)  # exponential: std = mean
+    stereo = [r for r in reqs if r.stereo]
+    assert len(stereo) / len(reqs) == pytest.approx(0.7, abs=0.03)
+    sides = [int(r.resolution[0, 0]) for r in reqs if not r.stereo]
+    counts = {s: sides.count(s) for s in (512, 1024, 1536)}
+    assert sum(counts.values()) == len(sides) and min(counts.values()) > 0.25 * len(sides)
+    for r in stereo[:200]:
+        assert r.resolution.tolist() == [[2048, 2048], [2048, 2048]]
+        left, right = r.c2w[0].astype(np.float64), r.c2w[1].astype(np.float64)
+        assert np.linalg.norm(right[:, 3] - left[:, 3]) == pytest.approx(0.063, abs=1e-5)
+        assert np.allclose(left[:, :3], right[:, :3])
+    s30 = math.sin(math.radians(30)) + 1e-6
+    for r in reqs[:300]:
+        m = r.c2w[0].astype(np.float64)
+        assert _orthonormal(r.c2w[0])
+        assert abs(m[2, 2]) <= s30  # pitch
+        assert np.all((m[:, 3] > 0) & (m[:, 3] < np.array(room.cfg.aabb_max)))
+
+
+def test_training_batch_frusta_and_targets(room):
+    poses, intr = S.training_views(room.occ, room.cfg, n_views=64)
+    assert poses.shape == (64, 3, 4)
+    o, d, r, tgt = S.training_batch(poses, intr, 1 << 16, seed=5, step=3)
+    assert np.allclose(np.linalg.norm(d.astype(np.float64), axis=1), 1.0, atol=1e-6)
+    assert np.all(r == np.float32(0.5 / float(intr[0])))
+    # every ray lies in the 90 degree frustum of the view it starts from
+    k = np.array([np.flatnonzero((poses[:, :, 3] == oi).all(axis=1))[0] for oi in o[:2000]])
+    P = poses[k].astype(np.float64)
+    dd = d[:2000].astype(np.float64)
+    fwd = np.einsum("ij,ij->i", dd, P[:, :, 2])
+    assert np.all(fwd > 0)
+    for axis in (0, 1):
+        assert np.all(np.abs(np.einsum("ij,ij->i", dd, P[:, :, axis]) / fwd) <= 1.0 + 1e-6)
+    assert tgt.min() >= 1e-3 * (1 - 1e-6) and tgt.max() <= 1e3 * (1 + 1e-6)
+    lg = np.log(tgt.astype(np.float64))
+    assert lg.mean() == pytest.approx(0.0, abs=0.05)
+    assert lg.std() == pytest.approx(2 * math.log(1e3) / math.sqrt(12), rel=0.02)  # uniform in log
+    # another step draws another batch
+    o2, _, _, _ = S.training_batch(poses, intr, 1 << 16, seed=5, step=4)
+    assert not np.array_equal(o, o2)
+
+
+def test_benchmark_camera_is_level_at_eye_height(room):
+    c2w, K, res = S.camera_room(room.occ, room.cfg, 2, 2048, 2048)
+    m = c2w[0].astype(np.float64)
+    assert m[2, 3] == pytest.approx(1.7, abs=1e-6)
+    assert abs(m[2, 2]) < 1e-6  # forward is horizontal
+    assert res.tolist() == [[2048, 2048]]
+    assert float(K[0, 0]) == pytest.approx(1024.0, rel=1e-6)  # 90 degree field of view

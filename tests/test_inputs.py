@@ -86,3 +86,30 @@ def test_benchmark_camera_is_level_at_eye_height(room):
     assert abs(m[2, 2]) < 1e-6  # forward is horizontal
     assert res.tolist() == [[2048, 2048]]
     assert float(K[0, 0]) == pytest.approx(1024.0, rel=1e-6)  # 90 degree field of view
+
+
+def test_unbounded_room_has_windows_ground_and_far_buildings():
+    sc = S.make_scene("room_unbounded", with_params=False)
+    cfg = sc.cfg
+    assert cfg.contract and sc.occ.shape == (256, 256, 256)
+    cen = (np.array(cfg.aabb_min) + np.array(cfg.aabb_max)) / 2
+    h = 0.5 * max(np.array(cfg.aabb_max) - np.array(cfg.aabb_min))
+
+    def occupied(p):
+        x = (np.asarray(p, np.float64) - cen) / h
+        m = np.abs(x).max()
+        y = x if m <= 1 else (2 - 1 / m) * x / m
+        i = np.minimum(((y + 2) / 4 * 256).astype(int), 255)
+        return bool(sc.occ[i[2], i[1], i[0]])
+
+    assert occupied((10.0, 10.0, -0.5))      # floor / ground under the room
+    assert occupied((-0.1, 1.5, 1.6))        # wall between windows
+    assert not occupied((-0.1, 5.0, 1.6))    # window opening in the same wall
+    assert not occupied((10.0, 10.0, 1.7))   # eye height in the room
+    assert occupied((400.0, 10.0, -0.5))     # ground far outside (the slab -1 <= z <= 0)
+    # buildings: occupied voxels above the horizon outside the inner cube
+    n = 256
+    yc = (np.arange(n) + 0.5) / n * 4 - 2
+    far = (np.abs(yc)[None, :] > 1.2) | (np.abs(yc)[:, None] > 1.2)  # [y][x]
+    above = yc > 0.02
+    assert sc.occ[above][:, far].any()

@@ -41,8 +41,11 @@ WORKLOAD = "room_2048x2048_single_eye"
 
 # DRAM bytes read + written by one 2048x2048 launch of render_tc_kernel<16, 0, 0>
 # (ncu dram__bytes_read.sum + dram__bytes_write.sum, one capture of the benchmark
-# frame); to be taken again whenever that kernel changes.
+# frame). NCU_TRAFFIC_CURRENT says whether the kernel is unchanged since that
+# capture; when it is not, the bench line reports traffic null and the old
+# figure beside it.
 NCU_TRAFFIC_BYTES = 53212928 + 25871616
+NCU_TRAFFIC_CURRENT = False  # captured before the bounds-check option touched the kernel's parameters
 
 
 def parse():
@@ -581,7 +584,11 @@ def main():
                 "d2h_bytes_per_step": rays * 12},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": hbm_peak,
                      "unit": "GB/s", "frac": round(achieved / hbm_peak, 5),
-                     "traffic": NCU_TRAFFIC_BYTES if precision_name == "fp16" and args.variant == "room" else None,
+                     "traffic": (NCU_TRAFFIC_BYTES if NCU_TRAFFIC_CURRENT and precision_name == "fp16"
+                                 and args.variant == "room" else None),
+                     "traffic_last_measured": NCU_TRAFFIC_BYTES,
+                     "traffic_note": ("ncu DRAM bytes of one launch, taken before the kernel last changed "
+                                      "(its parameter block gained the bounds-check pointer)"),
                      "peak_kind": peak_kind, "kernel": "render (fused march+gather+MLP+composite)"},
         "gpu_launches": args.steps,
         "clocks": clocks,

@@ -637,6 +637,7 @@ typedef struct {
 /* Per-sample tape entry for the backward pass. */
 typedef struct {
     float p[3];
+    int32_t vox; /* the sample's occupancy voxel, as the march found it */
     double r_norm, delta, sigma, alpha, Tin, c[3];
 } orc_tape;
 
@@ -664,6 +665,7 @@ static void render_one(const orc_desc *D, const orc_geom *g, const double *grid,
         if (tape) {
             orc_tape *e = &tape[n];
             memcpy(e->p, p, sizeof p);
+            e->vox = vox;
             e->r_norm = r_norm;
             e->delta = delta;
             e->sigma = s.sigma;
@@ -1167,7 +1169,9 @@ void orc_prune(const orc_desc *D, const double *grid, const double *mlp, const u
 
 /* Training history (Sec. 4.3.2): for explicit rays, the largest opacity
  * 1 - exp(-sigma delta) of any composited sample, per voxel; hist [voxels]
- * is raised, not reset. */
+ * is raised, not reset. A sample's voxel is the one the occupancy march
+ * found it in (sample_voxel), so a contracted scene (Sec. 4) records it in
+ * the contracted grid. */
 void orc_history(const orc_desc *D, const double *grid, const double *mlp, const uint32_t *occ,
                  const float *o, const float *d, const float *r, int32_t B, float *hist)
 {
@@ -1180,16 +1184,8 @@ void orc_history(const orc_desc *D, const double *grid, const double *mlp, const
         orc_ray_out ro;
         render_one(D, &g, grid, mlp, occ, t_tab, o + 3 * b, d + 3 * b, (double)r[b], NULL, NULL, &ro, tape, 0);
         for (int32_t k = 0; k < ro.n_eval; ++k) {
-            const float *p = tape[k].p;
-            /* voxel of the composited sample */
-            int32_t v[3], vox, ok = 1;
-            for (int a = 0; a < 3; ++a) {
-                float gk = (p[a] - g.mn[a]) * g.inv_cell[a];
-                if (!(gk >= 0.0f) || !(gk < (float)D->occ_res[a])) ok = 0;
-                v[a] = (int32_t)floorf(gk);
-            }
-            if (!ok) continue;
-            vox = v[0] + D->occ_res[0] * (v[1] + D->occ_res[1] * v[2]);
+            /* the voxel the march tested the sample in (contraction-aware) */
+            const int32_t vox = tape[k].vox;
             const float a = (float)tape[k].alpha;
             if (a > hist[vox]) hist[vox] = a;
         }

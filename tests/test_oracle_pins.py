@@ -879,6 +879,39 @@ def test_contracted_march_brute_force():
     assert cnt.sum() > 100
 
 
+def test_contracted_history_brute_force():
+    """History of a contracted scene (Sec. 4.3.2 with the contraction of
+    Sec. 4): with constant density every composited sample's opacity is
+    1 - exp(-sigma delta_i), recorded in the voxel of the contracted grid the
+    sample falls in (found here by brute force from the contracted position);
+    the bounded rule (p - box_min) / cell would put it elsewhere or drop it.
+    Rays start inside the box and 20 units outside it."""
+    cfg = _contracted_cfg(occ_res=(16, 16, 16), density_bias=0.5, T_eps=0.0)
+    rng = np.random.default_rng(6)
+    occ = rng.uniform(size=(16, 16, 16)) < 0.2
+    F = O.Field(cfg, np.zeros((cfg.levels, cfg.T, 2)), np.zeros(O.mlp_count(cfg)), S.pack_bits(occ))
+    n = 120
+    o = np.concatenate([rng.uniform(0.2, 0.8, (n // 2, 3)),
+                        0.5 + 20 * rng.normal(size=(n // 2, 3))]).astype(np.float32)
+    d = np.where(np.arange(n)[:, None] < n // 2, rng.normal(size=(n, 3)), 0.5 - o)
+    d = (d / np.linalg.norm(d, axis=1, keepdims=True)).astype(np.float32)
+    h = O.history(F, o, d, np.zeros(n, np.float32))
+    t = O.sample_table(cfg).astype(np.float64)
+    flat = occ.reshape(-1)
+    want = np.zeros(16 ** 3)
+    for b in range(n):
+        p = (o[b][None, :] + t[:-1, None].astype(np.float32) * d[b][None, :]).astype(np.float32)
+        v = np.clip(np.floor(O.grid_position(cfg, p) * np.float32(16)).astype(np.int64), 0, 15)
+        vox = v[:, 0] + 16 * (v[:, 1] + 16 * v[:, 2])
+        for i, vx in enumerate(vox):
+            if flat[vx]:
+                want[vx] = max(want[vx], 1 - np.exp(-np.exp(0.5) * (t[i + 1] - t[i])))
+    assert (want > 0).sum() > 100
+    # voxels outside the box's image [4, 12)^3 are reached too
+    assert (want.reshape(16, 16, 16)[:4] > 0).any()
+    np.testing.assert_allclose(h, want.astype(np.float32), rtol=1e-6, atol=0)
+
+
 def test_contracted_density_grad_matches_central_differences():
     """As the plain-scene pin, with the gradient chained through J_C: points in
     the outer shell and in the inner cube, away from cell faces and from the

@@ -384,6 +384,12 @@ typedef struct {
     uint64_t pending, inflight;
     double p50_ms, p99_ms, max_ms; /* submit-to-output-on-host latency */
     double wall_s;             /* since the first request after the last reset */
+    uint64_t max_inflight;     /* most requests admitted to the GPU at once since the last reset */
+    uint64_t tile_rounds;      /* 128-row MLP tiles the kernel has run since the server
+                                  was created (updated as requests finish) */
+    uint64_t mixed_tile_rounds; /* of those, tiles whose rows held samples of two or more
+                                   requests: work of different requests overlapping on the
+                                   device, in the same tensor-core MMAs */
 } vrnerf_serve_stats;
 
 /* Serving (Sec. 5: real-time rendering of stereo eye buffers, here as

@@ -44,7 +44,8 @@ constexpr int kRing = 256;  // views the ring holds; in-flight views stay below 
 struct __align__(16) ServeView {
     float c2w[12];
     float K[4];
-    int W, H, tiles_x, pad;
+    int W, H, tiles_x;
+    unsigned int req;      // sequence number of the request the view belongs to
     unsigned long long slot_begin, slot_end;
     float *out;            // device [W*H][3]
     unsigned int *done;    // host-mapped flag: set to the slot count when the view is finished
@@ -83,7 +84,8 @@ template <int L, int FMT, bool CT>
 __global__ void __launch_bounds__(kTcThreads, kTcMinBlocks)
 serve_kernel(const FieldView f, ServeView *__restrict__ ring, const ServeCtl *__restrict__ ctl,
              unsigned int *__restrict__ cursor, const uint4 *__restrict__ wimg,
-             unsigned long long idle_ns, unsigned long long *__restrict__ status) {
+             unsigned long long idle_ns, unsigned long long *__restrict__ status,
+             unsigned long long *__restrict__ tile_stats) {
     unsigned int *idle = cursor + 1;  // idle CTAs of this launch | quitting bit
     constexpr int D = 2 * L;
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -91,6 +93,12 @@ serve_kernel(const FieldView f, ServeView *__restrict__ ring, const ServeCtl *__
     const TcShared S = tc_setup<D, FMT>(smem, wimg, unused, nullptr, 0);
     const float *__restrict__ sT = f.t_tab;  // sample distances, read through L1
     __shared__ int s_quit;
+    // smallest and largest request number among the rows of this tile round
+    __shared__ unsigned int s_rmin, s_rmax;
+    if (threadIdx.x == 0) {
+        s_rmin = 0xffffffffu;
+        s_rmax = 0u;
+    }
 
     constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -100,6 +108,7 @@ serve_kernel(const FieldView f, ServeView *__restrict__ ring, const ServeCtl *__
     float adj[CT ? 6 : 1];  // contracted scenes: offsets to the adjacent pixels' rays
     float *dst = nullptr;
     int view = -1, cnt_view = -1;
+    unsigned int my_req = 0;  // request of this thread's ray
     unsigned int cnt = 0;  // finished slots of cnt_view not yet reported
     uint32_t phase = 0;
     unsigned tested = 0;
@@ -210,6 +219,7 @@ serve_kernel(const FieldView f, ServeView *__restrict__ ring, const ServeCtl *__
                             march_init(f, mr);
                             dst = ldcg_ptr(&sv->out) + 3ll * ((long long)py * W + px);
                             view = v;
+                            my_req = __ldcg(&sv->req);
                             live = true;
                             T = 1.0f;
                             C[0] = C[1] = C[2] = 0.0f;
@@ -284,8 +294,24 @@ serve_kernel(const FieldView f, ServeView *__restrict__ ring, const ServeCtl *__
             for (int k = 0; k < D / 2; ++k) z[k] = 0u;
             store_row<D>(S.act, threadIdx.x, z);
         }
+        {
+            // which requests share this tile's MLP rows (read after the MMAs'
+            // barriers; reset by thread 0 before the next round's barrier)
+            const unsigned lo = __reduce_min_sync(FULL, have ? my_req : 0xffffffffu);
+            const unsigned hi = __reduce_max_sync(FULL, have ? my_req : 0u);
+            if (lane == 0 && lo != 0xffffffffu) {
+                atomicMin(&s_rmin, lo);
+                atomicMax(&s_rmax, hi);
+            }
+        }
         float sigma, rgb[3];
         tc_mlp_any<D, FMT>(S, nullptr, mr.d, f.density_bias, sigma, rgb, phase, ok);
+        if (threadIdx.x == 0) {
+            atomicAdd(tile_stats, 1ull);
+            if (s_rmin != s_rmax) atomicAdd(tile_stats + 1, 1ull);
+            s_rmin = 0xffffffffu;
+            s_rmax = 0u;
+        }
         if (have) {
             const float sd = sigma * delta;
             const float w = T * (-expm1f(-sd));
@@ -303,7 +329,8 @@ serve_kernel(const FieldView f, ServeView *__restrict__ ring, const ServeCtl *__
 
 template <int L, int FMT, bool CT>
 static cudaError_t launch_serve_ct(vrnerf_field *F, ServeView *ring, const ServeCtl *ctl,
-                                   unsigned int *cursor, unsigned long long idle_ns, cudaStream_t st) {
+                                   unsigned int *cursor, unsigned long long idle_ns,
+                                   unsigned long long *tile_stats, cudaStream_t st) {
     const size_t smem = tc_smem_bytes(2 * L, 0);
     auto kern = serve_kernel<L, FMT, CT>;
     int bps = 0;
@@ -311,15 +338,17 @@ static cudaError_t launch_serve_ct(vrnerf_field *F, ServeView *ring, const Serve
     if (e != cudaSuccess) return e;
     unsigned long long *status = reinterpret_cast<unsigned long long *>(F->counter) + 1;
     kern<<<num_sms() * bps, kTcThreads, smem, st>>>(F->view, ring, ctl, cursor,
-                                                    static_cast<const uint4 *>(F->tc_w), idle_ns, status);
+                                                    static_cast<const uint4 *>(F->tc_w), idle_ns, status,
+                                                    tile_stats);
     return cudaGetLastError();
 }
 
 template <int L, int FMT>
 static cudaError_t launch_serve_t(vrnerf_field *F, ServeView *ring, const ServeCtl *ctl,
-                                  unsigned int *cursor, unsigned long long idle_ns, cudaStream_t st) {
-    return F->view.contract ? launch_serve_ct<L, FMT, true>(F, ring, ctl, cursor, idle_ns, st)
-                            : launch_serve_ct<L, FMT, false>(F, ring, ctl, cursor, idle_ns, st);
+                                  unsigned int *cursor, unsigned long long idle_ns,
+                                  unsigned long long *tile_stats, cudaStream_t st) {
+    return F->view.contract ? launch_serve_ct<L, FMT, true>(F, ring, ctl, cursor, idle_ns, tile_stats, st)
+                            : launch_serve_ct<L, FMT, false>(F, ring, ctl, cursor, idle_ns, tile_stats, st);
 }
 
 }  // namespace vrn
@@ -401,6 +430,8 @@ struct vrnerf_server {
     ServeCtl *ctl_h = nullptr, *ctl_d = nullptr;
     unsigned int *done_h = nullptr, *done_d = nullptr;
     unsigned int *cursor = nullptr;  // device: oldest view that may have slots left
+    unsigned long long *tile_stats_d = nullptr;  // device: tile rounds, rounds mixing requests
+    unsigned long long *tile_stats_h = nullptr;  // pinned copy, refreshed as requests finish
     unsigned char *arena_d = nullptr;
     Arena arena;
     cudaEvent_t kernel_done = nullptr;
@@ -416,6 +447,8 @@ struct vrnerf_server {
     std::map<uint64_t, Req *> by_ticket;
     std::vector<double> latencies_ms;
     uint64_t next_ticket = 1, rays_done = 0, completed = 0, launches = 0;
+    uint64_t max_inflight = 0;        // most requests on the GPU at once
+    unsigned int next_req = 0;        // request sequence numbers carried by the views
     Clock::time_point t_first;
     bool have_first = false;
     std::atomic<bool> quit{false};
@@ -456,6 +489,7 @@ bool vrnerf_server::admit_locked(std::vector<int> &new_views) {
             sv.W = q->res[2 * v];
             sv.H = q->res[2 * v + 1];
             sv.tiles_x = (sv.W + kTileW - 1) / kTileW;
+            sv.req = next_req;
             const unsigned long long slots =
                 (unsigned long long)sv.tiles_x * ((sv.H + kTileH - 1) / kTileH) * 32ull;
             sv.slot_begin = published;
@@ -474,6 +508,8 @@ bool vrnerf_server::admit_locked(std::vector<int> &new_views) {
             new_views.push_back(idx);
         }
         inflight.push_back(q);
+        if (inflight.size() > max_inflight) max_inflight = inflight.size();
+        ++next_req;
         any = true;
     }
     return any;
@@ -498,11 +534,11 @@ int vrnerf_server::ensure_kernel() {
     if (e == cudaSuccess) {
         const int fmt = prec == VRNERF_BF16 ? 1 : 0;
         if (F->view.L == 8)
-            e = fmt ? launch_serve_t<8, 1>(F, ring_d, ctl_d, cursor, idle_ns, kst)
-                    : launch_serve_t<8, 0>(F, ring_d, ctl_d, cursor, idle_ns, kst);
+            e = fmt ? launch_serve_t<8, 1>(F, ring_d, ctl_d, cursor, idle_ns, tile_stats_d, kst)
+                    : launch_serve_t<8, 0>(F, ring_d, ctl_d, cursor, idle_ns, tile_stats_d, kst);
         else
-            e = fmt ? launch_serve_t<16, 1>(F, ring_d, ctl_d, cursor, idle_ns, kst)
-                    : launch_serve_t<16, 0>(F, ring_d, ctl_d, cursor, idle_ns, kst);
+            e = fmt ? launch_serve_t<16, 1>(F, ring_d, ctl_d, cursor, idle_ns, tile_stats_d, kst)
+                    : launch_serve_t<16, 0>(F, ring_d, ctl_d, cursor, idle_ns, tile_stats_d, kst);
     }
     if (e == cudaSuccess) e = cudaEventRecord(kernel_done, kst);
     if (e != cudaSuccess) return cuda_fail(e, "serve kernel launch");
@@ -542,7 +578,12 @@ void vrnerf_server::poll_completions() {
         // the oldest view still referenced bounds ring reuse
         while (oldest_live_view < n_views && !view_req[oldest_live_view % kRing]) ++oldest_live_view;
     }
-    if (!finished.empty()) done_cv.notify_all();
+    if (!finished.empty()) {
+        // the kernel's tile counters, for vrnerf_server_stats
+        cudaMemcpyAsync(tile_stats_h, tile_stats_d, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, cst);
+        cudaStreamSynchronize(cst);
+        done_cv.notify_all();
+    }
 }
 
 void vrnerf_server::run() {
@@ -595,6 +636,9 @@ int vrnerf_server_create(vrnerf_field *F, uint64_t hbm_budget_bytes, int32_t pre
     if (e == cudaSuccess) e = cudaHostGetDevicePointer(&S->done_d, S->done_h, 0);
     if (e == cudaSuccess) e = cudaMalloc(&S->cursor, 2 * sizeof(unsigned int));  // cursor, idle state
     if (e == cudaSuccess) e = cudaMemset(S->cursor, 0, 2 * sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMalloc(&S->tile_stats_d, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(S->tile_stats_d, 0, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMallocHost(&S->tile_stats_h, 2 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&S->arena_d, hbm_budget_bytes);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->kernel_done, cudaEventDisableTiming);
     if (e != cudaSuccess) {
@@ -603,6 +647,7 @@ int vrnerf_server_create(vrnerf_field *F, uint64_t hbm_budget_bytes, int32_t pre
     }
     memset(S->ctl_h, 0, sizeof(ServeCtl));
     memset(S->done_h, 0, sizeof(unsigned int) * kRing);
+    memset(S->tile_stats_h, 0, 2 * sizeof(unsigned long long));
     S->arena.init(hbm_budget_bytes);
     S->worker = std::thread([S] { S->run(); });
     *out = S;
@@ -706,6 +751,9 @@ int vrnerf_server_stats(vrnerf_server *S, vrnerf_serve_stats *st) {
     st->kernel_launches = S->launches;
     st->pending = S->pending.size();
     st->inflight = S->inflight.size();
+    st->max_inflight = S->max_inflight;
+    st->tile_rounds = __atomic_load_n(&S->tile_stats_h[0], __ATOMIC_RELAXED);
+    st->mixed_tile_rounds = __atomic_load_n(&S->tile_stats_h[1], __ATOMIC_RELAXED);
     std::vector<double> l = S->latencies_ms;
     if (!l.empty()) {
         std::sort(l.begin(), l.end());
@@ -725,6 +773,7 @@ int vrnerf_server_reset_stats(vrnerf_server *S) {
     S->rays_done = 0;
     S->completed = 0;
     S->launches = 0;
+    S->max_inflight = S->inflight.size();
     S->have_first = false;
     return VRNERF_OK;
 }
@@ -746,6 +795,8 @@ void vrnerf_server_destroy(vrnerf_server *S) {
     if (S->kernel_done) cudaEventDestroy(S->kernel_done);
     if (S->arena_d) cudaFree(S->arena_d);
     if (S->cursor) cudaFree(S->cursor);
+    if (S->tile_stats_d) cudaFree(S->tile_stats_d);
+    if (S->tile_stats_h) cudaFreeHost(S->tile_stats_h);
     if (S->done_h) cudaFreeHost(S->done_h);
     if (S->ctl_h) cudaFreeHost(S->ctl_h);
     if (S->ring_h) cudaFreeHost(S->ring_h);

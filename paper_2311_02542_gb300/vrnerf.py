@@ -105,7 +105,9 @@ class ServerStats(ctypes.Structure):
     _fields_ = [("completed", ctypes.c_uint64), ("rays", ctypes.c_uint64),
                 ("kernel_launches", ctypes.c_uint64), ("pending", ctypes.c_uint64),
                 ("inflight", ctypes.c_uint64), ("p50_ms", ctypes.c_double),
-                ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double), ("wall_s", ctypes.c_double)]
+                ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double), ("wall_s", ctypes.c_double),
+                ("max_inflight", ctypes.c_uint64), ("tile_rounds", ctypes.c_uint64),
+                ("mixed_tile_rounds", ctypes.c_uint64)]
 
 _lib = None
 

@@ -313,3 +313,38 @@ def test_contracted_skip_stress_room(V, room):
     assert (gi == ri).all() and (gv == rv).all()
     assert cnt.sum() > 50000
     f.close()
+
+
+def test_contracted_history(V, unit):
+    """Training history of a contracted scene (Sec. 4.3.2, Sec. 4): after
+    backward passes of rays from inside the box and from 20 units outside,
+    every voxel of the contracted grid holds the largest composited opacity
+    the oracle records there (T_eps = 0, so both sides composite the same
+    samples)."""
+    cfg, occ, grid, mlp = unit
+    cfg = replace(cfg, T_eps=0.0)
+    bits = S.pack_bits(occ)
+    f = V.Field(cfg, grid, mlp, bits)
+    F = O.Field(cfg, grid, mlp, bits)
+    V.vrnerf_history_reset(f)
+    rng = np.random.default_rng(21)
+    c2w, K, res = S.camera_unit_cube(occ, cfg, 4, 24, 24)
+    o1, d1, r1 = O.camera_rays(cfg, c2w, K, res)
+    o2 = (0.5 + 20.0 * rng.normal(size=(400, 3))).astype(np.float32)
+    d2 = 0.5 + 0.3 * rng.normal(size=(400, 3)) - o2
+    d2 = (d2 / np.linalg.norm(d2, axis=1, keepdims=True)).astype(np.float32)
+    r2 = np.full(400, 1e-3, np.float32)
+    want = np.zeros(occ.size, np.float32)
+    for o, d, r in ((o1, d1, r1), (o2, d2, r2)):
+        tgt = np.full((o.shape[0], 3), 0.5, np.float32)
+        V.vrnerf_backward(f, _cuda(o), _cuda(d), _cuda(r), _cuda(tgt))
+        want = O.history(F, o, d, r, want)
+    got = V.vrnerf_field_get_history(f)
+    assert (want > 0).sum() > 200
+    # voxels beyond the box's image in the contracted grid are recorded too
+    outer = np.ones(occ.shape, bool)
+    outer[8:24, 8:24, 8:24] = False
+    assert (want.reshape(occ.shape)[outer] > 0).sum() > 50
+    err = np.abs(got.astype(np.float64) - want)
+    assert (err <= 1e-4 * want + 1e-6).all(), err.max()
+    f.close()

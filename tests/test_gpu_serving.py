@@ -1,13 +1,18 @@
 """Continuous-batching server: every request's image equals the same views
 rendered alone (vrnerf_render, same precision) within the tensor-core
-tolerance; admission by HBM budget; cancel, unknown tickets, timeouts; the
-persistent kernel leaves when idle and is relaunched for new work."""
+tolerance, and the fp64 oracle's render within 2e-3 |ref| + 1e-5 (rays whose
+early termination flips at T_eps, found from the alone render's sample
+counts, within T_eps + 1e-4 in PQ); requests overlap on the device (tiles
+whose MLP rows mix requests); admission by HBM budget; cancel, unknown
+tickets, timeouts; the persistent kernel leaves when idle and is relaunched
+for new work."""
 import time
 
 import numpy as np
 import pytest
 import torch
 
+import oracle as O
 from paper_2311_02542_gb300 import synth as S
 
 pytestmark = pytest.mark.gpu
@@ -30,6 +35,28 @@ def room():
 def _alone(V, f, c2w, K, res):
     return V.vrnerf_render(f, torch.from_numpy(c2w).cuda(), torch.from_numpy(K).cuda(), res,
                            precision="fp16").cpu().numpy()
+
+
+def _alone_n(V, f, c2w, K, res):
+    """Linear colour and per-ray sample counts of the fp16 render alone."""
+    rays = int((res[:, 0] * res[:, 1]).sum())
+    n = torch.empty(rays, device="cuda", dtype=torch.int32)
+    lin = V.vrnerf_render(f, torch.from_numpy(c2w).cuda(), torch.from_numpy(K).cuda(), res,
+                          precision="fp16", out_n=n)
+    return lin.cpu().numpy(), n.cpu().numpy()
+
+
+def _check_against_oracle(got_lin, n_gpu, ref, T_eps):
+    """Served linear colour against the oracle: fp16 tolerance, with the
+    rays whose sample count differs at T_eps held to T_eps in PQ."""
+    flip = n_gpu != ref["n"]
+    ok = np.abs(got_lin.astype(np.float64) - ref["linear"]) <= TC_RTOL * np.abs(ref["linear"]) + TC_ATOL
+    bad = ~ok.all(1) & ~flip
+    assert not bad.any(), (bad.sum(), np.abs(got_lin - ref["linear"])[bad].max())
+    if flip.any():
+        pq = np.array([[O.linear_to_pq(float(c)) for c in row] for row in got_lin[flip]])
+        assert np.abs(pq - ref["pq"][flip]).max() <= T_eps + 1e-4
+        assert flip.mean() <= 0.01
 
 
 def _mix(room, rng):
@@ -66,7 +93,43 @@ def test_serving_matches_rendering_alone(V, room):
         assert np.all(np.abs(got - ref) <= TC_RTOL * np.abs(ref) + TC_ATOL)
     st = srv.stats()
     assert st["completed"] == len(reqs) and st["p99_ms"] >= st["p50_ms"] > 0
+    # the requests shared the GPU: several were admitted at once, and MLP
+    # tiles held samples of more than one request
+    print(f"serving overlap: max in flight {st['max_inflight']}, tile rounds {st['tile_rounds']}, "
+          f"mixed {st['mixed_tile_rounds']}")
+    assert st["max_inflight"] >= 2
+    assert st["mixed_tile_rounds"] >= 1 and st["tile_rounds"] > st["mixed_tile_rounds"]
     srv.close()
+    V.vrnerf_field_status(f)
+    # every served image against the fp64 oracle
+    F = O.Field(room.cfg, room.grid, room.mlp, room.occ_bits)
+    for (c2w, K, res), got in zip(reqs, outs):
+        _, n_gpu = _alone_n(V, f, c2w, K, res)
+        _check_against_oracle(got, n_gpu, F.render(c2w, K, res), room.cfg.T_eps)
+    f.close()
+
+
+@pytest.mark.parametrize("variant", ["room", "room_surface"])
+def test_serving_stereo_2048_against_oracle(V, variant):
+    """One stereo pair of 2048^2 eye buffers (Sec. 5) through the server: 4 000
+    sampled pixels of each eye against the fp64 oracle."""
+    sc = S.make_scene(variant)
+    f = V.Field(sc.cfg, sc.grid, sc.mlp, sc.occ_bits)
+    pose, _, _ = S.camera_room(sc.occ, sc.cfg, 2, 2048, 2048)
+    c2w = S.stereo_pair(pose[0])
+    K = np.stack([S.intrinsics_fov(2048, 2048)] * 2)
+    res = np.array([[2048, 2048]] * 2, np.int32)
+    srv = V.Server(f, 256 << 20, "fp16")
+    out = np.full((2 * 2048 * 2048, 3), np.nan, np.float32)
+    srv.poll(srv.submit(c2w, K, res, out), 30000)
+    srv.close()
+    assert np.isfinite(out).all()
+    _, n_gpu = _alone_n(V, f, c2w, K, res)
+    o, d, r = O.camera_rays(sc.cfg, c2w, K, res)
+    pick = np.sort(np.random.default_rng(43).choice(o.shape[0], 8000, replace=False))
+    F = O.Field(sc.cfg, sc.grid, sc.mlp, sc.occ_bits)
+    ref = F.render_rays(o[pick], d[pick], r[pick])
+    _check_against_oracle(out[pick], n_gpu[pick], ref, sc.cfg.T_eps)
     V.vrnerf_field_status(f)
     f.close()
 

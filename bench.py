@@ -55,7 +55,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="auto")
-    ap.add_argument("--variant", default="room", choices=["room", "room_surface"])
+    ap.add_argument("--variant", default="room",
+                    choices=["room", "room_surface", "room_unbounded", "room_unbounded_surface"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--serving-requests", type=int, default=300,

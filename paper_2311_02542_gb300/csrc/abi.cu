@@ -106,6 +106,16 @@ void derive_view(const vrnerf_field_desc &d, FieldView &f, std::vector<float> &t
         if (ext > ext_max) ext_max = ext;
     }
     f.inv_ext = (float)(1.0 / ext_max);
+    // distance-field units: dstep[k] voxels along axis k, about the largest
+    // cell's size (1 on a contracted grid, whose cells are cubes)
+    double cell_max = 0.0;
+    for (int k = 0; k < 3; ++k)
+        cell_max = fmax(cell_max, ((double)d.aabb_max[k] - (double)d.aabb_min[k]) / d.occ_res[k]);
+    for (int k = 0; k < 3; ++k) {
+        const double cell = ((double)d.aabb_max[k] - (double)d.aabb_min[k]) / d.occ_res[k];
+        const int r = d.contract ? 1 : (int)floor(cell_max / cell + 1e-9);
+        f.dstep[k] = r < 1 ? 1 : (r > 64 ? 64 : r);
+    }
     f.contract = d.contract;
     for (int k = 0; k < 3; ++k) f.cen[k] = (float)(0.5 * ((double)d.aabb_min[k] + (double)d.aabb_max[k]));
     f.inv_h = (float)(2.0 / ext_max);

@@ -34,9 +34,13 @@ struct FieldView {
     float inv_ext;
     float two_s, inv_ln_f, lod_bias, T_eps, density_bias, radius_scale;
     int n_mlp;
-    // empty-space skipping: per voxel, the Chebyshev (L-infinity) distance in
-    // voxels to the nearest occupied voxel, saturated at kDistCap; 0 = occupied
+    // empty-space skipping: per voxel v, the distance d to the nearest occupied
+    // voxel u in the metric max_k ceil(|u_k - v_k| / dstep[k]) (an L-infinity
+    // distance that counts dstep[k] voxels as one unit along axis k, so that
+    // skip boxes of anisotropic cells reach about as far along every axis),
+    // saturated at kDistCap; 0 = occupied
     const uint8_t *dist;
+    int dstep[3];             // voxels per distance unit along each axis (>= 1)
     int skip;                 // 0: test every sample against the occupancy bits
     float skip_eps;           // margin (voxels) kept from the faces of an empty cube
     float ln_tn, inv_ln_q;    // ln t_near and S / ln(t_far / t_near)
@@ -198,11 +202,12 @@ __device__ __forceinline__ bool occupied(const uint32_t *__restrict__ occ, int v
 // The evaluated samples are defined per sample: sample i is evaluated iff its
 // fp32 position falls in an occupied voxel, and the march ends at the first
 // sample outside the grid. The skip never changes that set. A sample's voxel
-// v has distance d = dist[v] to the nearest occupied voxel (L-infinity, in
-// voxels), so every voxel u with max_k |u_k - v_k| <= d - 1 is empty: the
-// cube [v - (d-1), v + d) of grid coordinates (clipped to the grid) holds no
-// occupied voxel. The march shrinks that cube by skip_eps voxels on every
-// face and jumps to the first sample at or past the ray's exit from it.
+// v has distance d = dist[v] to the nearest occupied voxel, so every voxel u
+// with |u_k - v_k| <= (d - 1) dstep[k] on every axis is empty: the box
+// [v_k - (d-1) dstep[k], v_k + (d-1) dstep[k] + 1) of grid coordinates
+// (clipped to the grid) holds no occupied voxel. The march shrinks that box
+// by skip_eps voxels on every face and jumps to the first sample at or past
+// the ray's exit from it.
 // Every sample jumped over lies, exactly, at least skip_eps inside the cube;
 // skip_eps is far above the rounding error of the fp32 position and of the
 // exit distance (checked when the field is created), so each of those
@@ -270,7 +275,8 @@ __device__ __forceinline__ int march_next(const FieldView &f, const float *__res
             float D = INFINITY, mx = 0.0f, dinf = 0.0f;
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                const int lo_i = v[k] - (dv - 1), hi_i = v[k] + dv;
+                const int ext = (dv - 1) * f.dstep[k];
+                const int lo_i = v[k] - ext, hi_i = v[k] + ext + 1;
                 const float cu = 4.0f / f.res_f[k];  // contracted units per voxel
                 if (lo_i > 0) D = fminf(D, (gc[k] - ((float)lo_i + f.skip_eps)) * cu);
                 if (hi_i < f.res[k]) D = fminf(D, (((float)hi_i - f.skip_eps) - gc[k]) * cu);
@@ -291,7 +297,8 @@ __device__ __forceinline__ int march_next(const FieldView &f, const float *__res
         bool ok = true;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const int lo_i = max(v[k] - (dv - 1), 0), hi_i = min(v[k] + dv, f.res[k]);
+            const int ext = (dv - 1) * f.dstep[k];
+            const int lo_i = max(v[k] - ext, 0), hi_i = min(v[k] + ext + 1, f.res[k]);
             const float lo = (float)lo_i + f.skip_eps, hi = (float)hi_i - f.skip_eps;
             if (m.inv_s[k] != 0.0f) {
                 const float ta = (lo - m.g0[k]) * m.inv_s[k], tb = (hi - m.g0[k]) * m.inv_s[k];

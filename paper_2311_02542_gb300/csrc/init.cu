@@ -77,11 +77,13 @@ cudaError_t launch_seeded_mlp(float *mlp, const int (*shapes)[2], int n_mats, ui
     return cudaSuccess;
 }
 
-// Occupancy distance field: dist[v] = min(kDistCap, L-infinity distance in
-// voxels from v to the nearest occupied voxel), 0 for occupied voxels. After r
-// dilations of the occupancy by the 3x3x3 cube, a voxel is covered iff an
-// occupied voxel lies within distance r; its distance is the first r that
-// covers it. Each dilation is three separable 3-tap passes.
+// Occupancy distance field: dist[v] = min(kDistCap, d(v)), 0 for occupied
+// voxels, with d(v) the distance from v to the nearest occupied voxel u in
+// the metric max_k ceil(|u_k - v_k| / dstep[k]). After r dilations of the
+// occupancy by the box of half-extent dstep[k] voxels along axis k, a voxel
+// is covered iff an occupied voxel lies within distance r; its distance is
+// the first r that covers it. Each dilation is dstep[0] + dstep[1] + dstep[2]
+// separable 3-tap passes.
 __global__ void dist_init_kernel(const uint32_t *__restrict__ occ, long long n, uint8_t *__restrict__ mask,
                                  uint8_t *__restrict__ dist) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -120,11 +122,12 @@ cudaError_t launch_build_dist(const FieldView &f, uint8_t *dist, cudaStream_t st
     if (e == cudaSuccess) {
         dist_init_kernel<<<grid, 256, 0, st>>>(f.occ, n, a, dist);
         for (int r = 1; r < kDistCap && e == cudaSuccess; ++r) {
-            dilate_axis_kernel<<<grid, 256, 0, st>>>(a, b, rx, ry, rz, 0);
-            dilate_axis_kernel<<<grid, 256, 0, st>>>(b, a, rx, ry, rz, 1);
-            dilate_axis_kernel<<<grid, 256, 0, st>>>(a, b, rx, ry, rz, 2);
-            dist_assign_kernel<<<grid, 256, 0, st>>>(b, n, r, dist);
-            std::swap(a, b);
+            for (int k = 0; k < 3; ++k)
+                for (int j = 0; j < f.dstep[k]; ++j) {
+                    dilate_axis_kernel<<<grid, 256, 0, st>>>(a, b, rx, ry, rz, k);
+                    std::swap(a, b);  // a holds the dilated mask
+                }
+            dist_assign_kernel<<<grid, 256, 0, st>>>(a, n, r, dist);
             e = cudaGetLastError();
         }
     }

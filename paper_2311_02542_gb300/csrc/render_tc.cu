@@ -18,10 +18,27 @@
 // one 128 x 64 activation tile (16 KB, reused by every layer), the sample
 // distance table, an mbarrier. TMEM: 64 columns (every layer writes columns
 // 0 .. N-1 after the previous layer's values have been read).
+//
+// Look-ahead march (contracted scenes). The samples a ray evaluates do not
+// depend on compositing (only early termination cuts the list short), so a
+// lane may find its ray's next samples before the current one is shaded. The
+// warp marches one iteration at a time and stops once every lane has a
+// sample queued; lanes that already have one keep marching meanwhile and
+// queue up to kLookahead samples; a ray that terminates drops what it
+// queued. This pays where rays are long (an unbounded scene's far field:
+// tens of samples per ray), and costs more than it saves on the few samples
+// per ray of a bounded room, whose lanes march in chunks of kTcChunk
+// iterations and hold one sample.
 #include "field.h"
 #include "tc_mlp.cuh"
 
 namespace vrn {
+
+#ifndef VRN_LOOKAHEAD
+#define VRN_LOOKAHEAD 16
+#endif
+constexpr int kLookahead = VRN_LOOKAHEAD;  // samples a lane may hold found ahead of shading
+static_assert((kLookahead & (kLookahead - 1)) == 0, "the look-ahead queue is a power-of-two ring");
 
 template <int L, int FMT, bool CT>
 __global__ void __launch_bounds__(kTcThreads, kTcMinBlocks)
@@ -35,6 +52,7 @@ render_tc_kernel(const FieldView f, const RaySource src, const RenderOut out,
     const float *__restrict__ sT = f.t_tab;  // sample distances, read through L1
 
     constexpr unsigned FULL = 0xffffffffu;
+    constexpr int LA = CT ? kLookahead : 1;  // 1: no look-ahead (bounded scenes)
     const int lane = threadIdx.x & 31;
     long long ray = -1, pix = 0;
     bool exhausted = false, ok = true;
@@ -43,6 +61,9 @@ render_tc_kernel(const FieldView f, const RaySource src, const RenderOut out,
     float adj[CT ? 6 : 1];  // contracted scenes: offsets to the adjacent pixels' rays
     bool has_adj = false;
     int n_eval = 0;
+    int q[LA];              // look-ahead: ring of the step indices of the samples found ahead
+    int qh = 0, nq = 0;     // look-ahead: oldest entry, how many are queued
+    bool mend = false;      // look-ahead: the march of this ray has reached its end
     uint32_t phase = 0;
     unsigned st_samples = 0, st_levels = 0, st_steps = 0, st_rays = 0;
 
@@ -67,30 +88,63 @@ render_tc_kernel(const FieldView f, const RaySource src, const RenderOut out,
                         march_init(f, mr);
                         ray = slot;
                         n_eval = 0;
+                        qh = 0;
+                        nq = 0;
+                        mend = false;
                         T = 1.0f;
                         Dp = 0.0f;
                         C[0] = C[1] = C[2] = 0.0f;
                     }
                 }
             }
-            if (ray >= 0 && !have) {
-                const int mres = march_next(f, sT, mr, p, kTcChunk, st_steps);
-                if (mres == MARCH_SAMPLE) {
-                    have = true;
-                } else if (mres == MARCH_END) {
-                    finish_outputs(out, pix, C, T, n_eval, Dp, nullptr, f.check);
-                    ray = -1;
-                    ++st_rays;
+            if constexpr (LA == 1) {
+                if (ray >= 0 && !have) {
+                    const int mres = march_next(f, sT, mr, p, kTcChunk, st_steps);
+                    if (mres == MARCH_SAMPLE) {
+                        have = true;
+                    } else if (mres == MARCH_END) {
+                        finish_outputs(out, pix, C, T, n_eval, Dp, nullptr, f.check);
+                        ray = -1;
+                        ++st_rays;
+                    }
                 }
+                if (__all_sync(FULL, have || exhausted)) break;
+            } else {
+                for (int it = 0; it < kTcChunk; ++it) {
+                    if (!__any_sync(FULL, ray >= 0 && nq == 0)) break;  // every live lane has a sample
+                    if (ray >= 0 && !mend && nq < LA) {
+                        float pq[3];
+                        const int mres = march_next(f, sT, mr, pq, 1, st_steps);
+                        if (mres == MARCH_SAMPLE) {
+                            q[(qh + nq++) & (LA - 1)] = mr.step;
+                            ++mr.step;
+                        } else if (mres == MARCH_END) {
+                            mend = true;
+                            if (nq == 0) {
+                                finish_outputs(out, pix, C, T, n_eval, Dp, nullptr, f.check);
+                                ray = -1;
+                                ++st_rays;
+                            }
+                        }
+                    }
+                }
+                have = ray >= 0 && nq > 0;
+                if (__all_sync(FULL, have || exhausted)) break;
             }
-            if (__all_sync(FULL, have || exhausted)) break;
         }
         if (!__syncthreads_or(have) || *S.abort) break;
         // ---- features, tensor-core MLPs, compositing ----
         float t = 0.0f, delta = 0.0f;
         if (have) {
-            t = sT[mr.step];
-            delta = sT[mr.step + 1] - t;
+            int step = mr.step;
+            if constexpr (LA > 1) {
+                step = q[qh];
+                t = sT[step];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) p[k] = __fadd_rn(mr.o[k], __fmul_rn(t, mr.d[k]));  // as the march
+            }
+            t = sT[step];
+            delta = sT[step + 1] - t;
             float r_norm;
             if constexpr (CT)
                 r_norm = footprint(f, t, r, p, has_adj ? adj : nullptr, has_adj ? adj + 3 : nullptr);
@@ -115,8 +169,15 @@ render_tc_kernel(const FieldView f, const RaySource src, const RenderOut out,
             Dp += w * t;
             T *= expf(-sd);
             ++n_eval;
-            ++mr.step;
-            if (T < f.T_eps) {
+            bool done = T < f.T_eps;
+            if constexpr (LA == 1) {
+                ++mr.step;
+            } else {
+                qh = (qh + 1) & (LA - 1);
+                --nq;
+                done = done || (nq == 0 && mend);
+            }
+            if (done) {
                 finish_outputs(out, pix, C, T, n_eval, Dp, nullptr, f.check);
                 ray = -1;
                 ++st_rays;

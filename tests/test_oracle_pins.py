@@ -89,7 +89,8 @@ def test_lod_level_closed_form():
 
 def test_level_resolutions_and_dense_rule():
     rows = {(r[0], r[1]): [int(x) for x in r[2:]] for r in _rows("level_res.txt")}
-    for name, cfg in (("unit_cube", S.cfg_unit_cube()), ("room", S.cfg_room())):
+    for name, cfg in (("unit_cube", S.cfg_unit_cube()), ("room", S.cfg_room()),
+                      ("room_paper_grid", S.cfg_room_paper_grid())):
         N, dense, _, _ = O.geometry(cfg)
         assert list(N) == rows[(name, "N")]
         assert list(dense.astype(int)) == rows[(name, "dense")]
@@ -432,6 +433,9 @@ def test_march_single_voxel_brute_force():
 # Backward (central finite differences, fp64) and Adam (closed form)
 # ----------------------------------------------------------------------------
 def test_backward_matches_finite_differences():
+    """Central differences (fp64, step 1e-6) of the L1 loss on 1 000 randomly
+    chosen parameters, 300 hash-grid entries touched by the batch and 700
+    MLP weights, the count the training configuration names."""
     cfg = replace(S.cfg_unit_cube(), levels=4, log2_T=9, occ_res=(16, 16, 16), max_steps=48,
                   T_eps=0.0)
     rng = np.random.default_rng(6)
@@ -452,8 +456,9 @@ def test_backward_matches_finite_differences():
 
     h = 1e-6
     touched = np.nonzero(gg.reshape(-1))[0]
-    picks = [("g", i) for i in rng.choice(touched, 60, replace=False)]
-    picks += [("m", i) for i in rng.choice(mlp.size, 140, replace=False)]
+    assert touched.size >= 300
+    picks = [("g", i) for i in rng.choice(touched, 300, replace=False)]
+    picks += [("m", i) for i in rng.choice(mlp.size, 700, replace=False)]
     bad = 0
     for kind, i in picks:
         g2, m2 = grid.reshape(-1).copy(), mlp.copy()
@@ -466,6 +471,7 @@ def test_backward_matches_finite_differences():
         an = (gg.reshape(-1) if kind == "g" else gm)[i]
         if abs(fd - an) > 1e-7 + 1e-4 * abs(an):
             bad += 1
+    print("finite differences on", len(picks), "parameters:", bad, "outside the bound")
     assert bad <= 2, bad  # at most a ReLU kink crossed by the finite step
 
 

@@ -37,6 +37,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "room_2048x2048_single_eye"
+STEREO_BUDGET_MS = 1000.0 / 36.0  # one frame at the 36 Hz the paper's demo sustains
 
 
 # DRAM bytes read + written by one 2048x2048 launch of render_tc_kernel<16, 0, 0>
@@ -168,6 +169,21 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# Keys printed last, in this order: a reader that keeps only the end of the
+# line still sees the measurement record and the headline comparisons
+# (stereo latency, tuned against plain fp32, the precision sweep).
+TAIL_KEYS = ("work", "roofline", "e2e", "cpu_baseline", "clocks", "gpu_launches", "wall_s_timed",
+             "serving_summary", "precision_sweep", "plain_fp32", "stereo_2x2048")
+
+
+def tail_order(line):
+    """The bench line with the bulky extras (serving runs, training steps,
+    other workloads) first and TAIL_KEYS last."""
+    head = {k: v for k, v in line.items() if k not in TAIL_KEYS}
+    head.update({k: line[k] for k in TAIL_KEYS if k in line})
+    return head
+
+
 def pick_precision(V, arg):
     if arg != "auto":
         return V.PRECISIONS[arg]
@@ -279,7 +295,9 @@ def serving_bench(V, field, sc, n_req, warm=30, rate_hz=36.0 / 0.7, seed=4, in_f
             srv.reset_stats()
             t_meas = time.perf_counter()
         b = free.get()
-        done.put((i, srv.submit(r.c2w, r.intrinsics, r.resolution, bufs[b][:r.rays]), b))
+        # stereo frames are due within one 36 Hz frame time; single views carry no deadline
+        dl = STEREO_BUDGET_MS if r.stereo else None
+        done.put((i, srv.submit(r.c2w, r.intrinsics, r.resolution, bufs[b][:r.rays], deadline_ms=dl), b))
     done.put(None)
     th.join()
     wall = time.perf_counter() - t_meas
@@ -294,9 +312,16 @@ def serving_bench(V, field, sc, n_req, warm=30, rate_hz=36.0 / 0.7, seed=4, in_f
             "stereo_p99_ms": round(float(np.percentile(st_lat, 99)), 3),
             "all_p50_ms": round(float(np.percentile(all_lat, 50)), 3),
             "all_p99_ms": round(float(np.percentile(all_lat, 99)), 3),
+            "stereo_within_budget": round(float(np.mean(st_lat <= STEREO_BUDGET_MS)), 4),
+            "late_stereo": int(st["late"]),
+            "stage_ms": {k: round(float(st[k]), 3) for k in ("wait_p50_ms", "wait_p99_ms", "gpu_p50_ms",
+                                                               "gpu_p99_ms", "copy_p50_ms", "copy_p99_ms")},
             "Mrays_s": round(rays / wall / 1e6, 2), "wall_s": round(wall, 2),
             "kernel_launches": int(st["kernel_launches"]),
-            "note": "latency = submit to image in pinned host memory; fp16 tensor-core MLP"}
+            "overlap": {"max_inflight": int(st["max_inflight"]), "mixed_tile_frac":
+                        round(st["mixed_tile_rounds"] / max(st["tile_rounds"], 1), 4)},
+            "note": ("latency = submit to image in pinned host memory; fp16 tensor-core MLP; stereo "
+                     f"requests admitted earliest-deadline-first with a {STEREO_BUDGET_MS:.1f} ms deadline")}
 
 
 def train_bench(V, sc, steps, batch=1 << 20, precision="fp32"):
@@ -619,6 +644,10 @@ def main():
             direct_ms += a.elapsed_time(b)
             direct_rays += nr
         line["serving_saturated"]["direct_render_Mrays_s"] = round(direct_rays / (direct_ms * 1e-3) / 1e6, 2)
+        line["serving_summary"] = {
+            k: {"stereo_p50_ms": line[k]["stereo_p50_ms"], "stereo_p99_ms": line[k]["stereo_p99_ms"],
+                "Mrays_s": line[k]["Mrays_s"]} for k in ("serving", "serving_surface_variant")}
+        line["serving_summary"]["budget_ms"] = round(STEREO_BUDGET_MS, 2)
     if args.train_steps > 0:
         line["train_step"] = train_bench(V, sc, args.train_steps)
         # the paper's batch: 12 800 rays (256 rays from each of 50 images)
@@ -659,7 +688,7 @@ def main():
         line["cpu_baseline"]["gpu_psnr_pq_vs_oracle_db"] = psnr
         line["cpu_baseline"]["psnr_sample"] = "256x256 window at (896, 896) of the frame, PQ peak 1.0"
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        print(json.dumps(tail_order(line)), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0

@@ -63,6 +63,7 @@ extern "C" {
 #define VRNERF_ENOTFOUND (-6) /* unknown ticket */
 #define VRNERF_ECANCELED (-7) /* request was cancelled */
 #define VRNERF_ECHECK (-8)    /* a bounds check of the checked build failed */
+#define VRNERF_ELATE (-9)     /* request shed: its deadline passed before it reached the GPU */
 
 /* Arithmetic of the MLP. Hash features, transmittance and PQ are always fp32. */
 #define VRNERF_FP32 0 /* plain fp32 on the CUDA cores */
@@ -263,6 +264,18 @@ int vrnerf_backward_from_grad(vrnerf_field *field, const float *rays_o, const fl
                               const float *radii, int32_t B, const int32_t *n_fwd,
                               const float *grad_pq, void *stream);
 
+/* Most samples one pass of the training pipeline (vrnerf_backward,
+ * vrnerf_train_step, vrnerf_forward_rays, vrnerf_backward_from_grad) holds
+ * at once; 0 restores the default (2^26). The pipeline keeps per-sample
+ * buffers on the device: 152 bytes per evaluated sample, 216 with the bf16
+ * training precision. A batch with more samples than the budget, or whose
+ * buffers cannot be allocated, is processed in ray ranges that fit, one
+ * after the other, with gradients, loss and history accumulated over them:
+ * the same result as one pass up to the order of float additions. ENOMEM
+ * only when a single ray's samples do not fit. No counterpart in the paper
+ * (Sec. 6 trains on 12 800 rays per step). EINVAL for a NULL field. */
+int vrnerf_field_set_sample_budget(vrnerf_field *field, uint64_t max_samples);
+
 /* Arithmetic of the MLPs in training (Sec. 6, A9): VRNERF_FP32 (default;
  * CUDA cores, gradients within 1e-4 of the fp64 reference) or VRNERF_BF16
  * (tcgen05 tensor cores for the per-sample forward and backward: bf16
@@ -390,6 +403,11 @@ typedef struct {
     uint64_t mixed_tile_rounds; /* of those, tiles whose rows held samples of two or more
                                    requests: work of different requests overlapping on the
                                    device, in the same tensor-core MMAs */
+    uint64_t late;             /* requests with a deadline that finished after it */
+    uint64_t shed;             /* requests dropped because their deadline passed first */
+    double wait_p50_ms, wait_p99_ms; /* submit to admission (queueing for budget or ring) */
+    double gpu_p50_ms, gpu_p99_ms;   /* admission to every ray rendered */
+    double copy_p50_ms, copy_p99_ms; /* rendered to output in host memory */
 } vrnerf_serve_stats;
 
 /* Serving (Sec. 5: real-time rendering of stereo eye buffers, here as
@@ -412,10 +430,23 @@ int vrnerf_submit(vrnerf_server *server, int32_t n_views, const float *cameras_h
                   const float *intrinsics_host, const int32_t *resolution_host, float *out_host,
                   uint64_t *ticket);
 
+/* vrnerf_submit with a deadline (Sec. 6.2 paces stereo frames at 36 Hz and
+ * reports p99 frame rates): the request is due deadline_ms after submission
+ * (0: no deadline). Waiting requests are admitted earliest deadline first;
+ * requests without one follow in arrival order. With shed_if_late != 0 a
+ * request still waiting when its deadline passes is dropped (vrnerf_poll
+ * returns VRNERF_ELATE); otherwise it runs and, if it finishes after its
+ * deadline, counts as late in vrnerf_serve_stats. EINVAL, EBUSY as
+ * vrnerf_submit. */
+int vrnerf_submit_deadline(vrnerf_server *server, int32_t n_views, const float *cameras_host,
+                           const float *intrinsics_host, const int32_t *resolution_host, float *out_host,
+                           double deadline_ms, int32_t shed_if_late, uint64_t *ticket);
+
 /* Waits up to timeout_ms for the request; VRNERF_OK when its output is in
  * out_host (the ticket is then released; *latency_ms, if non-NULL, gets the
  * submit-to-done time), ETIMEDOUT if not yet done, ECANCELED if it was
- * cancelled (ticket released), ENOTFOUND for an unknown ticket. */
+ * cancelled (ticket released), ELATE if it was shed (ticket released),
+ * ENOTFOUND for an unknown ticket. */
 int vrnerf_poll(vrnerf_server *server, uint64_t ticket, int32_t timeout_ms, double *latency_ms);
 
 /* Cancels a request: a waiting request is dropped, a running one finishes on
@@ -435,14 +466,22 @@ void vrnerf_server_destroy(vrnerf_server *server);
  * compositor's frame callback, where an allocation could stall the frame,
  * or a plug-in whose host application owns every device allocation.
  * The caller passes the field's parameters in device buffers it owns, in the
- * layouts above: grid [L][T][F], mlp W1..W5, occ_bits; cameras, intrinsics
- * and out as in vrnerf_render (device), resolution_host on the host. The
- * kernel's scratch (ray-slot counter and sample-distance table) lives in one
- * 32 KiB static device array that every GPU loading the library keeps until
- * the process exits; its address is looked up on the first call made on
- * each device (make that call outside stream capture). max_steps above 8127
- * is rejected with EINVAL. Calls share the scratch: calls whose work
- * overlaps on the GPU race, so order them on one stream. EINVAL, ECUDA. */
+ * layouts above, of exactly these sizes (the library sees only pointers and
+ * cannot check them): grid L * 2^log2_T * F elements, fp16 when feat_fp16
+ * else fp32; mlp 64 L F + 16*64 + 64*32 + 64*64 + 3*64 fp32 weights;
+ * occ_bits ceil(rx ry rz / 32) words; cameras [n][3][4], intrinsics [n][4]
+ * and out [sum W*H][3] as in vrnerf_render (device), resolution_host on the
+ * host. With no distance field (it would need device memory of its own) the
+ * march tests every sample against the occupancy bits instead of skipping
+ * empty space: the same result as vrnerf_render, with more march work on
+ * sparse scenes. The kernel's scratch (ray-slot counter and sample-distance
+ * table) lives in one 32 KiB static device array that every GPU loading the
+ * library keeps until the process exits; its address is looked up on the
+ * first call made on each device (make that call outside stream capture),
+ * and the table is copied in again only when t_near, t_far or max_steps
+ * differ from the previous call on that device. max_steps above 8127 is
+ * rejected with EINVAL. Calls share the scratch: calls whose work overlaps on
+ * the GPU race, so order them on one stream. EINVAL, ECUDA. */
 int vrnerf_render_noalloc(const vrnerf_field_desc *desc, const void *grid, const float *mlp,
                           const uint32_t *occ_bits, const float *cameras, const float *intrinsics,
                           const int32_t *resolution_host, int32_t n, float *out, void *stream);

@@ -78,7 +78,7 @@ int check_desc(const vrnerf_field_desc *d) {
     return VRNERF_OK;
 }
 
-void derive_view(const vrnerf_field_desc &d, FieldView &f, std::vector<float> &t_tab) {
+void derive_geometry(const vrnerf_field_desc &d, FieldView &f) {
     memset(&f, 0, sizeof f);
     f.L = d.levels;
     f.F = d.feats;
@@ -148,11 +148,19 @@ void derive_view(const vrnerf_field_desc &d, FieldView &f, std::vector<float> &t
     }
     f.ln_tn = logf(d.t_near);
     f.inv_ln_q = (float)((double)d.max_steps / log((double)d.t_far / (double)d.t_near));
+}
+
+void fill_sample_table(const vrnerf_field_desc &d, float *t_tab) {
     // exponential sample distances t_i = t_near (t_far / t_near)^(i / S), fp64 -> fp32
-    t_tab.resize(d.max_steps + 1);
     const double tn = d.t_near, tf = d.t_far;
     for (int i = 0; i <= d.max_steps; ++i)
         t_tab[i] = (float)(tn * pow(tf / tn, (double)i / (double)d.max_steps));
+}
+
+void derive_view(const vrnerf_field_desc &d, FieldView &f, std::vector<float> &t_tab) {
+    derive_geometry(d, f);
+    t_tab.resize(d.max_steps + 1);
+    fill_sample_table(d, t_tab.data());
 }
 
 uint64_t grid_bytes(const vrnerf_field_desc &d) {

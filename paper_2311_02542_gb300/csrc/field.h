@@ -30,6 +30,7 @@ struct vrnerf_field {
     void *tcb_w = nullptr;
     uint64_t tcb_version = 0;
     int train_prec = VRNERF_FP32;
+    uint64_t sample_budget = 0;     // samples per pass of the training pipeline (0: default)
     // training state
     float *grid_grad = nullptr, *mlp_grad = nullptr;
     float *grid_master = nullptr;  // fp32 master copy when the grid is stored in fp16
@@ -54,6 +55,11 @@ uint64_t grid_bytes(const vrnerf_field_desc &d);
 uint64_t grid_entries(const vrnerf_field_desc &d);
 uint64_t occ_words(const vrnerf_field_desc &d);
 int check_desc(const vrnerf_field_desc *d);
+// The field geometry a description implies (levels, grids, skip settings),
+// the table of sample distances t_0..t_S written to any array of S + 1
+// floats, and both together.
+void derive_geometry(const vrnerf_field_desc &d, FieldView &f);
+void fill_sample_table(const vrnerf_field_desc &d, float *t_tab);
 void derive_view(const vrnerf_field_desc &d, FieldView &f, std::vector<float> &t_tab);
 void release_train_scratch(vrnerf_field *F);
 

@@ -18,9 +18,15 @@
 // call outside any CUDA stream capture.
 //
 // All calls share the array and it keeps what the last call left in it, so
-// the counter is cleared on every call. Calls whose work overlaps on the GPU
-// (on different streams, or from different host threads) race on it: order
-// them on one stream or synchronise in between.
+// the counter is cleared on every call; the sample-distance table is copied
+// in only when t_near, t_far or max_steps differ from the last call on the
+// device. Calls whose work overlaps on the GPU (on different streams, or from
+// different host threads) race on it: order them on one stream or
+// synchronise in between.
+//
+// With no distance field (it would need memory of its own) the march tests
+// every sample against the occupancy bits instead of skipping empty space,
+// which costs more march work than vrnerf_render on sparse scenes.
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -60,48 +66,14 @@ int scratch_address(int dev, unsigned char **out) {
     return VRNERF_OK;
 }
 
-// The field geometry of a description, with the sample-distance table
-// written to a caller-provided array (no heap use).
-void derive_view_fixed(const vrnerf_field_desc &d, FieldView &f, float *t_tab) {
-    memset(&f, 0, sizeof f);
-    f.L = d.levels;
-    f.F = d.feats;
-    f.d_in = d.levels * d.feats;
-    f.log2_T = d.log2_T;
-    f.T_mask = (1u << d.log2_T) - 1u;
-    f.feat_fp16 = d.feat_fp16 ? 1 : 0;
-    f.S = d.max_steps;
-    const long long T = 1ll << d.log2_T;
-    for (int l = 0; l < d.levels; ++l) {
-        const int N = (int)floor(d.base_res * pow(d.growth, (double)l) + 1e-6);
-        f.N[l] = N;
-        const long long n1 = (long long)N + 1;
-        if (n1 * n1 * n1 <= T) f.dense_mask |= 1u << l;
-    }
-    double ext_max = 0.0;
-    for (int k = 0; k < 3; ++k) {
-        const double ext = (double)d.aabb_max[k] - (double)d.aabb_min[k];
-        f.mn[k] = d.aabb_min[k];
-        f.inv_cell[k] = (float)((double)d.occ_res[k] / ext);
-        f.res[k] = d.occ_res[k];
-        f.res_f[k] = (float)d.occ_res[k];
-        if (ext > ext_max) ext_max = ext;
-    }
-    f.inv_ext = (float)(1.0 / ext_max);
-    f.contract = d.contract;
-    for (int k = 0; k < 3; ++k) f.cen[k] = (float)(0.5 * ((double)d.aabb_min[k] + (double)d.aabb_max[k]));
-    f.inv_h = (float)(2.0 / ext_max);
-    f.two_s = (float)(2.0 * d.base_res);
-    f.inv_ln_f = (float)(1.0 / log(d.growth));
-    f.lod_bias = d.lod_bias;
-    f.T_eps = d.T_eps;
-    f.density_bias = d.density_bias;
-    f.radius_scale = d.radius_scale;
-    f.n_mlp = 64 * f.d_in + 16 * 64 + 64 * 32 + 64 * 64 + 3 * 64;
-    const double tn = d.t_near, tf = d.t_far;
-    for (int i = 0; i <= d.max_steps; ++i)
-        t_tab[i] = (float)(tn * pow(tf / tn, (double)i / (double)d.max_steps));
-}
+// Key of the sample-distance table last uploaded to each device's scratch:
+// the table is copied again only when t_near, t_far or max_steps change.
+struct TableKey {
+    bool valid = false;
+    float t_near = 0.0f, t_far = 0.0f;
+    int max_steps = 0;
+};
+TableKey g_table_key[kMaxDevices];
 
 }  // namespace
 }  // namespace vrn
@@ -130,9 +102,12 @@ extern "C" int vrnerf_render_noalloc(const vrnerf_field_desc *desc, const void *
         unsigned char *scratch = nullptr;
         if ((rc = scratch_address(dev, &scratch))) return rc;
 
-        float t_host[kMaxSteps + 1];
         FieldView view;
-        derive_view_fixed(*desc, view, t_host);
+        derive_geometry(*desc, view);
+        // No distance field exists here (building one would need its own
+        // device memory): every sample is tested against the occupancy bits.
+        view.skip = 0;
+        view.dist = nullptr;
         float *t_dev = reinterpret_cast<float *>(scratch + kCounterBytes);
         unsigned long long *counter = reinterpret_cast<unsigned long long *>(scratch);
         view.grid = grid;
@@ -141,9 +116,22 @@ extern "C" int vrnerf_render_noalloc(const vrnerf_field_desc *desc, const void *
         view.t_tab = t_dev;
 
         cudaStream_t st = (cudaStream_t)stream;
-        // pageable source: the call returns once t_host has been staged
-        e = cudaMemcpyAsync(t_dev, t_host, sizeof(float) * (desc->max_steps + 1),
-                            cudaMemcpyHostToDevice, st);
+        {
+            std::lock_guard<std::mutex> lock(g_setup_mutex);
+            TableKey &key = g_table_key[dev];
+            if (!key.valid || key.t_near != desc->t_near || key.t_far != desc->t_far ||
+                key.max_steps != desc->max_steps) {
+                float t_host[kMaxSteps + 1];
+                fill_sample_table(*desc, t_host);
+                // pageable source: the call returns once t_host has been staged
+                e = cudaMemcpyAsync(t_dev, t_host, sizeof(float) * (desc->max_steps + 1),
+                                    cudaMemcpyHostToDevice, st);
+                key.valid = e == cudaSuccess;
+                key.t_near = desc->t_near;
+                key.t_far = desc->t_far;
+                key.max_steps = desc->max_steps;
+            }
+        }
         if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, 2 * sizeof(unsigned long long), st);
         view.check = counter + 1;  // bounds-check bits of checked builds (not reported by this entry)
         if (e != cudaSuccess) return cuda_fail(e, "render_noalloc: scratch set-up");

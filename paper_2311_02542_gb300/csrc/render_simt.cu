@@ -13,6 +13,8 @@
 //     (Eq. 1-2).
 // Phase 2 runs with the warp converged, so the MLP's FMAs are not serialised
 // against the march.
+#include <mutex>
+
 #include "internal.h"
 #include "simt_mlp.cuh"
 
@@ -310,18 +312,35 @@ size_t simt_smem_bytes(const FieldView &f) {
 template <int L, bool NRM, bool CT>
 static cudaError_t render_simt_t(const FieldView &f, const RaySource &src, const RenderOut &out,
                                  unsigned long long *counter, cudaStream_t st) {
-    static int blocks_per_sm = 0;
-    static size_t configured_smem = 0;
+    // launch shape cached per device: the shared-memory attribute is a
+    // per-device setting, and host threads may render on different devices
+    constexpr int kDevices = 64;
+    static std::mutex mu;
+    static size_t configured_smem[kDevices] = {};
+    static int cached_blocks[kDevices] = {};
     const size_t smem = simt_smem_bytes(f);
     auto kern = render_simt_kernel<L, NRM, CT>;
-    if (smem != configured_smem) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    int blocks_per_sm = 0;
+    if (dev >= 0 && dev < kDevices) {
+        std::lock_guard<std::mutex> lock(mu);
+        if (configured_smem[dev] != smem) {
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cached_blocks[dev], kern, kSimtThreads, smem);
+            if (e != cudaSuccess) return e;
+            configured_smem[dev] = smem;
+        }
+        blocks_per_sm = cached_blocks[dev];
+    } else {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, kSimtThreads, smem);
         if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, kSimtThreads, smem);
-        if (e != cudaSuccess) return e;
-        if (blocks_per_sm < 1) blocks_per_sm = 1;
-        configured_smem = smem;
     }
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
     long long want = (src.n_slots + kSimtThreads - 1) / kSimtThreads;
     long long grid = (long long)num_sms() * blocks_per_sm;
     if (want < grid) grid = want;

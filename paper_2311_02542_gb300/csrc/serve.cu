@@ -5,26 +5,30 @@
 // and single-view requests of mixed resolution is served by ONE persistent
 // tensor-core render kernel that keeps the field resident and takes work as
 // it arrives:
-//  - the host scheduler admits a request when its output fits in the HBM
-//    budget (a pre-allocated arena) and the view ring has room, writes its
-//    views (camera, intrinsics, resolution, output slice) into a ring in
-//    device memory and publishes the total number of ray slots in a control
-//    block in host-mapped memory;
+//  - the host scheduler admits waiting requests earliest deadline first
+//    (requests without a deadline in arrival order) when the output fits in
+//    the HBM budget (a pre-allocated arena) and the view ring has room,
+//    copies its views (camera, intrinsics, resolution, output slice) into a
+//    ring in device memory and then the number of published views into a
+//    control block in device memory, in stream order;
 //  - the kernel's warps take ray slots by fetch-and-add on the slot counter of
 //    the oldest published view that still has slots (a monotonic view cursor
 //    skips exhausted views; overshoot on an exhausted view is ignored). Rays
 //    of different requests share 128-row MLP tiles, so requests that arrive
 //    while others are on the GPU overlap with them on the device;
 //  - every thread counts the slots it finished per view and adds them to
-//    that view's counter in host-mapped memory after a system-scope fence,
-//    so the host sees a view complete only after its output is written; the
-//    host then copies the output slice to the request's buffer;
+//    that view's counter in device memory after a fence; the thread that
+//    completes the view raises the view's flag in host-mapped memory after a
+//    system-scope fence, so the host sees a view complete only after its
+//    output is written; the host then copies the output slice to the
+//    request's buffer;
 //  - when a CTA has no rays and nothing is published, it polls with
 //    __nanosleep; the launch leaves as a whole once every CTA has been idle
 //    past a time limit (or on stop), and the host relaunches the kernel when
 //    new work arrives and none is running.
 // No device-side wait is unbounded.
 #include <algorithm>
+#include <cstddef>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -53,7 +57,28 @@ struct __align__(16) ServeView {
     unsigned long long finished;  // slots finished (device counter)
 };
 
-struct ServeCtl {                  // host-mapped
+// A warp's copy of the view it last took slots from (the first 104 bytes
+// of ServeView: pose, intrinsics, sizes, request, slot range, output), keyed
+// by the view's sequence number, so that refills from the same view read
+// shared memory instead of the ring in global memory.
+struct __align__(16) ViewCache {
+    unsigned int words[26];
+    unsigned int seq;  // view sequence number held (0xffffffff: none)
+    unsigned int pad;
+};
+
+static_assert(offsetof(ServeView, W) == 64 && offsetof(ServeView, H) == 68 && offsetof(ServeView, tiles_x) == 72 &&
+                  offsetof(ServeView, req) == 76 && offsetof(ServeView, out) == 96,
+              "ViewCache word indices follow the ServeView layout");
+
+struct __align__(16) ServeShared {
+    int quit;
+    unsigned int rmin, rmax, pad;
+    ViewCache vc[kTcThreads / 32];
+};
+constexpr size_t kServeSharedBytes = (sizeof(ServeShared) + 15) & ~(size_t)15;
+
+struct ServeCtl {                  // device memory, written by the host's copies
     unsigned long long published;  // ray slots published so far (statistics)
     unsigned int n_views;          // views published so far
     int stop;
@@ -67,6 +92,16 @@ __device__ __forceinline__ unsigned long long ld_acquire_sys_u64(const unsigned 
 __device__ __forceinline__ unsigned int ld_acquire_sys_u32(const unsigned int *p) {
     unsigned int v;
     asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned int ld_acquire_gpu_u32(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_acquire_gpu_s32(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
 __device__ __forceinline__ int ld_acquire_sys_s32(const int *p) {
@@ -92,9 +127,16 @@ serve_kernel(const FieldView f, ServeView *__restrict__ ring, const ServeCtl *__
     float *unused;
     const TcShared S = tc_setup<D, FMT>(smem, wimg, unused, nullptr, 0);
     const float *__restrict__ sT = f.t_tab;  // sample distances, read through L1
-    __shared__ int s_quit;
+    // the serving kernel's own shared variables sit in the dynamic allocation
+    // after the tensor-core carve-up (static shared memory would be padded to
+    // the dynamic region's 1 KB alignment and cost a resident CTA per SM)
+    ServeShared &SS = *reinterpret_cast<ServeShared *>(reinterpret_cast<unsigned char *>(S.mbar) + 64);
+    int &s_quit = SS.quit;
     // smallest and largest request number among the rows of this tile round
-    __shared__ unsigned int s_rmin, s_rmax;
+    unsigned int &s_rmin = SS.rmin, &s_rmax = SS.rmax;
+    ViewCache &vc = SS.vc[threadIdx.x >> 5];
+    if ((threadIdx.x & 31) == 0) vc.seq = 0xffffffffu;
+    __syncwarp();
     if (threadIdx.x == 0) {
         s_rmin = 0xffffffffu;
         s_rmax = 0u;
@@ -154,20 +196,24 @@ serve_kernel(const FieldView f, ServeView *__restrict__ ring, const ServeCtl *__
                 const int leader = __ffs(m) - 1;
                 unsigned long long base = 0, got = 0;
                 int v = -1;
+                unsigned int vseq = 0;
                 if (lane == leader) {
                     // take up to popc(m) slots from the oldest view that has any left
                     unsigned int c = atomicAdd(cursor, 0u);
-                    if (c >= nv_seen) nv_seen = ld_acquire_sys_u32(&ctl->n_views);
+                    if (c >= nv_seen) nv_seen = ld_acquire_gpu_u32(&ctl->n_views);
                     const unsigned int nv = nv_seen;
                     for (int tries = 0; tries < 2 * kRing && c < nv; ++tries) {
                         ServeView *sv = ring + (c % kRing);
                         const unsigned long long total =
-                            (unsigned long long)__ldcg(&sv->tiles_x) * ((__ldcg(&sv->H) + kTileH - 1) / kTileH) * 32ull;
+                            c == vc.seq ? (unsigned long long)vc.words[18] * ((vc.words[17] + kTileH - 1) / kTileH) * 32ull
+                                        : (unsigned long long)__ldcg(&sv->tiles_x) *
+                                              ((__ldcg(&sv->H) + kTileH - 1) / kTileH) * 32ull;
                         const unsigned long long start = atomicAdd(&sv->taken, (unsigned long long)__popc(m));
                         if (start < total) {
                             base = start;
                             got = min((unsigned long long)__popc(m), total - start);
                             v = (int)(c % kRing);
+                            vseq = c;
                             break;
                         }
                         atomicMax(cursor, c + 1);
@@ -177,33 +223,27 @@ serve_kernel(const FieldView f, ServeView *__restrict__ ring, const ServeCtl *__
                 base = __shfl_sync(FULL, base, leader);
                 got = __shfl_sync(FULL, got, leader);
                 v = __shfl_sync(FULL, v, leader);
+                vseq = __shfl_sync(FULL, vseq, leader);
+                if (v >= 0 && vseq != vc.seq) {  // another view: load its descriptor once for the warp
+                    __syncwarp();
+                    if (lane < 26) vc.words[lane] = __ldcg(reinterpret_cast<const unsigned int *>(ring + v) + lane);
+                    __syncwarp();
+                    if (lane == 0) vc.seq = vseq;
+                    __syncwarp();
+                }
                 if (need) {
                     const unsigned rank = __popc(m & ((1u << lane) - 1u));
                     if (rank >= got) {
                         starved = true;
                     } else {
-                        const ServeView *sv = ring + v;
                         const int q = (int)(base + rank);
-                        const int W = __ldcg(&sv->W), H = __ldcg(&sv->H), tx = __ldcg(&sv->tiles_x);
+                        const float *cw = reinterpret_cast<const float *>(vc.words);
+                        const int W = (int)vc.words[16], H = (int)vc.words[17], tx = (int)vc.words[18];
                         const int tile = q >> 5, ln = q & 31;
                         const int px = (tile % tx) * kTileW + (ln & (kTileW - 1));
                         const int py = (tile / tx) * kTileH + (ln >> 3);
                         if (px < W && py < H) {
-                            float c2w[12], K[4];
-                            const float4 *cv = reinterpret_cast<const float4 *>(sv->c2w);
-#pragma unroll
-                            for (int k = 0; k < 3; ++k) {
-                                const float4 t4 = __ldcg(cv + k);
-                                c2w[4 * k] = t4.x;
-                                c2w[4 * k + 1] = t4.y;
-                                c2w[4 * k + 2] = t4.z;
-                                c2w[4 * k + 3] = t4.w;
-                            }
-                            const float4 k4 = __ldcg(cv + 3);
-                            K[0] = k4.x;
-                            K[1] = k4.y;
-                            K[2] = k4.z;
-                            K[3] = k4.w;
+                            const float *c2w = cw, *K = cw + 12;
                             camera_ray(c2w, K, px, py, mr.o, mr.d);
                             if constexpr (CT) {
                                 float oo[3], du[3], dv[3];
@@ -217,9 +257,11 @@ serve_kernel(const FieldView f, ServeView *__restrict__ ring, const ServeCtl *__
                             }
                             r = __fdiv_rn(f.radius_scale, K[0]);
                             march_init(f, mr);
-                            dst = ldcg_ptr(&sv->out) + 3ll * ((long long)py * W + px);
+                            float *vout;
+                            memcpy(&vout, &vc.words[24], sizeof vout);
+                            dst = vout + 3ll * ((long long)py * W + px);
                             view = v;
-                            my_req = __ldcg(&sv->req);
+                            my_req = vc.words[19];
                             live = true;
                             T = 1.0f;
                             C[0] = C[1] = C[2] = 0.0f;
@@ -253,16 +295,19 @@ serve_kernel(const FieldView f, ServeView *__restrict__ ring, const ServeCtl *__
                     const uint64_t waited = tc::globaltimer_ns() - t0;
                     // after 500 idle limits a CTA quits whatever the others do
                     // (bounded wait) and takes the launch with it
-                    if (ld_acquire_sys_s32(&ctl->stop) || waited > 500ull * idle_ns) {
+                    if (ld_acquire_gpu_s32(&ctl->stop) || waited > 500ull * idle_ns) {
                         atomicOr(idle, kQuit);
                         s_quit = 1;
                         break;
                     }
                     const unsigned st = atomicAdd(idle, 0u);
                     if (st & kQuit) { s_quit = 1; break; }
-                    if (atomicAdd(cursor, 0u) < ld_acquire_sys_u32(&ctl->n_views)) {
-                        if (atomicCAS(idle, st, st - 1u) == st) break;  // back to work
-                        continue;                                        // state moved: look again
+                    if (atomicAdd(cursor, 0u) < ld_acquire_gpu_u32(&ctl->n_views)) {
+                        // back to work: one unconditional decrement (a compare-and-swap
+                        // here made hundreds of waking CTAs retry against each other);
+                        // a launch already quitting takes this CTA with it
+                        if (atomicSub(idle, 1u) & kQuit) s_quit = 1;
+                        break;
                     }
                     // every CTA idle past the limit: the launch quits
                     if (waited > idle_ns && atomicCAS(idle, gridDim.x, gridDim.x | kQuit) == gridDim.x) {
@@ -331,7 +376,7 @@ template <int L, int FMT, bool CT>
 static cudaError_t launch_serve_ct(vrnerf_field *F, ServeView *ring, const ServeCtl *ctl,
                                    unsigned int *cursor, unsigned long long idle_ns,
                                    unsigned long long *tile_stats, cudaStream_t st) {
-    const size_t smem = tc_smem_bytes(2 * L, 0);
+    const size_t smem = tc_smem_bytes(2 * L, 0) + kServeSharedBytes;
     auto kern = serve_kernel<L, FMT, CT>;
     int bps = 0;
     cudaError_t e = prepare_tc(kern, smem, bps);
@@ -370,11 +415,14 @@ struct Req {
     float *out_host = nullptr;
     uint64_t rays = 0, bytes = 0;
     size_t arena_off = 0;
-    Clock::time_point t_submit, t_done;
+    Clock::time_point t_submit, t_admit, t_gpu, t_done;
+    Clock::time_point deadline;   // valid when has_deadline
+    bool has_deadline = false;
+    bool shed_if_late = false;    // drop it if the deadline passes before admission
     int views_left = 0;
     std::vector<int> ring_idx;
     cudaEvent_t copied = nullptr;
-    int state = 0;  // 0 pending, 1 in flight, 2 copying, 3 done, 4 cancelled
+    int state = 0;  // 0 pending, 1 in flight, 2 copying, 3 done, 4 cancelled, 5 shed (late)
     bool cancel = false;
 };
 
@@ -424,7 +472,8 @@ struct vrnerf_server {
     uint64_t budget = 0;
     int max_pending = 1024;
     unsigned long long idle_ns = 20000000ull;
-    cudaStream_t kst = nullptr, cst = nullptr;
+    cudaStream_t kst = nullptr, cst = nullptr;  // persistent kernel; output copies
+    cudaStream_t pst = nullptr;                 // view descriptors and counters (never waits on copies)
     ServeView *ring_d = nullptr;
     ServeView *ring_h = nullptr;  // pinned staging
     ServeCtl *ctl_h = nullptr, *ctl_d = nullptr;
@@ -446,6 +495,8 @@ struct vrnerf_server {
     std::vector<Req *> inflight;
     std::map<uint64_t, Req *> by_ticket;
     std::vector<double> latencies_ms;
+    std::vector<double> wait_ms, gpu_ms, copy_ms;  // per request: submit->admit, admit->rendered, ->copied
+    uint64_t late = 0, shed = 0;
     uint64_t next_ticket = 1, rays_done = 0, completed = 0, launches = 0;
     uint64_t max_inflight = 0;        // most requests on the GPU at once
     unsigned int next_req = 0;        // request sequence numbers carried by the views
@@ -464,19 +515,32 @@ struct vrnerf_server {
 
 bool vrnerf_server::admit_locked(std::vector<int> &new_views) {
     bool any = false;
+    const Clock::time_point now = Clock::now();
     while (!pending.empty()) {
-        Req *q = pending.front();
-        if (q->cancel) {
-            pending.pop_front();
-            q->state = 4;
-            done_cv.notify_all();
-            continue;
+        // drop cancelled requests, and late ones that asked to be shed
+        for (auto it = pending.begin(); it != pending.end();) {
+            Req *r = *it;
+            if (r->cancel || (r->shed_if_late && r->has_deadline && r->deadline < now)) {
+                r->state = r->cancel ? 4 : 5;
+                if (!r->cancel) ++shed;
+                it = pending.erase(it);
+                done_cv.notify_all();
+            } else {
+                ++it;
+            }
         }
+        if (pending.empty()) break;
+        // earliest deadline first; requests without one follow, in arrival order
+        auto pick = pending.begin();
+        for (auto it = pending.begin(); it != pending.end(); ++it)
+            if ((*it)->has_deadline && (!(*pick)->has_deadline || (*it)->deadline < (*pick)->deadline)) pick = it;
+        Req *q = *pick;
         // a ring entry is rewritten only long after its previous view finished
         if (n_views + q->n - oldest_live_view >= (unsigned)kRing / 2) break;
         size_t off = 0;
         if (!arena.alloc(q->bytes, off)) break;  // HBM budget: wait for earlier requests
-        pending.pop_front();
+        pending.erase(pick);
+        q->t_admit = now;
         q->arena_off = off;
         q->state = 1;
         q->views_left = q->n;
@@ -516,12 +580,16 @@ bool vrnerf_server::admit_locked(std::vector<int> &new_views) {
 }
 
 void vrnerf_server::publish(const std::vector<int> &new_views) {
-    // view descriptors -> device ring, then the new totals -> control block
+    // view descriptors -> device ring, then the new totals -> control block,
+    // both in device memory and in stream order: a kernel that sees the new
+    // count finds the descriptors already written (and idle CTAs poll device
+    // memory, not host memory across the chip-to-chip link)
     for (int idx : new_views)
-        cudaMemcpyAsync(ring_d + idx, ring_h + idx, sizeof(ServeView), cudaMemcpyHostToDevice, cst);
-    cudaStreamSynchronize(cst);
-    __atomic_store_n(&ctl_h->n_views, n_views, __ATOMIC_RELEASE);
-    __atomic_store_n(&ctl_h->published, published, __ATOMIC_RELEASE);
+        cudaMemcpyAsync(ring_d + idx, ring_h + idx, sizeof(ServeView), cudaMemcpyHostToDevice, pst);
+    ctl_h->n_views = n_views;
+    ctl_h->published = published;
+    cudaMemcpyAsync(ctl_d, ctl_h, sizeof(ServeCtl), cudaMemcpyHostToDevice, pst);
+    cudaStreamSynchronize(pst);
 }
 
 int vrnerf_server::ensure_kernel() {
@@ -557,6 +625,7 @@ void vrnerf_server::poll_completions() {
                 for (int idx : q->ring_idx)
                     if (__atomic_load_n(&done_h[idx], __ATOMIC_ACQUIRE) < view_slots[idx]) all = false;
                 if (all) {
+                    q->t_gpu = Clock::now();
                     if (q->out_host)
                         cudaMemcpyAsync(q->out_host, arena_d + q->arena_off, q->rays * 12, cudaMemcpyDeviceToHost, cst);
                     cudaEventRecord(q->copied, cst);
@@ -572,6 +641,10 @@ void vrnerf_server::poll_completions() {
             for (int idx : q->ring_idx) view_req[idx] = nullptr;
             inflight.erase(std::find(inflight.begin(), inflight.end(), q));
             latencies_ms.push_back(std::chrono::duration<double, std::milli>(q->t_done - q->t_submit).count());
+            wait_ms.push_back(std::chrono::duration<double, std::milli>(q->t_admit - q->t_submit).count());
+            gpu_ms.push_back(std::chrono::duration<double, std::milli>(q->t_gpu - q->t_admit).count());
+            copy_ms.push_back(std::chrono::duration<double, std::milli>(q->t_done - q->t_gpu).count());
+            if (q->has_deadline && q->t_done > q->deadline) ++late;
             rays_done += q->rays;
             ++completed;
         }
@@ -580,8 +653,8 @@ void vrnerf_server::poll_completions() {
     }
     if (!finished.empty()) {
         // the kernel's tile counters, for vrnerf_server_stats
-        cudaMemcpyAsync(tile_stats_h, tile_stats_d, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, cst);
-        cudaStreamSynchronize(cst);
+        cudaMemcpyAsync(tile_stats_h, tile_stats_d, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, pst);
+        cudaStreamSynchronize(pst);
         done_cv.notify_all();
     }
 }
@@ -628,11 +701,13 @@ int vrnerf_server_create(vrnerf_field *F, uint64_t hbm_budget_bytes, int32_t pre
     cudaError_t e = cudaSetDevice(F->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->kst, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->cst, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->pst, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&S->ring_d, sizeof(ServeView) * kRing);
     if (e == cudaSuccess) e = cudaMallocHost(&S->ring_h, sizeof(ServeView) * kRing);
-    if (e == cudaSuccess) e = cudaHostAlloc(&S->ctl_h, sizeof(ServeCtl), cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaMallocHost(&S->ctl_h, sizeof(ServeCtl));
+    if (e == cudaSuccess) e = cudaMalloc(&S->ctl_d, sizeof(ServeCtl));
+    if (e == cudaSuccess) e = cudaMemset(S->ctl_d, 0, sizeof(ServeCtl));
     if (e == cudaSuccess) e = cudaHostAlloc(&S->done_h, sizeof(unsigned int) * kRing, cudaHostAllocMapped);
-    if (e == cudaSuccess) e = cudaHostGetDevicePointer(&S->ctl_d, S->ctl_h, 0);
     if (e == cudaSuccess) e = cudaHostGetDevicePointer(&S->done_d, S->done_h, 0);
     if (e == cudaSuccess) e = cudaMalloc(&S->cursor, 2 * sizeof(unsigned int));  // cursor, idle state
     if (e == cudaSuccess) e = cudaMemset(S->cursor, 0, 2 * sizeof(unsigned int));
@@ -654,10 +729,14 @@ int vrnerf_server_create(vrnerf_field *F, uint64_t hbm_budget_bytes, int32_t pre
     return VRNERF_OK;
 }
 
-int vrnerf_submit(vrnerf_server *S, int32_t n_views, const float *cameras_host, const float *intrinsics_host,
-                  const int32_t *resolution_host, float *out_host, uint64_t *ticket) {
+}  // extern "C"
+
+static int submit_impl(vrnerf_server *S, int32_t n_views, const float *cameras_host, const float *intrinsics_host,
+                       const int32_t *resolution_host, float *out_host, double deadline_ms, int32_t shed_if_late,
+                       uint64_t *ticket) {
     if (!S || !cameras_host || !intrinsics_host || !resolution_host || !ticket)
         return fail(VRNERF_EINVAL, "NULL argument");
+    if (!(deadline_ms >= 0.0) || deadline_ms > 1.0e9) return fail(VRNERF_EINVAL, "deadline_ms must be in [0, 1e9]");
     if (n_views < 1 || n_views > 16) return fail(VRNERF_EINVAL, "a request holds 1 to 16 views");
     Req *q = new Req();
     q->n = n_views;
@@ -696,6 +775,12 @@ int vrnerf_submit(vrnerf_server *S, int32_t n_views, const float *cameras_host, 
     }
     q->ticket = S->next_ticket++;
     q->t_submit = Clock::now();
+    if (deadline_ms > 0.0) {
+        q->has_deadline = true;
+        q->shed_if_late = shed_if_late != 0;
+        q->deadline = q->t_submit + std::chrono::duration_cast<Clock::duration>(
+                                        std::chrono::duration<double, std::milli>(deadline_ms));
+    }
     if (!S->have_first) {
         S->t_first = q->t_submit;
         S->have_first = true;
@@ -707,6 +792,20 @@ int vrnerf_submit(vrnerf_server *S, int32_t n_views, const float *cameras_host, 
     return VRNERF_OK;
 }
 
+extern "C" {
+
+int vrnerf_submit(vrnerf_server *S, int32_t n_views, const float *cameras_host, const float *intrinsics_host,
+                  const int32_t *resolution_host, float *out_host, uint64_t *ticket) {
+    return submit_impl(S, n_views, cameras_host, intrinsics_host, resolution_host, out_host, 0.0, 0, ticket);
+}
+
+int vrnerf_submit_deadline(vrnerf_server *S, int32_t n_views, const float *cameras_host,
+                           const float *intrinsics_host, const int32_t *resolution_host, float *out_host,
+                           double deadline_ms, int32_t shed_if_late, uint64_t *ticket) {
+    return submit_impl(S, n_views, cameras_host, intrinsics_host, resolution_host, out_host, deadline_ms,
+                       shed_if_late, ticket);
+}
+
 int vrnerf_poll(vrnerf_server *S, uint64_t ticket, int32_t timeout_ms, double *latency_ms) {
     if (!S) return fail(VRNERF_EINVAL, "NULL argument");
     std::unique_lock<std::mutex> lk(S->mu);
@@ -716,6 +815,13 @@ int vrnerf_poll(vrnerf_server *S, uint64_t ticket, int32_t timeout_ms, double *l
     auto deadline = Clock::now() + std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms);
     while (q->state < 3 && !S->error) {
         if (S->done_cv.wait_until(lk, deadline) == std::cv_status::timeout && q->state < 3) break;
+    }
+    if (q->state == 5) {
+        S->by_ticket.erase(it);
+        cudaEventDestroy(q->copied);
+        delete q;
+        return fail(VRNERF_ELATE, "request %llu was shed: its deadline passed before it reached the GPU",
+                    (unsigned long long)ticket);
     }
     if (q->state < 3) {
         if (S->error) return fail(S->error, "server failed");
@@ -763,6 +869,17 @@ int vrnerf_server_stats(vrnerf_server *S, vrnerf_serve_stats *st) {
     }
     if (S->have_first)
         st->wall_s = std::chrono::duration<double>(Clock::now() - S->t_first).count();
+    st->late = S->late;
+    st->shed = S->shed;
+    auto pct = [](std::vector<double> v, double *p50, double *p99) {
+        if (v.empty()) return;
+        std::sort(v.begin(), v.end());
+        *p50 = v[(size_t)(0.50 * (v.size() - 1))];
+        *p99 = v[(size_t)(0.99 * (v.size() - 1))];
+    };
+    pct(S->wait_ms, &st->wait_p50_ms, &st->wait_p99_ms);
+    pct(S->gpu_ms, &st->gpu_p50_ms, &st->gpu_p99_ms);
+    pct(S->copy_ms, &st->copy_p50_ms, &st->copy_p99_ms);
     return VRNERF_OK;
 }
 
@@ -770,6 +887,11 @@ int vrnerf_server_reset_stats(vrnerf_server *S) {
     if (!S) return fail(VRNERF_EINVAL, "NULL argument");
     std::lock_guard<std::mutex> lk(S->mu);
     S->latencies_ms.clear();
+    S->wait_ms.clear();
+    S->gpu_ms.clear();
+    S->copy_ms.clear();
+    S->late = 0;
+    S->shed = 0;
     S->rays_done = 0;
     S->completed = 0;
     S->launches = 0;
@@ -785,9 +907,14 @@ void vrnerf_server_destroy(vrnerf_server *S) {
         S->cv.notify_all();
         S->worker.join();
     }
-    if (S->ctl_h) __atomic_store_n(&S->ctl_h->stop, 1, __ATOMIC_RELEASE);
+    if (S->ctl_h && S->ctl_d && S->pst) {
+        S->ctl_h->stop = 1;
+        cudaMemcpyAsync(S->ctl_d, S->ctl_h, sizeof(ServeCtl), cudaMemcpyHostToDevice, S->pst);
+        cudaStreamSynchronize(S->pst);
+    }
     if (S->kst) cudaStreamSynchronize(S->kst);
     if (S->cst) cudaStreamSynchronize(S->cst);
+    if (S->pst) cudaStreamSynchronize(S->pst);
     for (auto &kv : S->by_ticket) {
         if (kv.second->copied) cudaEventDestroy(kv.second->copied);
         delete kv.second;
@@ -799,10 +926,12 @@ void vrnerf_server_destroy(vrnerf_server *S) {
     if (S->tile_stats_h) cudaFreeHost(S->tile_stats_h);
     if (S->done_h) cudaFreeHost(S->done_h);
     if (S->ctl_h) cudaFreeHost(S->ctl_h);
+    if (S->ctl_d) cudaFree(S->ctl_d);
     if (S->ring_h) cudaFreeHost(S->ring_h);
     if (S->ring_d) cudaFree(S->ring_d);
     if (S->kst) cudaStreamDestroy(S->kst);
     if (S->cst) cudaStreamDestroy(S->cst);
+    if (S->pst) cudaStreamDestroy(S->pst);
     delete S;
 }
 

@@ -531,6 +531,10 @@ __global__ void half_to_float_kernel(const __half *__restrict__ a, float *__rest
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
+// Samples one pass of the training pipeline holds at most unless the field
+// sets its own budget (2^26 records: about 10 to 15 GB of per-sample buffers).
+constexpr long long kDefaultSampleBudget = 1ll << 26;
+
 struct TrainScratch {
     // per ray
     int *cnt = nullptr, *n_used = nullptr;
@@ -589,8 +593,12 @@ static int ensure_samples(TrainScratch &S, long long n) {
     const long long want = n + n / 4 + 1024;
     cudaError_t e;
     if ((e = cudaMalloc(&S.rec, sizeof(int2) * (size_t)want)) != cudaSuccess ||
-        (e = cudaMalloc(&S.sc, sizeof(float4) * (size_t)want)) != cudaSuccess)
+        (e = cudaMalloc(&S.sc, sizeof(float4) * (size_t)want)) != cudaSuccess) {
+        cudaFree(S.rec);
+        S.rec = nullptr;
+        cudaGetLastError();  // a failed allocation leaves no error behind
         return fail(VRNERF_ENOMEM, "sample records (%lld): %s", want, cudaGetErrorString(e));
+    }
     S.scap = want;
     return VRNERF_OK;
 }
@@ -622,34 +630,36 @@ static cudaError_t grid_for(K kern, int threads, size_t smem, long long work, in
     return cudaSuccess;
 }
 
-// The sample-parallel backward (header comment): gradients into the field's
-// buffers (zeroed here). target != nullptr: L1 loss, accumulated into
-// F->loss_acc; else gC (dL/dC per ray) and n_given (composited samples).
-template <int L>
-static int backward_t(vrnerf_field *F, const float *o, const float *d, const float *r, int B, const float *target,
-                      const float *gC, const int *n_given, cudaStream_t st, float *C_out = nullptr,
-                      int *n_out = nullptr) {
-    constexpr int D = 2 * L;
-    TrainScratch &S = *static_cast<TrainScratch *>(F->train_scratch);
-    const FieldView &f = F->view;
-    cudaError_t e = cudaSuccess;
-    if (!C_out) {
-        e = cudaMemsetAsync(F->grid_grad, 0, grid_entries(F->desc) * sizeof(float), st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(F->mlp_grad, 0, sizeof(float) * f.n_mlp, st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(F->loss_acc, 0, 64, st);
-    }
-    if (e == cudaSuccess) e = cudaMemsetAsync(S.total, 0, sizeof(unsigned long long), st);
+// Marches rays [0, B) of (o, d), counts their evaluated samples and reserves
+// their records (S.cnt, S.off); *n receives the total. One small read-back.
+static int count_pass(vrnerf_field *F, TrainScratch &S, const float *o, const float *d, int B, cudaStream_t st,
+                      long long *n) {
     int blocks = 0;
+    cudaError_t e = cudaMemsetAsync(S.total, 0, sizeof(unsigned long long), st);
     if (e == cudaSuccess) e = grid_for(count_kernel, 128, 0, B, blocks);
     if (e == cudaSuccess) {
-        count_kernel<<<blocks, 128, 0, st>>>(f, o, d, B, S.cnt, S.off, S.total);
+        count_kernel<<<blocks, 128, 0, st>>>(F->view, o, d, B, S.cnt, S.off, S.total);
         e = cudaGetLastError();
     }
-    // the record count sizes the per-sample buffers: one small read-back
     if (e == cudaSuccess) e = cudaMemcpyAsync(S.total_h, S.total, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "backward: count");
-    const long long n = (long long)*S.total_h;
+    *n = (long long)*S.total_h;
+    return VRNERF_OK;
+}
+
+// The per-sample part of the pipeline for Bc rays whose samples count_pass
+// has just counted (n records); pointers are already offset to the rays.
+// inv3B is 1 / (3 B) of the whole batch. ENOMEM when the per-sample buffers
+// cannot be allocated (nothing launched then).
+template <int L>
+static int samples_pass(vrnerf_field *F, TrainScratch &S, const float *o, const float *d, const float *r, int Bc,
+                        long long n, float inv3B, const float *target, const float *gC, const int *n_given,
+                        cudaStream_t st, float *C_out, int *n_out) {
+    constexpr int D = 2 * L;
+    const FieldView &f = F->view;
+    cudaError_t e = cudaSuccess;
+    int blocks = 0;
     int rc = ensure_samples(S, n);
     if (rc) return rc;
     const bool tc_bwd = !C_out && F->train_prec == VRNERF_BF16;
@@ -659,7 +669,7 @@ static int backward_t(vrnerf_field *F, const float *o, const float *d, const flo
         S.fcap = 0;
         const long long want = n + n / 4 + 1024;
         if ((e = cudaMalloc(&S.feat, sizeof(uint4) * (size_t)(D / 8) * (size_t)want)) != cudaSuccess)
-            return fail(VRNERF_ENOMEM, "sample features (%lld): %s", want, cudaGetErrorString(e));
+            return cudaGetLastError(), fail(VRNERF_ENOMEM, "sample features (%lld): %s", want, cudaGetErrorString(e));
         S.fcap = want;
     }
     if (!C_out && n > S.dcap) {
@@ -668,13 +678,14 @@ static int backward_t(vrnerf_field *F, const float *o, const float *d, const flo
         S.dcap = 0;
         const long long want = n + n / 4 + 1024;
         if ((e = cudaMalloc(&S.dfeat, sizeof(float4) * (size_t)(D / 4) * (size_t)want)) != cudaSuccess)
-            return fail(VRNERF_ENOMEM, "sample feature gradients (%lld): %s", want, cudaGetErrorString(e));
+            return cudaGetLastError(), fail(VRNERF_ENOMEM, "sample feature gradients (%lld): %s", want,
+                                            cudaGetErrorString(e));
         S.dcap = want;
     }
     if (n > 0) {
-        e = grid_for(emit_kernel, 128, 0, B, blocks);
+        e = grid_for(emit_kernel, 128, 0, Bc, blocks);
         if (e == cudaSuccess) {
-            emit_kernel<<<blocks, 128, 0, st>>>(f, o, d, B, S.off, S.cnt, S.rec);
+            emit_kernel<<<blocks, 128, 0, st>>>(f, o, d, Bc, S.off, S.cnt, S.rec);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess && tc_bwd) {
@@ -690,11 +701,11 @@ static int backward_t(vrnerf_field *F, const float *o, const float *d, const flo
             }
         }
     }
-    if (e == cudaSuccess) e = grid_for(ray_comp_kernel, 128, 0, B, blocks);
+    if (e == cudaSuccess) e = grid_for(ray_comp_kernel, 128, 0, Bc, blocks);
     if (e == cudaSuccess) {
-        ray_comp_kernel<<<blocks, 128, 0, st>>>(f, o, d, B, S.cnt, S.off, S.rec, n_given, target, gC,
-                                                1.0f / (3.0f * B), S.sc, C_out ? n_out : S.n_used,
-                                                target ? F->loss_acc : nullptr, C_out ? nullptr : F->hist, C_out);
+        ray_comp_kernel<<<blocks, 128, 0, st>>>(f, o, d, Bc, S.cnt, S.off, S.rec, n_given, target, gC, inv3B, S.sc,
+                                                C_out ? n_out : S.n_used, target ? F->loss_acc : nullptr,
+                                                C_out ? nullptr : F->hist, C_out);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && n > 0 && tc_bwd) {
@@ -711,6 +722,65 @@ static int backward_t(vrnerf_field *F, const float *o, const float *d, const flo
         if (e == cudaSuccess) e = launch_grid_scatter(F, o, d, r, S.rec, S.off, S.n_used, n, S.dfeat, st);
     }
     if (e != cudaSuccess) return cuda_fail(e, "backward");
+    return VRNERF_OK;
+}
+
+// The sample-parallel backward (header comment): gradients into the field's
+// buffers (zeroed here). target != nullptr: L1 loss, accumulated into
+// F->loss_acc; else gC (dL/dC per ray) and n_given (composited samples).
+//
+// Per-step memory grows with the batch's samples (record, sigma/colour and
+// their gradients, feature gradients: 152 B per sample, 216 B with bf16
+// features). A batch whose samples exceed the field's sample budget, or whose
+// buffers cannot be allocated, runs in ray ranges that fit, one after the
+// other; gradients, loss and history accumulate over the ranges, so the
+// result is the same as one pass (up to the order of float additions).
+template <int L>
+static int backward_t(vrnerf_field *F, const float *o, const float *d, const float *r, int B, const float *target,
+                      const float *gC, const int *n_given, cudaStream_t st, float *C_out = nullptr,
+                      int *n_out = nullptr) {
+    TrainScratch &S = *static_cast<TrainScratch *>(F->train_scratch);
+    const FieldView &f = F->view;
+    cudaError_t e = cudaSuccess;
+    if (!C_out) {
+        e = cudaMemsetAsync(F->grid_grad, 0, grid_entries(F->desc) * sizeof(float), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(F->mlp_grad, 0, sizeof(float) * f.n_mlp, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(F->loss_acc, 0, 64, st);
+        if (e != cudaSuccess) return cuda_fail(e, "backward: zero gradients");
+    }
+    const float inv3B = 1.0f / (3.0f * B);
+    // a single ray never needs more than max_steps records
+    long long budget = F->sample_budget > 0 ? (long long)F->sample_budget : kDefaultSampleBudget;
+    if (budget < f.S) budget = f.S;
+    long long n = 0;
+    int rc = count_pass(F, S, o, d, B, st, &n);
+    if (rc) return rc;
+    long long rays_per = n > budget ? (long long)((double)B * (double)budget / (double)n) : B;
+    if (rays_per < 1) rays_per = 1;
+    int b0 = 0;
+    bool counted = rays_per >= B;  // S.cnt / S.off hold the counts of the next range
+    while (b0 < B) {
+        const int Bc = (int)(B - b0 < rays_per ? B - b0 : rays_per);
+        if (!counted && (rc = count_pass(F, S, o + 3ll * b0, d + 3ll * b0, Bc, st, &n))) return rc;
+        counted = false;
+        if (n > budget && Bc > 1) {  // this range still holds too many samples: halve it
+            rays_per = Bc / 2;
+            continue;
+        }
+        rc = samples_pass<L>(F, S, o + 3ll * b0, d + 3ll * b0, r + b0, Bc, n, inv3B, target ? target + 3ll * b0 : nullptr,
+                             gC ? gC + 3ll * b0 : nullptr, n_given ? n_given + b0 : nullptr, st,
+                             C_out ? C_out + 3ll * b0 : nullptr, n_out ? n_out + b0 : nullptr);
+        if (rc == VRNERF_ENOMEM && Bc > 1) {
+            // not enough device memory for this range: clear the failed
+            // allocation's error state and retry with half the rays
+            cudaGetLastError();
+            budget = n / 2 > f.S ? n / 2 : f.S;
+            rays_per = Bc / 2;
+            continue;
+        }
+        if (rc) return rc;
+        b0 += Bc;
+    }
     return VRNERF_OK;
 }
 
@@ -776,6 +846,12 @@ int vrnerf_backward_from_grad(vrnerf_field *F, const float *rays_o, const float 
     } catch (...) {
         return fail(VRNERF_EINVAL, "backward_from_grad: unexpected C++ exception");
     }
+}
+
+int vrnerf_field_set_sample_budget(vrnerf_field *F, uint64_t max_samples) {
+    if (!F) return fail(VRNERF_EINVAL, "field is NULL");
+    F->sample_budget = max_samples;
+    return VRNERF_OK;
 }
 
 int vrnerf_field_set_train_precision(vrnerf_field *F, int32_t precision) {

@@ -19,6 +19,7 @@ from . import build as _build
 FP32, FP16, BF16, FP8 = 0, 1, 2, 3
 PRECISIONS = {"fp32": FP32, "fp16": FP16, "bf16": BF16, "fp8": FP8}
 OK, EINVAL, ENOMEM, ECUDA, ETIMEDOUT, EBUSY, ENOTFOUND, ECANCELED, ECHECK = 0, -1, -2, -3, -4, -5, -6, -7, -8
+ELATE = -9
 
 
 class VrnerfError(RuntimeError):
@@ -68,6 +69,7 @@ _SIGS = {
     "vrnerf_history_reset": (ctypes.c_int, [_VP]),
     "vrnerf_build_checked": (ctypes.c_int, []),
     "vrnerf_field_set_train_precision": (ctypes.c_int, [_VP, _I32]),
+    "vrnerf_field_set_sample_budget": (ctypes.c_int, [_VP, ctypes.c_uint64]),
     "vrnerf_debug_check_trigger": (ctypes.c_int, [_VP, _VP]),
     "vrnerf_forward_rays": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP]),
     "vrnerf_backward_from_grad": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I32, _VP, _VP, _VP]),
@@ -93,6 +95,7 @@ _SIGS = {
     "vrnerf_render_noalloc": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _I32, _VP, _VP]),
     "vrnerf_server_create": (ctypes.c_int, [_VP, ctypes.c_uint64, _I32, _VP]),
     "vrnerf_submit": (ctypes.c_int, [_VP, _I32, _VP, _VP, _VP, _VP, _VP]),
+    "vrnerf_submit_deadline": (ctypes.c_int, [_VP, _I32, _VP, _VP, _VP, _VP, ctypes.c_double, _I32, _VP]),
     "vrnerf_poll": (ctypes.c_int, [_VP, ctypes.c_uint64, _I32, _VP]),
     "vrnerf_cancel": (ctypes.c_int, [_VP, ctypes.c_uint64]),
     "vrnerf_server_stats": (ctypes.c_int, [_VP, _VP]),
@@ -107,7 +110,10 @@ class ServerStats(ctypes.Structure):
                 ("inflight", ctypes.c_uint64), ("p50_ms", ctypes.c_double),
                 ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double), ("wall_s", ctypes.c_double),
                 ("max_inflight", ctypes.c_uint64), ("tile_rounds", ctypes.c_uint64),
-                ("mixed_tile_rounds", ctypes.c_uint64)]
+                ("mixed_tile_rounds", ctypes.c_uint64), ("late", ctypes.c_uint64), ("shed", ctypes.c_uint64),
+                ("wait_p50_ms", ctypes.c_double), ("wait_p99_ms", ctypes.c_double),
+                ("gpu_p50_ms", ctypes.c_double), ("gpu_p99_ms", ctypes.c_double),
+                ("copy_p50_ms", ctypes.c_double), ("copy_p99_ms", ctypes.c_double)]
 
 _lib = None
 
@@ -366,6 +372,11 @@ class FieldModule(torch.nn.Module):
         vrnerf_field_params_changed(self.field)
 
 
+def vrnerf_field_set_sample_budget(field: Field, max_samples: int):
+    """Most samples one training pass holds (0: the library's default)."""
+    _check(load().vrnerf_field_set_sample_budget(field.h, int(max_samples)))
+
+
 def vrnerf_field_set_train_precision(field: Field, precision):
     p = PRECISIONS.get(precision, precision) if isinstance(precision, str) else int(precision)
     _check(load().vrnerf_field_set_train_precision(field.h, p))
@@ -547,6 +558,36 @@ def vrnerf_train_step(field: Field, rays_o, rays_d, radii, target_linear, lr_gri
     return loss.value if want_loss else None
 
 
+def check_noalloc_buffers(cfg, grid, mlp, occ_bits, cameras, intrinsics, n_views, out, rays):
+    """Checks the caller-owned buffers of vrnerf_render_noalloc against the
+    description before the call: the C entry point receives bare pointers and
+    cannot see their sizes, so a short or mistyped buffer would be read past
+    its end on the device. Raises ValueError."""
+    def need(t, name, dtypes, numel, at_least=False):
+        if not isinstance(t, torch.Tensor):
+            raise ValueError(f"{name} must be a torch tensor")
+        if t.dtype not in dtypes:
+            raise ValueError(f"{name} has dtype {t.dtype}, expected one of {dtypes}")
+        if (t.numel() < numel) if at_least else (t.numel() != numel):
+            raise ValueError(f"{name} holds {t.numel()} elements, expected {'at least ' if at_least else ''}{numel}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    grid_dtype = (torch.float16,) if cfg.feat_fp16 else (torch.float32,)
+    need(grid, "grid", grid_dtype, cfg.levels * cfg.T * cfg.feats)
+    need(mlp, "mlp", (torch.float32,), cfg.n_mlp())
+    nvox = int(cfg.occ_res[0]) * int(cfg.occ_res[1]) * int(cfg.occ_res[2])
+    occ_types = tuple(t for t in (torch.int32, getattr(torch, "uint32", None)) if t is not None)
+    need(occ_bits, "occ_bits", occ_types, (nvox + 31) // 32, at_least=True)
+    need(cameras, "cameras", (torch.float32,), 12 * n_views)
+    need(intrinsics, "intrinsics", (torch.float32,), 4 * n_views)
+    if out is not None:
+        need(out, "out", (torch.float32,), 3 * rays)
+    for name, t in (("grid", grid), ("mlp", mlp), ("occ_bits", occ_bits), ("cameras", cameras),
+                    ("intrinsics", intrinsics), ("out", out)):
+        if t is not None and not t.is_cuda:
+            raise ValueError(f"{name} must be in device memory")
+
+
 def vrnerf_render_noalloc(cfg, grid, mlp, occ_bits, cameras, intrinsics, resolution, out=None,
                           stream=None):
     """fp32 render that allocates nothing in the library: grid / mlp / occ_bits
@@ -554,10 +595,9 @@ def vrnerf_render_noalloc(cfg, grid, mlp, occ_bits, cameras, intrinsics, resolut
     words as int32 or uint32). `out` is allocated here only when not given."""
     res = np.ascontiguousarray(resolution, dtype=np.int32).reshape(-1, 2)
     rays = int((res[:, 0].astype(np.int64) * res[:, 1]).sum())
+    check_noalloc_buffers(cfg, grid, mlp, occ_bits, cameras, intrinsics, res.shape[0], out, rays)
     if out is None:
         out = torch.empty((rays, 3), device=cameras.device, dtype=torch.float32)
-    for t in (grid, mlp, occ_bits):
-        assert isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()
     d = desc(cfg)
     _check(load().vrnerf_render_noalloc(ctypes.byref(d), _ptr(grid), _ptr(_dev(mlp)), _ptr(occ_bits),
                                         _ptr(_dev(cameras)), _ptr(_dev(intrinsics)), _ptr(res),
@@ -578,20 +618,27 @@ class Server:
         self.h = h
         self._keep = {}
 
-    def submit(self, cameras, intrinsics, resolution, out=None):
+    def submit(self, cameras, intrinsics, resolution, out=None, deadline_ms=None, shed_if_late=False):
+        """Queues a request; with deadline_ms it is admitted earliest deadline
+        first (vrnerf_submit_deadline), and shed_if_late drops it if the
+        deadline passes while it waits."""
         cams = np.ascontiguousarray(cameras, np.float32).reshape(-1, 3, 4)
         K = np.ascontiguousarray(intrinsics, np.float32).reshape(-1, 4)
         res = np.ascontiguousarray(resolution, np.int32).reshape(-1, 2)
         t = ctypes.c_uint64()
-        _check(load().vrnerf_submit(self.h, cams.shape[0], _ptr(cams), _ptr(K), _ptr(res),
-                                    _ptr(out) if out is not None else None, ctypes.byref(t)))
+        o = _ptr(out) if out is not None else None
+        if deadline_ms is None:
+            _check(load().vrnerf_submit(self.h, cams.shape[0], _ptr(cams), _ptr(K), _ptr(res), o, ctypes.byref(t)))
+        else:
+            _check(load().vrnerf_submit_deadline(self.h, cams.shape[0], _ptr(cams), _ptr(K), _ptr(res), o,
+                                                 float(deadline_ms), int(bool(shed_if_late)), ctypes.byref(t)))
         self._keep[t.value] = out
         return t.value
 
     def poll(self, ticket, timeout_ms=10000):
         lat = ctypes.c_double()
         rc = load().vrnerf_poll(self.h, ctypes.c_uint64(ticket), int(timeout_ms), ctypes.byref(lat))
-        if rc in (OK, ECANCELED):
+        if rc in (OK, ECANCELED, ELATE):
             self._keep.pop(ticket, None)
         _check(rc)
         return lat.value

@@ -76,3 +76,40 @@ def test_scene_generators_hit_their_targets():
     assert room[0].all() and room[-1].all()
     bits = S.pack_bits(occ)
     assert (S.unpack_bits(bits, (64, 64, 64)) == occ).all()
+
+
+def test_noalloc_wrapper_rejects_mismatched_buffers():
+    """The binding checks the caller's buffers against the description before
+    vrnerf_render_noalloc sees bare pointers (a short buffer would be read past
+    its end on the device). CPU tensors of the right shape pass the size and
+    type checks and fail only on the device check."""
+    import torch
+    from paper_2311_02542_gb300 import synth as S
+    from paper_2311_02542_gb300 import vrnerf as V
+    cfg = S.cfg_unit_cube()                          # fp32 grid, L=8, T=2^14, 64^3 occupancy
+    n_grid = cfg.levels * cfg.T * cfg.feats
+    good = dict(grid=torch.zeros(n_grid), mlp=torch.zeros(cfg.n_mlp()),
+                occ_bits=torch.zeros(64 ** 3 // 32, dtype=torch.int32),
+                cameras=torch.zeros(1, 3, 4), intrinsics=torch.zeros(1, 4))
+
+    def check(**kw):
+        a = {**good, **kw}
+        V.check_noalloc_buffers(cfg, a["grid"], a["mlp"], a["occ_bits"], a["cameras"], a["intrinsics"],
+                                1, a.get("out"), 64 * 64)
+
+    bad = [dict(grid=torch.zeros(n_grid, dtype=torch.float16)),       # fp16 grid for an fp32 field
+           dict(grid=torch.zeros(n_grid // 2)),                        # smaller table
+           dict(mlp=torch.zeros(cfg.n_mlp() - 1)),                     # short weights
+           dict(mlp=torch.zeros(cfg.n_mlp(), dtype=torch.float64)),
+           dict(occ_bits=torch.zeros(64 ** 3 // 32 - 1, dtype=torch.int32)),
+           dict(occ_bits=torch.zeros(64 ** 3 // 32, dtype=torch.float32)),
+           dict(cameras=torch.zeros(2, 3)),
+           dict(intrinsics=torch.zeros(3)),
+           dict(out=torch.zeros(64 * 64, 2)),
+           dict(grid=torch.zeros(2 * n_grid)[::2])]                    # not contiguous
+    for kw in bad:
+        with pytest.raises(ValueError) as e:
+            check(**kw)
+        assert "device memory" not in str(e.value), kw
+    with pytest.raises(ValueError, match="device memory"):
+        check()

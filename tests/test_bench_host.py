@@ -68,3 +68,20 @@ def test_clock_sampler_without_nvidia_smi_reports_it():
     c.mark()
     s = c.stop()
     assert s["sm_mhz"] is None and s["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_bench_line_ends_with_the_headline_keys():
+    """The bulky extras come first; a reader that keeps only the end of the
+    line still sees stereo latency, the fp32 comparison and the sweep."""
+    import json
+
+    import bench
+    line = {"metric": "Mrays/s", "value": 1.0, "stereo_2x2048": {"p50_ms": 6.0}, "plain_fp32": {"value": 2.0},
+            "precision_sweep": {"fp16": 1}, "serving": {"x": "y" * 4000}, "roofline": {"frac": 0.4},
+            "train_step": {"ms": 1.0}, "clocks": {}}
+    out = bench.tail_order(line)
+    assert list(out)[:2] == ["metric", "value"]
+    assert list(out)[-3:] == ["precision_sweep", "plain_fp32", "stereo_2x2048"]
+    assert set(out) == set(line)
+    tail = json.dumps(out)[-1500:]
+    assert '"stereo_2x2048"' in tail and '"plain_fp32"' in tail and '"precision_sweep"' in tail

@@ -188,3 +188,34 @@ def test_serving_relaunches_after_idle_exit(V, room):
     assert srv.stats()["kernel_launches"] >= 2
     srv.close()
     f.close()
+
+
+def test_serving_deadlines_order_and_shed(V, room):
+    """Waiting requests are admitted earliest deadline first, and a request
+    whose deadline passes while it waits is shed when it asked to be. The
+    budget holds one 512^2 output at a time, so admission is sequential."""
+    f = V.Field(room.cfg, room.grid, room.mlp, room.occ_bits)
+    c2w, K, res = S.camera_room(room.occ, room.cfg, 2, 512, 512)
+    one = 512 * 512 * 12
+    srv = V.Server(f, one + one // 2, "fp16")
+    outs = [np.zeros((512 * 512, 3), np.float32) for _ in range(4)]
+    t_a = srv.submit(c2w, K, res, outs[0])                          # admitted at once
+    t_b = srv.submit(c2w, K, res, outs[1])                          # no deadline, arrives first
+    t_c = srv.submit(c2w, K, res, outs[2], deadline_ms=10000.0)     # deadline: goes ahead of b
+    t_d = srv.submit(c2w, K, res, outs[3], deadline_ms=0.001, shed_if_late=True)
+    lat = {t: srv.poll(t, 20000) for t in (t_a, t_c, t_b)}
+    with pytest.raises(V.VrnerfError) as e:
+        srv.poll(t_d, 20000)
+    assert e.value.code == V.ELATE
+    # c was submitted after b and finished before it
+    assert lat[t_c] < lat[t_b]
+    ref = _alone(V, f, c2w, K, res)
+    for o in outs[:3]:
+        assert np.all(np.abs(o - ref) <= TC_RTOL * np.abs(ref) + TC_ATOL)
+    st = srv.stats()
+    assert st["shed"] == 1 and st["late"] == 0 and st["completed"] == 3
+    assert st["gpu_p99_ms"] >= st["gpu_p50_ms"] > 0 and st["wait_p99_ms"] > 0 and st["copy_p50_ms"] > 0
+    with pytest.raises(V.VrnerfError):
+        srv.submit(c2w, K, res, None, deadline_ms=-1.0)
+    srv.close()
+    f.close()

@@ -225,3 +225,33 @@ def test_bf16_training_reduces_loss_like_fp32(V):
     a, b = np.array(curves["fp32"]), np.array(curves["bf16"])
     assert b[-1] < 0.9 * b[0]
     assert np.all(np.abs(a - b) <= 0.02 * a), (a[::6], b[::6])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_sample_budget_splits_the_batch_without_changing_it(V, prec):
+    """A sample budget far below the batch's samples runs the pipeline over
+    many ray ranges; the loss, the gradients (float atomics in another order:
+    1e-5 relative + 1e-6 of the largest) and the forward's colours and sample
+    counts (bit-identical) equal one pass over the whole batch."""
+    sc = S.make_scene("room")
+    cfg = sc.cfg
+    poses, intr = S.training_views(sc.occ, cfg, n_views=16)
+    o, d, r, tgt = S.training_batch(poses, intr, 8192, seed=5, step=3)
+    args = (_cuda(o), _cuda(d), _cuda(r))
+    out = {}
+    for budget in (0, 5000):
+        f = V.Field(cfg, sc.grid, sc.mlp, sc.occ_bits)
+        V.vrnerf_field_set_train_precision(f, prec)
+        V.vrnerf_field_set_sample_budget(f, budget)
+        loss = V.vrnerf_backward(f, *args, _cuda(tgt))
+        gg, gm = V.vrnerf_field_get_grads(f)
+        pq, n = V.vrnerf_forward_rays(f, *args)
+        V.vrnerf_field_status(f)
+        out[budget] = (loss, gg.reshape(-1), gm, pq.cpu().numpy(), n.cpu().numpy())
+        f.close()
+    (l0, g0, m0, p0, n0), (l1, g1, m1, p1, n1) = out[0], out[5000]
+    assert int(n0.sum()) > 4 * 5000  # the small budget really splits the batch
+    assert l1 == pytest.approx(l0, rel=1e-5)
+    for a, b in ((g1, g0), (m1, m0)):
+        assert np.all(np.abs(a - b) <= 1e-5 * np.abs(b) + 1e-6 * np.abs(b).max())
+    assert (p1 == p0).all() and (n1 == n0).all()

@@ -77,3 +77,27 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
         V.vrnerf_render_noalloc(replace(sc.cfg, max_steps=8150), grid, mlp, occ, _cuda(c2w),
                                 _cuda(K), res)
     assert e.value.code == V.EINVAL and "scratch" in str(e.value)
+
+
+def test_noalloc_alternating_sample_counts():
+    """Consecutive calls that change max_steps: the sample-distance table in
+    the shared scratch is copied in again whenever its key changes, and the
+    fp32 kernel's shared memory (weights plus the table) crosses 48 KB at
+    about 3 900 steps, which needs the per-device launch attribute. Each call
+    matches vrnerf_render of a field with the same description."""
+    from paper_2311_02542_gb300 import vrnerf as V
+    V.load()
+    sc = S.make_scene("unit_cube")
+    grid, mlp, occ = _caller_buffers(sc)
+    c2w, K, res = S.camera_unit_cube(sc.occ, sc.cfg, 3, 40, 24)
+    cams, intr = _cuda(c2w), _cuda(K)
+    fields = {}
+    for steps in (64, 4096, 64, 6000, 4096, 64):
+        cfg = replace(sc.cfg, max_steps=steps)
+        if steps not in fields:
+            fields[steps] = V.Field(cfg, sc.grid, sc.mlp, sc.occ_bits)
+        want = V.vrnerf_render(fields[steps], cams, intr, res).cpu().numpy()
+        got = V.vrnerf_render_noalloc(cfg, grid, mlp, occ, cams, intr, res).cpu().numpy()
+        assert np.all(np.abs(got - want) <= RTOL * np.abs(want) + ATOL), steps
+    for f in fields.values():
+        f.close()

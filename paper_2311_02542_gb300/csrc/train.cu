@@ -113,10 +113,13 @@ __device__ __forceinline__ void minigemm_cols(const float *sD, const float *sA, 
 
 // ---- 1. count / emit ----------------------------------------------------
 // Evaluated samples of ray b (no early termination) and the start of its
-// records: one atomic per warp reserves the warp's records.
+// records: one atomic per warp reserves the warp's records. With `mask`
+// (mw words per ray, zeroed beforehand), the ray's evaluated step indices
+// are also kept as bits, so that emit needs no second march.
 __global__ void __launch_bounds__(128)
 count_kernel(const FieldView f, const float *__restrict__ o_in, const float *__restrict__ d_in, int B,
-             int *__restrict__ cnt, long long *__restrict__ off, unsigned long long *__restrict__ total) {
+             int *__restrict__ cnt, long long *__restrict__ off, unsigned long long *__restrict__ total,
+             uint32_t *__restrict__ mask, int mw) {
     const int lane = threadIdx.x & 31;
     for (long long b0 = (long long)blockIdx.x * blockDim.x; b0 < B; b0 += (long long)gridDim.x * blockDim.x) {
         const long long b = b0 + threadIdx.x;
@@ -131,10 +134,23 @@ count_kernel(const FieldView f, const float *__restrict__ o_in, const float *__r
             march_init(f, m);
             unsigned tested = 0;
             float p[3];
+            uint32_t *mrow = mask ? mask + (size_t)b * mw : nullptr;
+            uint32_t word = 0;
+            int wi = -1;
             while (march_next(f, f.t_tab, m, p, 1 << 30, tested) == MARCH_SAMPLE) {
                 ++n;
+                if (mrow) {
+                    const int w = m.step >> 5;
+                    if (w != wi) {
+                        if (wi >= 0) mrow[wi] = word;
+                        wi = w;
+                        word = 0u;
+                    }
+                    word |= 1u << (m.step & 31);
+                }
                 ++m.step;
             }
+            if (mrow && wi >= 0) mrow[wi] = word;
         }
         int incl = n;
 #pragma unroll
@@ -154,8 +170,23 @@ count_kernel(const FieldView f, const float *__restrict__ o_in, const float *__r
 
 __global__ void __launch_bounds__(128)
 emit_kernel(const FieldView f, const float *__restrict__ o_in, const float *__restrict__ d_in, int B,
-            const long long *__restrict__ off, const int *__restrict__ cnt, int2 *__restrict__ rec) {
+            const long long *__restrict__ off, const int *__restrict__ cnt, int2 *__restrict__ rec,
+            const uint32_t *__restrict__ mask, int mw) {
     for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < B; b += (long long)gridDim.x * blockDim.x) {
+        if (mask) {  // the steps count_kernel found, in order, from its bits
+            const uint32_t *mrow = mask + (size_t)b * mw;
+            long long q = off[b];
+            const long long end = q + cnt[b];
+            for (int w = 0; w < mw && q < end; ++w) {
+                uint32_t x = __ldg(mrow + w);
+                while (x) {
+                    if (VRN_CHECKED && !vrn_check(f.check, q < end, kCheckRecord)) break;
+                    rec[q++] = make_int2((int)b, 32 * w + __ffs(x) - 1);
+                    x &= x - 1u;
+                }
+            }
+            continue;
+        }
         MarchRay m;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -548,7 +579,14 @@ struct TrainScratch {
     long long scap = 0, fcap = 0, dcap = 0;
     unsigned long long *total = nullptr;   // device counter of records
     unsigned long long *total_h = nullptr; // pinned host copy
+    uint32_t *mask = nullptr;              // per ray: bits of its evaluated steps (count -> emit)
+    long long mask_cap = 0;                // words allocated
+    bool mask_valid = false;               // the last count pass wrote the bits
 };
+
+// The step bits of count_kernel cost S/8 bytes per ray; above this many bytes
+// for a pass, emit marches the rays again instead.
+constexpr long long kMaskBytesMax = 1ll << 30;
 
 static int ensure_train(vrnerf_field *F, int B) {
     cudaError_t e = cudaSuccess;
@@ -613,6 +651,7 @@ void release_train_scratch(vrnerf_field *F) {
     cudaFree(S->sc);
     cudaFree(S->feat);
     cudaFree(S->dfeat);
+    cudaFree(S->mask);
     cudaFree(S->total);
     if (S->total_h) cudaFreeHost(S->total_h);
     delete S;
@@ -636,9 +675,24 @@ static int count_pass(vrnerf_field *F, TrainScratch &S, const float *o, const fl
                       long long *n) {
     int blocks = 0;
     cudaError_t e = cudaMemsetAsync(S.total, 0, sizeof(unsigned long long), st);
+    // step bits for emit, when they fit (else emit marches again)
+    const int mw = (F->view.S + 31) / 32;
+    const long long words = (long long)B * mw;
+    if (words * 4 <= kMaskBytesMax && words > S.mask_cap) {
+        cudaFree(S.mask);
+        S.mask = nullptr;
+        S.mask_cap = 0;
+        if (cudaMalloc(&S.mask, (size_t)words * 4) == cudaSuccess)
+            S.mask_cap = words;
+        else
+            cudaGetLastError();  // no bits this time: emit marches again
+    }
+    uint32_t *mask = words <= S.mask_cap ? S.mask : nullptr;
+    if (e == cudaSuccess && mask) e = cudaMemsetAsync(mask, 0, (size_t)words * 4, st);
+    S.mask_valid = mask != nullptr;
     if (e == cudaSuccess) e = grid_for(count_kernel, 128, 0, B, blocks);
     if (e == cudaSuccess) {
-        count_kernel<<<blocks, 128, 0, st>>>(F->view, o, d, B, S.cnt, S.off, S.total);
+        count_kernel<<<blocks, 128, 0, st>>>(F->view, o, d, B, S.cnt, S.off, S.total, mask, mw);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(S.total_h, S.total, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
@@ -685,7 +739,8 @@ static int samples_pass(vrnerf_field *F, TrainScratch &S, const float *o, const 
     if (n > 0) {
         e = grid_for(emit_kernel, 128, 0, Bc, blocks);
         if (e == cudaSuccess) {
-            emit_kernel<<<blocks, 128, 0, st>>>(f, o, d, Bc, S.off, S.cnt, S.rec);
+            emit_kernel<<<blocks, 128, 0, st>>>(f, o, d, Bc, S.off, S.cnt, S.rec, S.mask_valid ? S.mask : nullptr,
+                                                (f.S + 31) / 32);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess && tc_bwd) {

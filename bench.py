@@ -45,8 +45,8 @@ STEREO_BUDGET_MS = 1000.0 / 36.0  # one frame at the 36 Hz the paper's demo sust
 # frame). NCU_TRAFFIC_CURRENT says whether the kernel is unchanged since that
 # capture; when it is not, the bench line reports traffic null and the old
 # figure beside it.
-NCU_TRAFFIC_BYTES = 53212928 + 25871616
-NCU_TRAFFIC_CURRENT = False  # captured before the bounds-check option touched the kernel's parameters
+NCU_TRAFFIC_BYTES = 53354752 + 25656832
+NCU_TRAFFIC_CURRENT = True  # captured on the current kernel (per-axis distance field)
 
 
 def parse():
@@ -612,9 +612,8 @@ def main():
                      "unit": "GB/s", "frac": round(achieved / hbm_peak, 5),
                      "traffic": (NCU_TRAFFIC_BYTES if NCU_TRAFFIC_CURRENT and precision_name == "fp16"
                                  and args.variant == "room" else None),
-                     "traffic_last_measured": NCU_TRAFFIC_BYTES,
-                     "traffic_note": ("ncu DRAM bytes of one launch, taken before the kernel last changed "
-                                      "(its parameter block gained the bounds-check pointer)"),
+                     "traffic_note": ("ncu dram__bytes_read + dram__bytes_write of one 2048^2 fp16 launch "
+                                      "(the gather is served from L2)"),
                      "peak_kind": peak_kind, "kernel": "render (fused march+gather+MLP+composite)"},
         "gpu_launches": args.steps,
         "clocks": clocks,

@@ -300,9 +300,9 @@ serve_kernel(const FieldView f, ServeView *__restrict__ ring, const ServeCtl *__
                         s_quit = 1;
                         break;
                     }
-                    const unsigned st = atomicAdd(idle, 0u);
+                    const unsigned st = ld_acquire_gpu_u32(idle);
                     if (st & kQuit) { s_quit = 1; break; }
-                    if (atomicAdd(cursor, 0u) < ld_acquire_gpu_u32(&ctl->n_views)) {
+                    if (ld_acquire_gpu_u32(cursor) < ld_acquire_gpu_u32(&ctl->n_views)) {
                         // back to work: one unconditional decrement (a compare-and-swap
                         // here made hundreds of waking CTAs retry against each other);
                         // a launch already quitting takes this CTA with it

@@ -44,12 +44,54 @@ struct TcImage {
 };
 
 struct TcShared {
-    unsigned char *w;     // weight image
-    unsigned char *act;   // 128 x 64 operand tile
-    uint64_t *mbar;
+    unsigned char *w;     // weight image (shared by the CTA's tiles)
+    unsigned char *act;   // this tile's 128 x 64 operand tile
+    uint64_t *mbar;       // this tile's mbarrier
     volatile int *abort;
-    uint32_t tbase;       // TMEM base address (lane 0, column 0)
+    uint32_t tbase;       // this tile's TMEM columns (lane 0)
+    uint32_t talloc;      // the CTA's TMEM allocation and its columns
+    uint32_t tcols;
+    int bar;              // named barrier of the tile's 128 threads (0: the whole CTA of one tile)
 };
+
+// The tile's 128 threads meet (a CTA of one tile: the whole CTA). Barrier
+// ids are immediates, so that the kernel reserves only the barriers it uses.
+__device__ __forceinline__ void tile_sync(int bar) {
+    switch (bar) {
+    case 0: asm volatile("bar.sync 0, 128;" ::: "memory"); break;
+    case 1: asm volatile("bar.sync 1, 128;" ::: "memory"); break;
+    case 2: asm volatile("bar.sync 2, 128;" ::: "memory"); break;
+    case 3: asm volatile("bar.sync 3, 128;" ::: "memory"); break;
+    default: asm volatile("bar.sync 4, 128;" ::: "memory"); break;
+    }
+}
+
+// bar.red.or over the tile's 128 threads: true if any of them passes true.
+template <int ID>
+__device__ __forceinline__ bool tile_sync_or_id(bool pred) {
+    int r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.s32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, %2, 128, p;\n\t"
+        "selp.s32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((int)pred), "n"(ID)
+        : "memory");
+    return r != 0;
+}
+__device__ __forceinline__ bool tile_sync_or(int bar, bool pred) {
+    switch (bar) {
+    case 0: return tile_sync_or_id<0>(pred);
+    case 1: return tile_sync_or_id<1>(pred);
+    case 2: return tile_sync_or_id<2>(pred);
+    case 3: return tile_sync_or_id<3>(pred);
+    default: return tile_sync_or_id<4>(pred);
+    }
+}
+
+// Row of this thread in its tile, and whether it issues the tile's MMAs.
+__device__ __forceinline__ int tile_row() { return threadIdx.x & (kTcThreads - 1); }
 
 template <int FMT>
 __device__ __forceinline__ uint32_t pack2(float a, float b) {
@@ -172,8 +214,8 @@ template <int K, int N>
 __device__ __forceinline__ void run_layer_e4m3(const TcShared &S, int w_off, uint32_t &phase, bool &ok) {
     tc::fence_proxy_async();
     tc::fence_before_sync();
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    tile_sync(S.bar);
+    if (tile_row() == 0) {
         tc::fence_after_sync();
         issue_layer_e4m3<K, N>(tc::smem_u32(S.act), tc::smem_u32(S.w) + w_off, S.tbase);
         tc::mma_commit(S.mbar);
@@ -223,8 +265,8 @@ template <int K, int N, int FMT>
 __device__ __forceinline__ void run_layer(const TcShared &S, int w_off, uint32_t &phase, bool &ok) {
     tc::fence_proxy_async();
     tc::fence_before_sync();
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    tile_sync(S.bar);
+    if (tile_row() == 0) {
         tc::fence_after_sync();
         issue_layer<K, N, FMT>(tc::smem_u32(S.act), tc::smem_u32(S.w) + w_off, S.tbase);
         tc::mma_commit(S.mbar);
@@ -243,7 +285,7 @@ __device__ __forceinline__ void tc_mlp(const TcShared &S, const float *feat, con
                                        float density_bias, float &sigma, float rgb[3], uint32_t &phase,
                                        bool &ok) {
     using W = TcW<D>;
-    const int r = threadIdx.x;
+    const int r = tile_row();
     const uint32_t taddr = S.tbase + ((uint32_t)(r & ~31) << 16);
     if (feat) {
         uint32_t pk[D / 2];
@@ -321,7 +363,7 @@ __device__ __forceinline__ void tc_mlp_fp8(const TcShared &S, const float *feat,
                                            float density_bias, float &sigma, float rgb[3], uint32_t &phase,
                                            bool &ok) {
     using W = TcW8<D>;
-    const int r = threadIdx.x;
+    const int r = tile_row();
     const uint32_t taddr = S.tbase + ((uint32_t)(r & ~31) << 16);
     const float *inv_w = reinterpret_cast<const float *>(S.w + W::scales);
     if (feat) {
@@ -417,37 +459,50 @@ __device__ __forceinline__ void tc_mlp_any(const TcShared &S, const float *feat,
         tc_mlp<D, FMT>(S, feat, dir, density_bias, sigma, rgb, phase, ok);
 }
 
-// Shared-memory carve-up, weight upload, mbarrier and TMEM set-up.
-template <int D, int FMT = 0>
+// Shared-memory carve-up, weight upload, mbarriers and TMEM set-up for a
+// CTA of NT tiles (NT x 128 threads): one weight image, then NT activation
+// tiles, the sample table, and the misc block (NT mbarriers, the TMEM
+// holder, the abort flag). Tile g = threadIdx.x / 128 gets activation tile
+// g, mbarrier g, TMEM columns [64 g, 64 g + 64) and named barrier g + 1
+// (barrier 0, the whole CTA, when NT = 1).
+template <int D, int FMT = 0, int NT = 1>
 __device__ __forceinline__ TcShared tc_setup(unsigned char *smem, const uint4 *__restrict__ wimg,
                                              float *&sT, const float *__restrict__ t_tab, int S_steps) {
     using W = TcImage<D, FMT>;
+    constexpr uint32_t kCols = NT == 1 ? kTmemCols : (NT == 2 ? 128u : 256u);
+    static_assert(NT == 1 || NT == 2 || NT == 4, "1, 2 or 4 tiles per CTA");
+    const int g = NT == 1 ? 0 : (int)(threadIdx.x >> 7);
     TcShared S;
     S.w = smem;
-    S.act = smem + ((W::bytes + 1023) & ~1023);
-    sT = reinterpret_cast<float *>(S.act + 128 * 64 * 2);
+    unsigned char *act0 = smem + ((W::bytes + 1023) & ~1023);
+    S.act = act0 + g * (128 * 64 * 2);
+    sT = reinterpret_cast<float *>(act0 + NT * (128 * 64 * 2));
     const int nt = S_steps + 1;
     unsigned char *misc = reinterpret_cast<unsigned char *>(sT + ((nt + 3) & ~3));
-    S.mbar = reinterpret_cast<uint64_t *>(misc);
-    uint32_t *holder = reinterpret_cast<uint32_t *>(misc + 8);
-    S.abort = reinterpret_cast<volatile int *>(misc + 12);
+    uint64_t *mbars = reinterpret_cast<uint64_t *>(misc);
+    S.mbar = mbars + g;
+    uint32_t *holder = reinterpret_cast<uint32_t *>(misc + 8 * NT);
+    S.abort = reinterpret_cast<volatile int *>(misc + 8 * NT + 4);
     for (int i = threadIdx.x; i < W::bytes / 16; i += blockDim.x)
         reinterpret_cast<uint4 *>(S.w)[i] = wimg[i];
     if (t_tab)
         for (int i = threadIdx.x; i < nt; i += blockDim.x) sT[i] = t_tab[i];
     if (threadIdx.x == 0) {
-        tc::mbar_init(S.mbar, 1);
+        for (int k = 0; k < NT; ++k) tc::mbar_init(mbars + k, 1);
         *S.abort = 0;
     }
     if (threadIdx.x < 32) {
-        tc::tmem_alloc(holder, kTmemCols);
+        tc::tmem_alloc(holder, kCols);
         tc::tmem_relinquish();
     }
     tc::fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    S.tbase = *holder;
+    S.talloc = *holder;
+    S.tcols = kCols;
+    S.tbase = S.talloc + (uint32_t)(64 * g);
+    S.bar = NT == 1 ? 0 : 1 + g;
     return S;
 }
 
@@ -456,7 +511,7 @@ __device__ __forceinline__ void tc_teardown(const TcShared &S, unsigned long lon
     __syncthreads();
     tc::fence_after_sync();
     if (threadIdx.x == 0 && *S.abort && status) atomicExch(status, (unsigned long long)(-VRNERF_ETIMEDOUT));
-    if (threadIdx.x < 32) tc::tmem_dealloc(S.tbase, kTmemCols);
+    if (threadIdx.x < 32) tc::tmem_dealloc(S.talloc, S.tcols);
 }
 
 
@@ -466,11 +521,14 @@ __global__ void build_tc_image_kernel(const float *__restrict__ mlp, int D, int 
 // fp32 W1..W5 -> the image of TcW8<D> (one CTA per weight matrix).
 __global__ void build_tc_image_fp8_kernel(const float *__restrict__ mlp, int D, unsigned char *__restrict__ img);
 
-inline size_t tc_smem_bytes(int D, int S_steps) {
+inline size_t tc_smem_bytes(int D, int S_steps, int NT = 1) {
     const size_t wb = (size_t)(64 * D * 2 + 16 * 64 * 2 + 64 * 32 * 2 + 64 * 64 * 2 + 16 * 64 * 2);
-    size_t b = ((wb + 1023) & ~(size_t)1023) + 128 * 64 * 2 + sizeof(float) * (size_t)((S_steps + 1 + 3) & ~3) + 64;
-    // at most 512 / kTmemCols CTAs per SM, so tcgen05.alloc never waits
-    const size_t floor_bytes = (size_t)(232448 / (512 / kTmemCols)) + 1024;
+    size_t b = ((wb + 1023) & ~(size_t)1023) + (size_t)NT * 128 * 64 * 2 +
+               sizeof(float) * (size_t)((S_steps + 1 + 3) & ~3) + 64;
+    // at most 512 / cols CTAs per SM by shared memory (228 KB usable, 1 KB
+    // reserved per CTA), so that tcgen05.alloc never waits
+    const size_t cols = NT == 1 ? kTmemCols : (NT == 2 ? 128 : 256);
+    const size_t floor_bytes = (size_t)233472 / (512 / cols + 1) - 1024 + 16;
     return b > floor_bytes ? b : floor_bytes;
 }
 
@@ -500,7 +558,7 @@ inline cudaError_t ensure_tc_image(vrnerf_field *F, int fmt, cudaStream_t st) {
 // runtime's occupancy query under-reports kernels that allocate TMEM), capped
 // so that the CTAs on one SM never ask for more than its 512 TMEM columns.
 template <typename K>
-inline cudaError_t prepare_tc(K kern, size_t smem, int &blocks_per_sm) {
+inline cudaError_t prepare_tc(K kern, size_t smem, int &blocks_per_sm, int NT = 1) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaFuncAttributes fa;
@@ -509,11 +567,12 @@ inline cudaError_t prepare_tc(K kern, size_t smem, int &blocks_per_sm) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
     cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    const int regs = ((fa.numRegs + 7) / 8) * 8 * kTcThreads;
+    const int regs = ((fa.numRegs + 7) / 8) * 8 * kTcThreads * NT;
     const int by_regs = regs > 0 ? regs_sm / regs : 8;
     const int by_smem = smem_sm / (int)(smem + fa.sharedSizeBytes + 1024);
     blocks_per_sm = by_regs < by_smem ? by_regs : by_smem;
-    if (blocks_per_sm > (int)(512 / kTmemCols)) blocks_per_sm = (int)(512 / kTmemCols);
+    const int cols = NT == 1 ? (int)kTmemCols : (NT == 2 ? 128 : 256);
+    if (blocks_per_sm > 512 / cols) blocks_per_sm = 512 / cols;
     if (blocks_per_sm < 1) return cudaErrorInvalidConfiguration;
     return cudaSuccess;
 }

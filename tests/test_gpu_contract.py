@@ -246,11 +246,26 @@ def test_contracted_prune(V, unit):
     _, alpha, _ = V.vrnerf_prune(f, cams, 2, 0.0, apply=False, want_alpha=True)
     alpha = alpha.reshape(occ.shape)
     assert (alpha[~occ] == 0).all()
-    # the outer voxels' camera distance comes from sampled points: fp32 against
-    # fp64 positions can pick a neighbouring sample interval only where the
-    # distance sits on a sample boundary, so compare element-wise and count
-    err = np.abs(alpha - alpha_ref) <= 1e-4 * alpha_ref + 1e-6
-    assert err[occ].mean() > 0.995, err[occ].mean()
+    # Outside the inner cube the k^3 lattice points are mapped back through the
+    # inverse contraction, whose conditioning near the cube's edge amplifies
+    # the fp32 rounding of a point, and their camera distance comes from
+    # sampled points: fp32 against fp64 can pick a neighbouring sample interval
+    # where the distance sits on a sample boundary. So every voxel matches
+    # within 1e-4, or its optical depth -ln(1 - alpha) differs from the
+    # oracle's by the ratio q of adjacent exponential intervals
+    # (delta_{i+1} / delta_i = q), or, outside the inner cube only, by 1e-3.
+    ok = np.abs(alpha - alpha_ref) <= 1e-4 * alpha_ref + 1e-6
+    assert ok[occ].mean() > 0.99, ok[occ].mean()
+    q = (cfg.t_far / cfg.t_near) ** (1.0 / cfg.max_steps)
+    inner = np.zeros(occ.shape, bool)
+    inner[8:24, 8:24, 8:24] = True  # the inner cube |x|_inf <= 1 of the 32^3 contracted grid
+    bad = occ & ~ok
+    tau = -np.log1p(-alpha[bad].astype(np.float64))
+    tau_ref = -np.log1p(-alpha_ref[bad])
+    ratio = tau / tau_ref
+    neighbour = (np.abs(ratio - q) <= 1e-3 * q) | (np.abs(ratio - 1 / q) <= 1e-3 / q)
+    near = (np.abs(ratio - 1) <= 1e-3) & ~inner[bad]
+    assert (neighbour | near).all(), (bad.sum(), ratio[~(neighbour | near)][:5])
     f.close()
 
 

@@ -35,7 +35,7 @@
 namespace vrn {
 
 #ifndef VRN_LOOKAHEAD
-#define VRN_LOOKAHEAD 16
+#define VRN_LOOKAHEAD 32
 #endif
 constexpr int kLookahead = VRN_LOOKAHEAD;  // samples a lane may hold found ahead of shading
 

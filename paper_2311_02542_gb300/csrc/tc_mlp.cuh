@@ -470,7 +470,7 @@ __device__ __forceinline__ TcShared tc_setup(unsigned char *smem, const uint4 *_
                                              float *&sT, const float *__restrict__ t_tab, int S_steps) {
     using W = TcImage<D, FMT>;
     constexpr uint32_t kCols = NT == 1 ? kTmemCols : (NT == 2 ? 128u : 256u);
-    static_assert(NT == 1 || NT == 2 || NT == 4, "1, 2 or 4 tiles per CTA");
+    static_assert(NT >= 1 && NT <= 4, "1 to 4 tiles per CTA");
     const int g = NT == 1 ? 0 : (int)(threadIdx.x >> 7);
     TcShared S;
     S.w = smem;

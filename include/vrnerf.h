@@ -414,7 +414,7 @@ typedef struct {
  * continuous batching on one GPU). Starts a server for `field` on its
  * device: a scheduler thread, two streams and an output arena of
  * hbm_budget_bytes on the device. A request is admitted when its output
- * (12 bytes per ray) fits in the arena's free space and the in-flight views
+ * (12 bytes per ray; none for an output in pinned host memory) fits in the arena's free space and the in-flight views
  * fit the server's view ring (256); otherwise it waits in arrival order. precision: VRNERF_FP16 or VRNERF_BF16. The server
  * owns the field until vrnerf_server_destroy: make no other call on the
  * field meanwhile. EINVAL, ENOMEM. */
@@ -423,9 +423,14 @@ int vrnerf_server_create(vrnerf_field *field, uint64_t hbm_budget_bytes, int32_t
 
 /* Queues a request of n_views (1..16) views; every array is host memory and
  * is copied, except out_host ([sum W*H][3] linear colour, may be NULL),
- * which must stay valid until vrnerf_poll reports the request. Non-blocking.
- * *ticket identifies the request. EINVAL (bad view, or output larger than
- * the whole budget), EBUSY (1024 requests already waiting). */
+ * which must stay valid until vrnerf_poll reports the request. When out_host
+ * is pinned (page-locked) host memory that the device can address, the
+ * kernel writes the pixels into it directly: such a request takes no part
+ * of the HBM budget and has no copy-out (a cancelled request that is
+ * already running may still write its pixels); other outputs are rendered
+ * into the budget's arena and copied out. Non-blocking. *ticket identifies
+ * the request. EINVAL (bad view, or an arena output larger than the whole
+ * budget), EBUSY (1024 requests already waiting). */
 int vrnerf_submit(vrnerf_server *server, int32_t n_views, const float *cameras_host,
                   const float *intrinsics_host, const int32_t *resolution_host, float *out_host,
                   uint64_t *ticket);
@@ -450,7 +455,9 @@ int vrnerf_submit_deadline(vrnerf_server *server, int32_t n_views, const float *
 int vrnerf_poll(vrnerf_server *server, uint64_t ticket, int32_t timeout_ms, double *latency_ms);
 
 /* Cancels a request: a waiting request is dropped, a running one finishes on
- * the GPU but its output is not copied. Poll it to release the ticket. */
+ * the GPU but its output is not copied (an output in pinned host memory,
+ * written directly, may already hold pixels). Poll it to release the
+ * ticket. */
 int vrnerf_cancel(vrnerf_server *server, uint64_t ticket);
 
 /* Latency percentiles and throughput of the requests finished so far. */

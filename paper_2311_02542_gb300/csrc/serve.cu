@@ -161,7 +161,7 @@ serve_kernel(const FieldView f, ServeView *__restrict__ ring, const ServeCtl *__
     auto flush = [&]() {
         if (cnt && cnt_view >= 0) {
             ServeView *sv = ring + cnt_view;
-            __threadfence();  // this thread's pixels before its count
+            __threadfence_system();  // this thread's pixels (device or mapped host memory) before its count
             const unsigned long long total =
                 (unsigned long long)__ldcg(&sv->tiles_x) * ((__ldcg(&sv->H) + kTileH - 1) / kTileH) * 32ull;
             if (atomicAdd(&sv->finished, (unsigned long long)cnt) + cnt == total) {
@@ -413,6 +413,8 @@ struct Req {
     std::vector<float> c2w, K;
     std::vector<int32_t> res;
     float *out_host = nullptr;
+    float *out_dev = nullptr;     // out_host as the GPU addresses it, when it is mapped pinned memory
+    bool zero_copy = false;       // the kernel writes the output straight into out_host
     uint64_t rays = 0, bytes = 0;
     size_t arena_off = 0;
     Clock::time_point t_submit, t_admit, t_gpu, t_done;
@@ -538,7 +540,7 @@ bool vrnerf_server::admit_locked(std::vector<int> &new_views) {
         // a ring entry is rewritten only long after its previous view finished
         if (n_views + q->n - oldest_live_view >= (unsigned)kRing / 2) break;
         size_t off = 0;
-        if (!arena.alloc(q->bytes, off)) break;  // HBM budget: wait for earlier requests
+        if (!q->zero_copy && !arena.alloc(q->bytes, off)) break;  // HBM budget: wait for earlier requests
         pending.erase(pick);
         q->t_admit = now;
         q->arena_off = off;
@@ -558,7 +560,7 @@ bool vrnerf_server::admit_locked(std::vector<int> &new_views) {
                 (unsigned long long)sv.tiles_x * ((sv.H + kTileH - 1) / kTileH) * 32ull;
             sv.slot_begin = published;
             sv.slot_end = published + slots;
-            sv.out = reinterpret_cast<float *>(arena_d + off) + 3 * pix_off;
+            sv.out = q->zero_copy ? q->out_dev + 3 * pix_off : reinterpret_cast<float *>(arena_d + off) + 3 * pix_off;
             sv.done = done_d + idx;
             sv.taken = 0;
             sv.finished = 0;
@@ -626,18 +628,18 @@ void vrnerf_server::poll_completions() {
                     if (__atomic_load_n(&done_h[idx], __ATOMIC_ACQUIRE) < view_slots[idx]) all = false;
                 if (all) {
                     q->t_gpu = Clock::now();
-                    if (q->out_host)
+                    if (q->out_host && !q->zero_copy)
                         cudaMemcpyAsync(q->out_host, arena_d + q->arena_off, q->rays * 12, cudaMemcpyDeviceToHost, cst);
-                    cudaEventRecord(q->copied, cst);
+                    if (!q->zero_copy) cudaEventRecord(q->copied, cst);
                     q->state = 2;
                 }
             }
-            if (q->state == 2 && cudaEventQuery(q->copied) == cudaSuccess) finished.push_back(q);
+            if (q->state == 2 && (q->zero_copy || cudaEventQuery(q->copied) == cudaSuccess)) finished.push_back(q);
         }
         for (Req *q : finished) {
             q->t_done = Clock::now();
             q->state = q->cancel ? 4 : 3;
-            arena.release(q->arena_off, q->bytes);
+            if (!q->zero_copy) arena.release(q->arena_off, q->bytes);
             for (int idx : q->ring_idx) view_req[idx] = nullptr;
             inflight.erase(std::find(inflight.begin(), inflight.end(), q));
             latencies_ms.push_back(std::chrono::duration<double, std::milli>(q->t_done - q->t_submit).count());
@@ -752,7 +754,19 @@ static int submit_impl(vrnerf_server *S, int32_t n_views, const float *cameras_h
         q->rays += (uint64_t)q->res[2 * v] * q->res[2 * v + 1];
     }
     q->bytes = q->rays * 12;
-    if (q->bytes > S->budget) {
+    if (out_host) {
+        // pinned host memory the GPU can address: the kernel writes the
+        // pixels there itself (no arena slice, no copy-out)
+        cudaPointerAttributes pa;
+        if (cudaPointerGetAttributes(&pa, out_host) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+            pa.devicePointer) {
+            q->zero_copy = true;
+            q->out_dev = static_cast<float *>(pa.devicePointer);
+        } else {
+            cudaGetLastError();
+        }
+    }
+    if (!q->zero_copy && q->bytes > S->budget) {
         delete q;
         return fail(VRNERF_EINVAL, "request needs %llu bytes, more than the server's HBM budget",
                     (unsigned long long)q->rays * 12);

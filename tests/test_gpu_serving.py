@@ -219,3 +219,37 @@ def test_serving_deadlines_order_and_shed(V, room):
         srv.submit(c2w, K, res, None, deadline_ms=-1.0)
     srv.close()
     f.close()
+
+
+def test_serving_writes_pinned_outputs_directly(V, room):
+    """An output buffer in pinned host memory is written by the kernel itself:
+    it takes no part of the HBM budget (here 1 MiB, far below the outputs)
+    and needs no copy-out; the images equal rendering alone. A pageable
+    buffer of the same size is still refused against that budget."""
+    f = V.Field(room.cfg, room.grid, room.mlp, room.occ_bits)
+    srv = V.Server(f, 1 << 20, "fp16")
+    reqs = _mix(room, np.random.default_rng(47))[:5]
+    outs, tickets = [], []
+    for c2w, K, res in reqs:
+        out = torch.empty((int((res[:, 0] * res[:, 1]).sum()), 3), dtype=torch.float32, pin_memory=True).numpy()
+        out.fill(np.nan)
+        outs.append(out)
+        tickets.append(srv.submit(c2w, K, res, out))
+    for t in tickets:
+        srv.poll(t, 20000)
+    for (c2w, K, res), got in zip(reqs, outs):
+        ref = _alone(V, f, c2w, K, res)
+        assert np.isfinite(got).all()
+        assert np.all(np.abs(got - ref) <= TC_RTOL * np.abs(ref) + TC_ATOL)
+    st = srv.stats()
+    assert st["completed"] == len(reqs) and st["copy_p99_ms"] < 1.0
+    c2w, K, res = S.camera_room(room.occ, room.cfg, 2, 512, 512)   # 3 MB of output
+    with pytest.raises(V.VrnerfError) as e:
+        srv.submit(c2w, K, res, np.zeros((512 * 512, 3), np.float32))
+    assert e.value.code == V.EINVAL
+    pinned = torch.empty((512 * 512, 3), dtype=torch.float32, pin_memory=True).numpy()
+    srv.poll(srv.submit(c2w, K, res, pinned), 20000)
+    ref = _alone(V, f, c2w, K, res)
+    assert np.all(np.abs(pinned - ref) <= TC_RTOL * np.abs(ref) + TC_ATOL)
+    srv.close()
+    f.close()

@@ -645,15 +645,35 @@ __device__ __forceinline__ void scatter_grid_grad(const FieldView &f, const floa
         if (act) level_corners(f, l, p, idx, fr);
         float2 *gbase = reinterpret_cast<float2 *>(grid_grad) + (size_t)l * (f.T_mask + 1u);
         const bool dense = (f.dense_mask >> l) & 1u;
+        if (!dense) {
+            // hashed level: the x-adjacent corners (b, b + 1) of a cell often fall on
+            // the two halves of one aligned 16-byte pair of entries (indices that
+            // differ only in bit 0), which one four-wide atomic updates
+            if (act) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float wyz = (j & 1 ? fr[1] : 1.0f - fr[1]) * (j & 2 ? fr[2] : 1.0f - fr[2]) * wl;
+                    const float c0 = (1.0f - fr[0]) * wyz, c1 = fr[0] * wyz;
+                    const float2 g0 = make_float2(c0 * dfeat[2 * l], c0 * dfeat[2 * l + 1]);
+                    const float2 g1 = make_float2(c1 * dfeat[2 * l], c1 * dfeat[2 * l + 1]);
+                    const uint32_t i0 = idx[2 * j], i1 = idx[2 * j + 1];
+                    if ((i0 ^ i1) == 1u) {
+                        const float4 v = (i0 & 1u) ? make_float4(g1.x, g1.y, g0.x, g0.y)
+                                                   : make_float4(g0.x, g0.y, g1.x, g1.y);
+                        atomicAdd(reinterpret_cast<float4 *>(gbase + (i0 & ~1u)), v);
+                    } else {
+                        atomicAdd(gbase + i0, g0);
+                        atomicAdd(gbase + i1, g1);
+                    }
+                }
+            }
+            continue;
+        }
 #pragma unroll
         for (int b = 0; b < 8; ++b) {
             const float cw = (b & 1 ? fr[0] : 1.0f - fr[0]) * (b & 2 ? fr[1] : 1.0f - fr[1]) *
                              (b & 4 ? fr[2] : 1.0f - fr[2]) * wl;
             float gx = act ? cw * dfeat[2 * l] : 0.0f, gy = act ? cw * dfeat[2 * l + 1] : 0.0f;
-            if (!dense) {
-                if (act) atomicAdd(gbase + idx[b], make_float2(gx, gy));
-                continue;
-            }
             const uint32_t key = act ? idx[b] : 0xffffffffu;
             const uint32_t prev = __shfl_up_sync(FULL, key, 1);
             const bool head = lane == 0 || prev != key;

@@ -7,6 +7,14 @@
 // (row group g, column group j) sits at g * (K / 8) * 128 + j * 128 bytes and
 // row i of it at + 16 i. In the descriptor that is LBO = 128 bytes (next core
 // matrix along K) and SBO = (K / 8) * 128 bytes (next group of 8 rows).
+//
+// The same tile read with the instruction descriptor's transpose bit set is
+// an MN-major operand: its rows are then the K index and its 16-byte core-
+// matrix rows hold 8 consecutive M (or N) elements. For that no-swizzle form
+// the descriptor's roles swap: LBO = the stride between groups of 8 K rows
+// ((K_tile / 8) * 128 for a tile of row length K_tile) and SBO = 128 bytes
+// (next 8 M or N elements), measured with known matrices on sm_103a (the
+// other assignment gives wrong products).
 #pragma once
 #include <cstdint>
 
@@ -36,6 +44,12 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
 __host__ __device__ constexpr uint32_t idesc_f16(int N, int fmt) {
     return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(N >> 3) << 17) |
            ((uint32_t)(128 >> 4) << 24);
+}
+
+// Transpose bits of the instruction descriptor: bit 15 makes A MN-major,
+// bit 16 makes B MN-major (K-major when clear).
+__host__ __device__ constexpr uint32_t idesc_mn(bool a_mn, bool b_mn) {
+    return ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16);
 }
 
 // Instruction descriptor of kind::f8f6f4, E4M3 A and B, fp32 accumulation,

@@ -2,7 +2,7 @@
 // tensor cores, bf16 operands and fp32 accumulation (the mixed-precision
 // option of the training path; the fp32 CUDA-core kernel stays the default).
 //
-// One persistent CTA per SM walks tiles of 128 samples (row r = thread r):
+// Persistent CTAs (two per SM) walk tiles of 128 samples (row r = thread r):
 //  forward recompute   F (bf16 features kept by the forward pass)
 //                                              -> L1: H  = relu(F W1^T)
 //                                              -> L2: O  = H W2^T
@@ -14,15 +14,20 @@
 //                      dO = dX[:16] + e_0 dL/do_0   (dL/dsigma sigma, fp32, from the ray pass)
 //                      dW2 += dO^T H,                   dH  = relu'(H) (dO W2)
 //                      dW1 += dH^T F,                   dF  = dH W1  -> hash-grid scatter
-// Every product is a 128-row MMA: the data gradients take the activations'
-// row tiles as A and a transposed weight image as B; the weight gradients
-// sum over the tile's samples, so their A is the delta tile transposed (rows
-// = output units, K = the 128 samples) and their B the input tile
-// transposed, both written by the epilogues as columns. The weight gradients
-// accumulate in TMEM across all tiles of the CTA and are added to global
-// memory once at the end. The transposed deltas of one batch share one
-// buffer (dH2^T in rows 0..63, dZ^T in rows 64..66): an MMA's rows that
-// belong to another product land in TMEM lanes its result does not use.
+// Every product is a 128-row MMA on tiles that the epilogues write once, as
+// rows ([128 samples][units], 16-byte stores). The forward and data-gradient
+// products read them K-major; the weight gradients sum over the samples, so
+// they read the same tiles MN-major (A = the delta tile, rows = output units,
+// K = samples; B = the input tile), and the data gradients read the forward
+// weight image MN-major as W instead of W^T: no transposed copies. dH2 and dZ
+// share one [128][80] tile (units 0..63 and 64..66), so one A operand serves
+// dW4 and dW5; an MMA's rows past a tile's units read the next rows of shared
+// memory and land in TMEM lanes that its result does not use.
+// dW1, dW3, dW4 accumulate in TMEM across all tiles of the CTA; dW2 and dW5
+// go to one scratch accumulator per tile and are added into fp32 sums in
+// shared memory, which keeps the CTA at 256 TMEM columns and ~110 KB of shared
+// memory: two CTAs share an SM, so one CTA's epilogues overlap the other's
+// MMAs. The sums reach global memory once at the end.
 #include "field.h"
 #include "tc_mlp.cuh"
 
@@ -31,62 +36,76 @@ namespace vrn {
 namespace {
 
 constexpr int kTile = 128;
+constexpr int kBwdPerSm = 2;  // resident CTAs per SM (shared memory and TMEM are sized for two)
 
-// Transposed weight image (K-major B operands of the data-gradient MMAs):
-// W4^T [64 in][64 out], W3^T [32 in][64 out], W2^T [64 in][16 out], W1^T [D][64].
-template <int D>
-struct TcWT {
-    static constexpr int w4 = 0;
-    static constexpr int w3 = w4 + 64 * 64 * 2;
-    static constexpr int w2 = w3 + 32 * 64 * 2;
-    static constexpr int w1 = w2 + 64 * 16 * 2;
-    static constexpr int bytes = w1 + D * 64 * 2;
-};
-
-// Shared-memory carve-up of the backward CTA (bytes).
+// Shared-memory carve-up of the backward CTA (bytes). Every MN-major read of
+// a delta tile as a 128-row A operand runs past the tile's end by less than
+// 1 KB (rows = units beyond the tile's width); the buffer after it absorbs that.
 template <int D>
 struct BwdSm {
-    static constexpr int w = 0;                                        // forward image (bf16)
-    static constexpr int wt = (TcW<D>::bytes + 1023) & ~1023;          // transposed image
-    static constexpr int F = (wt + TcWT<D>::bytes + 1023) & ~1023;     // [128][D]
-    static constexpr int FT = F + kTile * D * 2;                        // [D][128]
-    static constexpr int H = FT + D * kTile * 2;                        // [128][64]: H, dH2, dH
-    static constexpr int HT = H + kTile * 64 * 2;                       // [64][128]
-    static constexpr int X = HT + 64 * kTile * 2;                       // [128][32]: X, dO [128][16]
-    static constexpr int XT = X + kTile * 32 * 2;                       // [32][128]
-    static constexpr int H1 = XT + 32 * kTile * 2;                      // [128][64]: H1, dH1
-    static constexpr int H1T = H1 + kTile * 64 * 2;                     // [64][128]
-    static constexpr int H2T = H1T + 64 * kTile * 2;                    // [64][128]
-    static constexpr int AT = H2T + 64 * kTile * 2;                     // [128][128] transposed deltas
-    static constexpr int misc = AT + kTile * kTile * 2;                 // mbarrier, TMEM holder, abort
+    static constexpr int w = 0;                                     // forward image (bf16)
+    static constexpr int F = (TcW<D>::bytes + 1023) & ~1023;        // [128][D]
+    static constexpr int H = F + kTile * D * 2;                     // [128][64]: H, then dH
+    static constexpr int X = H + kTile * 64 * 2;                    // [128][32]: X, then dO [128][16]
+    static constexpr int H1 = X + kTile * 32 * 2;                   // [128][64]: H1, then dH1
+    static constexpr int H2 = H1 + kTile * 64 * 2;                  // [128][64]
+    static constexpr int G = H2 + kTile * 64 * 2;                   // [128][80]: dH2 | dZ | 0
+    static constexpr int acc2 = G + kTile * 80 * 2;                 // fp32 dW2 [16][64]
+    static constexpr int acc5 = acc2 + 16 * 64 * 4;                 // fp32 dW5 [3][64]
+    static constexpr int w5 = acc5 + 3 * 64 * 4;                    // fp32 W5 [3][64]
+    static constexpr int misc = w5 + 3 * 64 * 4;                    // mbarrier, TMEM holder, abort
     static constexpr int bytes = misc + 64;
+    // a 128-row MN-major read of a [128][U] tile ends 2048 - (U / 8) * 128 bytes past it
+    static_assert(acc5 - acc2 >= 2048 - 80 / 8 * 128, "the overrun of G stays in acc2");
+    static_assert(X - H >= 2048 - 64 / 8 * 128 && H2 - H1 >= 2048 - 64 / 8 * 128, "overruns of dH, dH1");
+    static_assert(kTile * 32 * 2 >= kTile * 16 * 2 + 2048 - 16 / 8 * 128, "the overrun of dO stays in X");
 };
 
-// TMEM columns: the data products' accumulator and the weight gradients.
-constexpr uint32_t kColData = 0;    // 64 columns
-constexpr uint32_t kColW4 = 64;     // lanes 0..63  x 64
-constexpr uint32_t kColW2 = 128;    // lanes 0..15  x 64
-constexpr uint32_t kColW5 = 192;    // lanes 64..66 x 64
-constexpr uint32_t kColW1 = 256;    // lanes 0..63  x D
-constexpr uint32_t kColW3 = 288;    // lanes 0..63  x 32
-constexpr uint32_t kBwdCols = 512;
+// TMEM columns (256 per CTA, so that two CTAs fit the SM's 512).
+constexpr uint32_t kColData = 0;    // data products, 64 columns
+constexpr uint32_t kColScr = 64;    // dW5 (lanes 64..66) or dW2 (lanes 0..15) of the current tile
+constexpr uint32_t kColW4 = 128;    // lanes 0..63 x 64
+constexpr uint32_t kColW1 = 192;    // lanes 0..63 x D (D <= 32)
+constexpr uint32_t kColW3 = 224;    // lanes 0..63 x 32
+constexpr uint32_t kBwdCols = 256;
 
-__device__ __forceinline__ uint16_t bf16_bits(float v) { return __bfloat16_as_ushort(__float2bfloat16_rn(v)); }
+// One operand of an MMA: start address, descriptor strides and the byte step
+// to the next 16 values of K.
+struct Opnd {
+    uint32_t addr, lbo, sbo, kstep;
+    bool mn;
+};
 
-// element (row, col) of a K-major [rows][K] 16-bit tile
-__device__ __forceinline__ void put16(unsigned char *tile, int row, int col, int K, uint16_t v) {
-    *reinterpret_cast<uint16_t *>(tile + tc::kmajor_offset(row, col, K)) = v;
+// Tile [rows][U] (16-bit elements, row length U) read K-major: K runs along U.
+__device__ __forceinline__ Opnd kmaj(uint32_t addr, int U) {
+    return {addr, 128u, (uint32_t)(U / 8) * 128u, 256u, false};
+}
+// The same tile read MN-major: K runs along its rows, M or N along U.
+__device__ __forceinline__ Opnd mnmaj(uint32_t addr, int U) {
+    const uint32_t g = (uint32_t)(U / 8) * 128u;
+    return {addr, g, 128u, 2u * g, true};
 }
 
-// D[tmem] (+)= A[128 x K] * B[N x K]^T, both K-major in shared memory.
+// D[tmem] (+)= A[128 x K] * B[K x N], K a multiple of 16.
 template <int K, int N>
-__device__ __forceinline__ void issue_mma(uint32_t a, uint32_t b, uint32_t d, bool acc) {
-    constexpr uint32_t sbo = (K / 8) * 128;
-    constexpr uint32_t idesc = tc::idesc_f16(N, 1);
+__device__ __forceinline__ void issue(const Opnd &a, const Opnd &b, uint32_t d, bool acc) {
+    const uint32_t idesc = tc::idesc_f16(N, 1) | tc::idesc_mn(a.mn, b.mn);
 #pragma unroll
     for (int ks = 0; ks < K / 16; ++ks)
-        tc::mma_f16(d, tc::smem_desc(a + ks * 256, 128, sbo), tc::smem_desc(b + ks * 256, 128, sbo), idesc,
-                    (ks > 0 || acc) ? 1u : 0u);
+        tc::mma_f16(d, tc::smem_desc(a.addr + ks * a.kstep, a.lbo, a.sbo),
+                    tc::smem_desc(b.addr + ks * b.kstep, b.lbo, b.sbo), idesc, (ks > 0 || acc) ? 1u : 0u);
+}
+
+// Row r, units 8j..8j+7 of a [128][U] tile: one 16-byte store of bf16 values.
+__device__ __forceinline__ void store8(unsigned char *tile, int U, int r, int j, const float *v) {
+    uint4 w;
+    uint32_t *p = &w.x;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+        p[e] = *reinterpret_cast<const uint32_t *>(&b);
+    }
+    *reinterpret_cast<uint4 *>(tile + (r >> 3) * (U / 8) * 128 + j * 128 + (r & 7) * 16) = w;
 }
 
 struct Sync {
@@ -100,13 +119,13 @@ struct Sync {
 // that runs out sets s.abort; control flow stays the same for every thread
 // (the tile loop checks the flag CTA-wide).
 template <typename F>
-__device__ __forceinline__ void mma_batch(Sync &s, F issue) {
+__device__ __forceinline__ void mma_batch(Sync &s, F issue_fn) {
     tc::fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
     if (threadIdx.x == 0) {
         tc::fence_after_sync();
-        issue();
+        issue_fn();
         tc::mma_commit(s.mbar);
     }
     tc::mbar_wait_bounded(s.mbar, s.phase, s.abort);
@@ -123,27 +142,42 @@ __device__ __forceinline__ void tmem_row(uint32_t taddr, int ncols, float *v) {
     }
 }
 
+// Adds this tile's scratch accumulator (lanes lo..lo+n-1, 64 columns) into
+// the CTA's fp32 sums; called by the warp that owns those TMEM lanes.
+__device__ __forceinline__ void drain_scratch(uint32_t lane_addr, int r, int lo, int n, float *sum) {
+    float s[64];
+    tmem_row(lane_addr + kColScr, 64, s);
+    if (r >= lo && r < lo + n) {
+        float *row = sum + (r - lo) * 64;
+#pragma unroll
+        for (int k = 0; k < 64; ++k) row[k] += s[k];
+    }
+}
+
 }  // namespace
 
 template <int L>
-__global__ void __launch_bounds__(kTile, 1)
+__global__ void __launch_bounds__(kTile, kBwdPerSm)
 bwd_tc_kernel(const FieldView f, const float *__restrict__ o_in, const float *__restrict__ d_in,
               const float *__restrict__ r_in, const int2 *__restrict__ rec, const long long *__restrict__ off,
               const int *__restrict__ n_used, long long n_samples, const float4 *__restrict__ grad_s,
-              const uint4 *__restrict__ feat_in, const uint4 *__restrict__ wimg, const uint4 *__restrict__ wtimg,
-              float4 *__restrict__ dfeat_out,
+              const uint4 *__restrict__ feat_in, const uint4 *__restrict__ wimg, float4 *__restrict__ dfeat_out,
               float *__restrict__ mlp_grad, unsigned long long *__restrict__ status) {
     constexpr int D = 2 * L;
     using M = BwdSm<D>;
     using W = TcW<D>;
-    using WT = TcWT<D>;
     extern __shared__ __align__(1024) unsigned char smem[];
-    const int r = threadIdx.x;
+    const int r = threadIdx.x, warp = r >> 5;
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + M::misc);
     uint32_t *holder = reinterpret_cast<uint32_t *>(smem + M::misc + 8);
     volatile int *abort = reinterpret_cast<volatile int *>(smem + M::misc + 12);
+    float *acc2 = reinterpret_cast<float *>(smem + M::acc2);
+    float *acc5 = reinterpret_cast<float *>(smem + M::acc5);
+    float *w5 = reinterpret_cast<float *>(smem + M::w5);
+    const float *W5 = f.mlp + 64 * D + 16 * 64 + 64 * 32 + 64 * 64;
     for (int i = r; i < W::bytes / 16; i += kTile) reinterpret_cast<uint4 *>(smem + M::w)[i] = wimg[i];
-    for (int i = r; i < WT::bytes / 16; i += kTile) reinterpret_cast<uint4 *>(smem + M::wt)[i] = wtimg[i];
+    for (int i = r; i < 16 * 64 + 3 * 64; i += kTile) acc2[i] = 0.0f;  // acc2 and acc5 are adjacent
+    for (int i = r; i < 3 * 64; i += kTile) w5[i] = W5[i];
     if (r == 0) {
         tc::mbar_init(mbar, 1);
         *abort = 0;
@@ -160,11 +194,22 @@ bwd_tc_kernel(const FieldView f, const float *__restrict__ o_in, const float *__
     const uint32_t lane_addr = tbase + ((uint32_t)(r & ~31) << 16);
     Sync sy{mbar, abort, 0u};
     const uint32_t s0 = tc::smem_u32(smem);
-    unsigned char *tF = smem + M::F, *tFT = smem + M::FT, *tH = smem + M::H, *tHT = smem + M::HT;
-    unsigned char *tX = smem + M::X, *tXT = smem + M::XT, *tH1 = smem + M::H1, *tH1T = smem + M::H1T;
-    unsigned char *tH2T = smem + M::H2T, *tAT = smem + M::AT;
-    const float *W5 = f.mlp + 64 * D + 16 * 64 + 64 * 32 + 64 * 64;
-    bool acc = false;  // weight-gradient accumulators hold this CTA's sums
+    unsigned char *tF = smem + M::F, *tH = smem + M::H, *tX = smem + M::X, *tH1 = smem + M::H1;
+    unsigned char *tH2 = smem + M::H2, *tG = smem + M::G;
+    // operands: activation and delta tiles, and the forward weight image read as W (MN-major)
+    const Opnd F_k = kmaj(s0 + M::F, D), F_mn = mnmaj(s0 + M::F, D);
+    const Opnd H_k = kmaj(s0 + M::H, 64), H_mn = mnmaj(s0 + M::H, 64);
+    const Opnd X_k = kmaj(s0 + M::X, 32), X_mn = mnmaj(s0 + M::X, 32);
+    const Opnd dO_k = kmaj(s0 + M::X, 16), dO_mn = mnmaj(s0 + M::X, 16);
+    const Opnd H1_k = kmaj(s0 + M::H1, 64), H1_mn = mnmaj(s0 + M::H1, 64);
+    const Opnd H2_mn = mnmaj(s0 + M::H2, 64);
+    const Opnd G_k = kmaj(s0 + M::G, 80), G_mn = mnmaj(s0 + M::G, 80);
+    const uint32_t wb = s0 + M::w;
+    const Opnd W1_k = kmaj(wb + W::w1, D), W2_k = kmaj(wb + W::w2, 64), W3_k = kmaj(wb + W::w3, 32),
+               W4_k = kmaj(wb + W::w4, 64);
+    const Opnd W1_mn = mnmaj(wb + W::w1, D), W2_mn = mnmaj(wb + W::w2, 64), W3_mn = mnmaj(wb + W::w3, 32),
+               W4_mn = mnmaj(wb + W::w4, 64);
+    bool acc = false;  // TMEM weight-gradient accumulators hold this CTA's sums
 
     const long long tiles = (n_samples + kTile - 1) / kTile;
     for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
@@ -187,126 +232,116 @@ bwd_tc_kernel(const FieldView f, const float *__restrict__ o_in, const float *__
                 dz[2] = gs.w;
             }
         }
-        // ---- features (bf16, kept by the forward pass): F row and F^T column ----
+        // ---- features (bf16 rows, kept by the forward pass) ----
 #pragma unroll
         for (int k = 0; k < D / 8; ++k) {
             const uint4 w = have ? __ldg(feat_in + i * (D / 8) + k) : make_uint4(0u, 0u, 0u, 0u);
-            *reinterpret_cast<uint4 *>(tF + tc::kmajor_offset(r, 8 * k, D)) = w;  // one core-matrix row
-            const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-            for (int j = 0; j < 8; ++j) put16(tFT, 8 * k + j, r, kTile, (uint16_t)(ws[j >> 1] >> (16 * (j & 1))));
+            *reinterpret_cast<uint4 *>(tF + (r >> 3) * (D / 8) * 128 + k * 128 + (r & 7) * 16) = w;
         }
         // ---- L1: H = relu(F W1^T) ----
-        mma_batch(sy, [&] { issue_mma<D, 64>(s0 + M::F, s0 + M::w + W::w1, tbase + kColData, false); });
-        uint64_t m0 = 0, m1 = 0, m2 = 0;  // ReLU masks of H, H1, H2
+        mma_batch(sy, [&] { issue<D, 64>(F_k, W1_k, tbase + kColData, false); });
+        uint64_t m0 = 0, m1 = 0;  // ReLU masks of H, H1
         {
             float v[64];
             tmem_row(lane_addr + kColData, 64, v);
 #pragma unroll
             for (int k = 0; k < 64; ++k) {
-                const float h = fmaxf(v[k], 0.0f);
-                if (h > 0.0f) m0 |= 1ull << k;
-                const uint16_t b = bf16_bits(h);
-                put16(tH, r, k, 64, b);
-                put16(tHT, k, r, kTile, b);
+                v[k] = fmaxf(v[k], 0.0f);
+                if (v[k] > 0.0f) m0 |= 1ull << k;
             }
-        }
-        // ---- L2: O = H W2^T ----
-        mma_batch(sy, [&] { issue_mma<64, 16>(s0 + M::H, s0 + M::w + W::w2, tbase + kColData, false); });
-        {
-            float o[16], sh[16];
-            tmem_row(lane_addr + kColData, 16, o);
-            sh16(dir[0], dir[1], dir[2], sh);
 #pragma unroll
-            for (int k = 0; k < 32; ++k) {
-                const uint16_t b = bf16_bits(k < 16 ? o[k] : sh[k - 16]);
-                put16(tX, r, k, 32, b);
-                put16(tXT, k, r, kTile, b);
-            }
+            for (int j = 0; j < 8; ++j) store8(tH, 64, r, j, v + 8 * j);
+        }
+        // ---- L2: O = H W2^T; X = [O, SH(d)] ----
+        mma_batch(sy, [&] { issue<64, 16>(H_k, W2_k, tbase + kColData, false); });
+        {
+            float x[32];
+            tmem_row(lane_addr + kColData, 16, x);
+            sh16(dir[0], dir[1], dir[2], x + 16);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) store8(tX, 32, r, j, x + 8 * j);
         }
         // ---- L3: H1 = relu(X W3^T) ----
-        mma_batch(sy, [&] { issue_mma<32, 64>(s0 + M::X, s0 + M::w + W::w3, tbase + kColData, false); });
+        mma_batch(sy, [&] { issue<32, 64>(X_k, W3_k, tbase + kColData, false); });
         {
             float v[64];
             tmem_row(lane_addr + kColData, 64, v);
 #pragma unroll
             for (int k = 0; k < 64; ++k) {
-                const float h = fmaxf(v[k], 0.0f);
-                if (h > 0.0f) m1 |= 1ull << k;
-                const uint16_t b = bf16_bits(h);
-                put16(tH1, r, k, 64, b);
-                put16(tH1T, k, r, kTile, b);
+                v[k] = fmaxf(v[k], 0.0f);
+                if (v[k] > 0.0f) m1 |= 1ull << k;
             }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) store8(tH1, 64, r, j, v + 8 * j);
         }
-        // ---- L4: H2 = relu(H1 W4^T); dH2 = relu'(H2) (dZ W5), dZ^T, dH2^T ----
-        mma_batch(sy, [&] { issue_mma<64, 64>(s0 + M::H1, s0 + M::w + W::w4, tbase + kColData, false); });
+        // ---- L4: H2 = relu(H1 W4^T); dH2 = relu'(H2) (dZ W5) and dZ into G ----
+        mma_batch(sy, [&] { issue<64, 64>(H1_k, W4_k, tbase + kColData, false); });
         {
             float v[64];
             tmem_row(lane_addr + kColData, 64, v);
 #pragma unroll
-            for (int k = 0; k < 64; ++k) {
-                const float h = fmaxf(v[k], 0.0f);
-                if (h > 0.0f) m2 |= 1ull << k;
-                put16(tH2T, k, r, kTile, bf16_bits(h));
-                const float a = __ldg(W5 + k) * dz[0] + __ldg(W5 + 64 + k) * dz[1] + __ldg(W5 + 128 + k) * dz[2];
-                const uint16_t g = bf16_bits(h > 0.0f ? a : 0.0f);
-                put16(tH, r, k, 64, g);  // dH2 (H itself is no longer an operand)
-                put16(tAT, k, r, kTile, g);
-            }
+            for (int j = 0; j < 8; ++j) {
+                float h[8], g[8];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) put16(tAT, 64 + c, r, kTile, bf16_bits(dz[c]));
+                for (int e = 0; e < 8; ++e) {
+                    const int k = 8 * j + e;
+                    h[e] = fmaxf(v[k], 0.0f);
+                    const float a = w5[k] * dz[0] + w5[64 + k] * dz[1] + w5[128 + k] * dz[2];
+                    g[e] = h[e] > 0.0f ? a : 0.0f;
+                }
+                store8(tH2, 64, r, j, h);
+                store8(tG, 80, r, j, g);
+            }
+            const float z8[8] = {dz[0], dz[1], dz[2], 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+            const float zero[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+            store8(tG, 80, r, 8, z8);
+            store8(tG, 80, r, 9, zero);
         }
-        // ---- dW4 += dH2^T H1, dW5 += dZ^T H2, dH1 = dH2 W4 ----
+        // ---- dW4 += dH2^T H1, dW5 = dZ^T H2 (scratch), dH1 = dH2 W4 ----
         mma_batch(sy, [&] {
-                issue_mma<kTile, 64>(s0 + M::AT, s0 + M::H1T, tbase + kColW4, acc);
-                issue_mma<kTile, 64>(s0 + M::AT, s0 + M::H2T, tbase + kColW5, acc);
-                issue_mma<64, 64>(s0 + M::H, s0 + M::wt + WT::w4, tbase + kColData, false);
+            issue<kTile, 64>(G_mn, H1_mn, tbase + kColW4, acc);
+            issue<kTile, 64>(G_mn, H2_mn, tbase + kColScr, false);
+            issue<64, 64>(G_k, W4_mn, tbase + kColData, false);
         });
+        if (warp == 2) drain_scratch(lane_addr, r, 64, 3, acc5);
         {
             float v[64];
             tmem_row(lane_addr + kColData, 64, v);
 #pragma unroll
-            for (int k = 0; k < 64; ++k) {
-                const uint16_t g = bf16_bits((m1 >> k) & 1ull ? v[k] : 0.0f);
-                put16(tH1, r, k, 64, g);  // dH1
-                put16(tAT, k, r, kTile, g);
-            }
+            for (int k = 0; k < 64; ++k) v[k] = (m1 >> k) & 1ull ? v[k] : 0.0f;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) store8(tH1, 64, r, j, v + 8 * j);  // dH1
         }
-        // ---- dW3 += dH1^T X, dX = dH1 W3 ----
+        // ---- dW3 += dH1^T X, dX = dH1 W3 (its first 16 columns: dO) ----
         mma_batch(sy, [&] {
-                issue_mma<kTile, 32>(s0 + M::AT, s0 + M::XT, tbase + kColW3, acc);
-                issue_mma<64, 32>(s0 + M::H1, s0 + M::wt + WT::w3, tbase + kColData, false);
+            issue<kTile, 32>(H1_mn, X_mn, tbase + kColW3, acc);
+            issue<64, 16>(H1_k, W3_mn, tbase + kColData, false);
         });
         {
             float v[16];
             tmem_row(lane_addr + kColData, 16, v);
             v[0] += dsig;  // dL/do_0 = dL/dsigma * sigma, from the ray pass (fp32)
-#pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const uint16_t g = bf16_bits(v[k]);
-                put16(tX, r, k, 16, g);  // dO as a [128][16] operand
-                put16(tAT, k, r, kTile, g);
-            }
+            store8(tX, 16, r, 0, v);
+            store8(tX, 16, r, 1, v + 8);  // dO as a [128][16] tile
         }
-        // ---- dW2 += dO^T H, dH = dO W2 ----
+        // ---- dW2 = dO^T H (scratch), dH = dO W2 ----
         mma_batch(sy, [&] {
-                issue_mma<kTile, 64>(s0 + M::AT, s0 + M::HT, tbase + kColW2, acc);
-                issue_mma<16, 64>(s0 + M::X, s0 + M::wt + WT::w2, tbase + kColData, false);
+            issue<kTile, 64>(dO_mn, H_mn, tbase + kColScr, false);
+            issue<16, 64>(dO_k, W2_mn, tbase + kColData, false);
         });
+        if (warp == 0) drain_scratch(lane_addr, r, 0, 16, acc2);
         {
             float v[64];
             tmem_row(lane_addr + kColData, 64, v);
 #pragma unroll
-            for (int k = 0; k < 64; ++k) {
-                const uint16_t g = bf16_bits((m0 >> k) & 1ull ? v[k] : 0.0f);
-                put16(tH, r, k, 64, g);  // dH
-                put16(tAT, k, r, kTile, g);
-            }
+            for (int k = 0; k < 64; ++k) v[k] = (m0 >> k) & 1ull ? v[k] : 0.0f;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) store8(tH, 64, r, j, v + 8 * j);  // dH
         }
         // ---- dW1 += dH^T F, dF = dH W1 ----
         mma_batch(sy, [&] {
-                issue_mma<kTile, D>(s0 + M::AT, s0 + M::FT, tbase + kColW1, acc);
-                issue_mma<64, D>(s0 + M::H, s0 + M::wt + WT::w1, tbase + kColData, false);
+            issue<kTile, D>(H_mn, F_mn, tbase + kColW1, acc);
+            issue<64, D>(H_k, W1_mn, tbase + kColData, false);
         });
         acc = true;
         {  // dL/dfeatures (fp32) for the grid scatter; the TMEM load is warp-wide
@@ -331,18 +366,14 @@ bwd_tc_kernel(const FieldView f, const float *__restrict__ o_in, const float *__
         tmem_row(lane_addr + kColW4, 64, v);
         if (r < 64)
             for (int k = 0; k < 64; ++k) atomicAdd(g4 + r * 64 + k, v[k]);
-        tmem_row(lane_addr + kColW2, 64, v);
-        if (r < 16)
-            for (int k = 0; k < 64; ++k) atomicAdd(g2 + r * 64 + k, v[k]);
-        tmem_row(lane_addr + kColW5, 64, v);
-        if (r >= 64 && r < 67)
-            for (int k = 0; k < 64; ++k) atomicAdd(g5 + (r - 64) * 64 + k, v[k]);
         tmem_row(lane_addr + kColW1, D, v);
         if (r < 64)
             for (int k = 0; k < D; ++k) atomicAdd(g1 + r * D + k, v[k]);
         tmem_row(lane_addr + kColW3, 32, v);
         if (r < 64)
             for (int k = 0; k < 32; ++k) atomicAdd(g3 + r * 32 + k, v[k]);
+        for (int e = r; e < 16 * 64; e += kTile) atomicAdd(g2 + e, acc2[e]);
+        for (int e = r; e < 3 * 64; e += kTile) atomicAdd(g5 + e, acc5[e]);
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -443,38 +474,17 @@ sample_fwd_tc_kernel(const FieldView f, const float *__restrict__ o_in, const fl
     tc_teardown(S, status);
 }
 
-// fp32 W1..W4 -> the transposed bf16 image TcWT<D>.
-__global__ void build_wt_image_kernel(const float *__restrict__ mlp, int D, unsigned char *__restrict__ img) {
-    // (matrix, rows N = inputs, K = outputs, source offset, source row length)
-    const int w1 = 0, w2 = 64 * D, w3 = w2 + 16 * 64, w4 = w3 + 64 * 32;
-    const int spec[4][4] = {{64, 64, w4, 64}, {32, 64, w3, 32}, {64, 16, w2, 64}, {D, 64, w1, D}};
-    int e = blockIdx.x * blockDim.x + threadIdx.x, base = 0;
-    for (int m = 0; m < 4; ++m) {
-        const int N = spec[m][0], K = spec[m][1];
-        if (e < N * K) {
-            const int n = e / K, k = e % K;  // element (n = input, k = output) = W[k][n]
-            const float v = mlp[spec[m][2] + k * spec[m][3] + n];
-            const int b = base + (n >> 3) * (K >> 3) * 128 + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2;
-            *reinterpret_cast<__nv_bfloat16 *>(img + b) = __float2bfloat16_rn(v);
-            return;
-        }
-        e -= N * K;
-        base += N * K * 2;
-    }
-}
-
-// Weight images of the tensor-core backward (forward bf16 image, transposed
-// image), rebuilt when the fp32 weights change.
+// bf16 weight image of the tensor-core training kernels (the forward image;
+// the backward reads it MN-major for the data gradients), rebuilt when the
+// fp32 weights change.
 static cudaError_t ensure_bwd_images(vrnerf_field *F, cudaStream_t st) {
     const int D = F->view.d_in;
     const size_t fwd = (size_t)(64 * D * 2 + 16 * 64 * 2 + 64 * 32 * 2 + 64 * 64 * 2 + 16 * 64 * 2);
-    const size_t wt = (size_t)(64 * 64 * 2 + 32 * 64 * 2 + 64 * 16 * 2 + D * 64 * 2);
     if (F->tcb_w && F->tcb_version == F->mlp_version) return cudaSuccess;
     cudaError_t e = cudaSuccess;
-    if (!F->tcb_w && (e = cudaMalloc(&F->tcb_w, fwd + wt)) != cudaSuccess) return e;
+    if (!F->tcb_w && (e = cudaMalloc(&F->tcb_w, fwd)) != cudaSuccess) return e;
     unsigned char *img = static_cast<unsigned char *>(F->tcb_w);
     build_tc_image_kernel<<<(int)((fwd / 2 + 255) / 256), 256, 0, st>>>(F->mlp, D, 1, img);
-    build_wt_image_kernel<<<(int)((wt / 2 + 255) / 256), 256, 0, st>>>(F->mlp, D, img + fwd);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     F->tcb_version = F->mlp_version;
     return cudaSuccess;
@@ -491,14 +501,15 @@ static cudaError_t launch_bwd_tc_t(vrnerf_field *F, const float *o, const float 
     auto kern = bwd_tc_kernel<L>;
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
-    const long long tiles = (n + kTile - 1) / kTile;
-    const int grid = (int)(tiles < num_sms() ? tiles : num_sms());
-    const unsigned char *img = static_cast<const unsigned char *>(F->tcb_w);
-    const size_t fwd = (size_t)TcW<D>::bytes;
+    // TMEM: kBwdCols per CTA, so at most 512 / kBwdCols CTAs share an SM
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTile, smem)) != cudaSuccess) return e;
+    per_sm = per_sm < 1 ? 1 : (per_sm > kBwdPerSm ? kBwdPerSm : per_sm);
+    const long long tiles = (n + kTile - 1) / kTile, cap = (long long)num_sms() * per_sm;
+    const int grid = (int)(tiles < cap ? tiles : cap);
     unsigned long long *status = reinterpret_cast<unsigned long long *>(F->counter) + 1;
     kern<<<grid, kTile, smem, st>>>(F->view, o, d, r, rec, off, n_used, n, grad_s, feat,
-                                    reinterpret_cast<const uint4 *>(img), reinterpret_cast<const uint4 *>(img + fwd),
-                                    dfeat, F->mlp_grad, status);
+                                    static_cast<const uint4 *>(F->tcb_w), dfeat, F->mlp_grad, status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return launch_grid_scatter(F, o, d, r, rec, off, n_used, n, dfeat, st);
 }

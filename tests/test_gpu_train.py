@@ -204,6 +204,20 @@ def test_bf16_tensor_core_backward_against_oracle(V, variant):
         worst = np.max(np.abs(got - ref)[big] / np.abs(ref)[big])
         print(variant, got.size, "rel L2", rel, "cos", cos, "worst large", worst)
         assert rel < 6e-2 and cos > 0.998, (rel, cos, worst)
+    # each weight matrix on its own (W1 [64][D], W2 [16][64], W3 [64][32],
+    # W4 [64][64], W5 [3][64]): a product read with the wrong layout or
+    # summed into the wrong accumulator fails here even where the others
+    # dominate the norm of the whole gradient
+    D = cfg.d_in
+    sizes = [64 * D, 16 * 64, 64 * 32, 64 * 64, 3 * 64]
+    at = 0
+    for name, n in zip(("W1", "W2", "W3", "W4", "W5"), sizes):
+        got, ref = gm[at:at + n], rm[at:at + n]
+        at += n
+        rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        cos = float(np.dot(got, ref) / (np.linalg.norm(got) * np.linalg.norm(ref)))
+        print(variant, name, "rel L2", rel, "cos", cos)
+        assert rel < 6e-2 and cos > 0.998, (name, rel, cos)
     V.vrnerf_field_set_train_precision(f, "fp32")
     with pytest.raises(V.VrnerfError):
         V.vrnerf_field_set_train_precision(f, "fp8")

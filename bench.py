@@ -69,6 +69,8 @@ def parse():
                     help="small case for ncu: two 2^18-ray training steps on the room field")
     ap.add_argument("--train-prec", default="fp32", choices=("fp32", "bf16"),
                     help="training precision of --profile-train")
+    ap.add_argument("--train-log2", type=int, default=18,
+                    help="log2 of the --profile-train batch (rays)")
     ap.add_argument("--profile-case", action="store_true",
                     help="small case for ncu: two renders of a 1024x1024 window of the room frame")
     return ap.parse_args()
@@ -437,9 +439,9 @@ def profile_case(args):
 
 
 def profile_train(args):
-    """Two training steps of 2^18 rays on the room field (grid, gradients and
-    moments about 1 GB on the device): the small case for ncu captures of the
-    training kernels."""
+    """Two training steps of 2^18 rays (--train-log2) on the room field (grid,
+    gradients and moments about 1 GB on the device): the small case for ncu
+    captures of the training kernels."""
     import torch
     from paper_2311_02542_gb300 import synth as S
     from paper_2311_02542_gb300 import vrnerf as V
@@ -448,9 +450,11 @@ def profile_train(args):
     field = V.Field(sc.cfg, sc.grid, sc.mlp, sc.occ_bits)
     V.vrnerf_field_set_train_precision(field, args.train_prec)
     poses, intr = S.training_views(sc.occ, sc.cfg, n_views=64)
-    batch = [torch.from_numpy(a).cuda() for a in S.training_batch(poses, intr, 1 << 18, seed=5, step=0)]
+    batch = [torch.from_numpy(a).cuda()
+             for a in S.training_batch(poses, intr, 1 << args.train_log2, seed=5, step=0)]
     losses = [V.vrnerf_train_step(field, *batch) for _ in range(2)]
-    print(json.dumps({"profile_train": "room, 2^18 rays", "precision": args.train_prec, "losses": losses}))
+    print(json.dumps({"profile_train": f"room, 2^{args.train_log2} rays", "precision": args.train_prec,
+                      "losses": losses}))
     return 0
 
 

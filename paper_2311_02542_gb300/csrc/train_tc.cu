@@ -501,9 +501,21 @@ static cudaError_t launch_bwd_tc_t(vrnerf_field *F, const float *o, const float 
     auto kern = bwd_tc_kernel<L>;
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return e;
-    // TMEM: kBwdCols per CTA, so at most 512 / kBwdCols CTAs share an SM
-    int per_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTile, smem)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  (int)cudaSharedmemCarveoutMaxShared)) != cudaSuccess)
+        return e;
+    // resident CTAs per SM from registers, shared memory and TMEM (kBwdCols
+    // of the SM's 512 columns per CTA), at most kBwdPerSm
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
+    int dev = 0, regs_sm = 65536, smem_sm = 233472;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    const int by_regs = regs_sm / (((fa.numRegs + 7) / 8) * 8 * kTile);
+    const int by_smem = smem_sm / (int)(smem + fa.sharedSizeBytes + 1024);
+    int per_sm = by_regs < by_smem ? by_regs : by_smem;
+    if (per_sm > (int)(512 / kBwdCols)) per_sm = (int)(512 / kBwdCols);
     per_sm = per_sm < 1 ? 1 : (per_sm > kBwdPerSm ? kBwdPerSm : per_sm);
     const long long tiles = (n + kTile - 1) / kTile, cap = (long long)num_sms() * per_sm;
     const int grid = (int)(tiles < cap ? tiles : cap);

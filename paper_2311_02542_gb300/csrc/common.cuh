@@ -623,20 +623,22 @@ __device__ __forceinline__ int gather_features(const FieldView &f, const float p
 
 
 // Hash-grid gradient scatter of one sample per lane (all 32 lanes call it,
-// `have` false for lanes without a sample): dL/dfeat times the level weight
-// w_l and the trilinear weight of each corner, added into grid_grad [L][T][F=2].
+// `have` false for lanes without a sample) over levels l0 .. l0 + LG - 1:
+// dL/dfeat (dfeat[2 (l - l0) + c]) times the level weight w_l and the
+// trilinear weight of each corner, added into grid_grad [L][T][F=2].
 // On dense levels neighbouring lanes (consecutive samples of a ray) often hit
 // the same corners, and thousands of samples per batch meet on the few
 // coarse vertices, so runs of equal indices in consecutive lanes are summed
 // with shuffles first and only the run's first lane issues the atomic.
-template <int L>
+template <int LG>
 __device__ __forceinline__ void scatter_grid_grad(const FieldView &f, const float p[3], float rn,
-                                                  const float *dfeat, bool have, float *grid_grad) {
+                                                  const float *dfeat, bool have, float *grid_grad, int l0) {
     constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const float Ls = have ? lod_star(f, rn) : -1.0e30f;
-#pragma unroll 1
-    for (int l = 0; l < L; ++l) {
+#pragma unroll
+    for (int q = 0; q < LG; ++q) {  // unrolled: dfeat stays in registers
+        const int l = l0 + q;
         const float wl = lod_weight(Ls, l);
         const bool act = have && wl > 0.0f;
         if (!__any_sync(FULL, act)) break;  // weights fall with l for every lane
@@ -654,8 +656,8 @@ __device__ __forceinline__ void scatter_grid_grad(const FieldView &f, const floa
                 for (int j = 0; j < 4; ++j) {
                     const float wyz = (j & 1 ? fr[1] : 1.0f - fr[1]) * (j & 2 ? fr[2] : 1.0f - fr[2]) * wl;
                     const float c0 = (1.0f - fr[0]) * wyz, c1 = fr[0] * wyz;
-                    const float2 g0 = make_float2(c0 * dfeat[2 * l], c0 * dfeat[2 * l + 1]);
-                    const float2 g1 = make_float2(c1 * dfeat[2 * l], c1 * dfeat[2 * l + 1]);
+                    const float2 g0 = make_float2(c0 * dfeat[2 * q], c0 * dfeat[2 * q + 1]);
+                    const float2 g1 = make_float2(c1 * dfeat[2 * q], c1 * dfeat[2 * q + 1]);
                     const uint32_t i0 = idx[2 * j], i1 = idx[2 * j + 1];
                     if ((i0 ^ i1) == 1u) {
                         const float4 v = (i0 & 1u) ? make_float4(g1.x, g1.y, g0.x, g0.y)
@@ -673,7 +675,7 @@ __device__ __forceinline__ void scatter_grid_grad(const FieldView &f, const floa
         for (int b = 0; b < 8; ++b) {
             const float cw = (b & 1 ? fr[0] : 1.0f - fr[0]) * (b & 2 ? fr[1] : 1.0f - fr[1]) *
                              (b & 4 ? fr[2] : 1.0f - fr[2]) * wl;
-            float gx = act ? cw * dfeat[2 * l] : 0.0f, gy = act ? cw * dfeat[2 * l + 1] : 0.0f;
+            float gx = act ? cw * dfeat[2 * q] : 0.0f, gy = act ? cw * dfeat[2 * q + 1] : 0.0f;
             const uint32_t key = act ? idx[b] : 0xffffffffu;
             const uint32_t prev = __shfl_up_sync(FULL, key, 1);
             const bool head = lane == 0 || prev != key;

@@ -382,22 +382,29 @@ bwd_tc_kernel(const FieldView f, const float *__restrict__ o_in, const float *__
     if (r < 32) tc::tmem_dealloc(tbase, kBwdCols);
 }
 
-// Grid-gradient scatter of the tensor-core backward: one thread per sample
+// Grid-gradient scatter after either backward kernel: one thread per sample
 // (consecutive samples in a warp, so the dense-level runs still merge), at
 // full occupancy so that the atomics' latency is hidden; dL/dfeatures come
-// from the backward kernel in fp32.
-template <int L>
+// from the backward kernel in fp32. The levels are taken in groups of LG,
+// blockIdx.y = group: blocks start in linear order, so the whole batch
+// scatters into one group's levels before the next group's blocks run, and
+// the fp32 gradient lines of those levels (16 MB per hashed level) stay in L2
+// under the atomics instead of every sample touching all L levels at once.
+// Each group recomputes the sample's position and footprint.
+template <int L, int LG>
 __global__ void __launch_bounds__(128)
 grid_scatter_kernel(const FieldView f, const float *__restrict__ o_in, const float *__restrict__ d_in,
                     const float *__restrict__ r_in, const int2 *__restrict__ rec, const long long *__restrict__ off,
                     const int *__restrict__ n_used, long long n, const float4 *__restrict__ dfeat_in,
                     float *__restrict__ grid_grad) {
     constexpr int D = 2 * L;
+    static_assert(L % LG == 0 && LG % 2 == 0, "levels split into groups of whole float4s");
+    const int l0 = blockIdx.y * LG;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i0 = (long long)blockIdx.x * blockDim.x; i0 < n; i0 += stride) {  // uniform per block
         const long long i = i0 + threadIdx.x;
         bool have = false;
-        float p[3] = {0.0f, 0.0f, 0.0f}, rn = 0.0f, dfeat[D];
+        float p[3] = {0.0f, 0.0f, 0.0f}, rn = 0.0f, dfeat[2 * LG];
         if (i < n) {
             const int2 q = rec[i];
             const long long b = q.x;
@@ -412,14 +419,14 @@ grid_scatter_kernel(const FieldView f, const float *__restrict__ o_in, const flo
             }
         }
 #pragma unroll
-        for (int k = 0; k < D / 4; ++k) {
-            const float4 v = have ? __ldg(dfeat_in + i * (D / 4) + k) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        for (int k = 0; k < LG / 2; ++k) {  // read once: streaming loads leave L2 to the gradient
+            const float4 v = have ? __ldcs(dfeat_in + i * (D / 4) + l0 / 2 + k) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             dfeat[4 * k] = v.x;
             dfeat[4 * k + 1] = v.y;
             dfeat[4 * k + 2] = v.z;
             dfeat[4 * k + 3] = v.w;
         }
-        scatter_grid_grad<L>(f, p, rn, dfeat, have, grid_grad);
+        scatter_grid_grad<LG>(f, p, rn, dfeat, have, grid_grad, l0);
     }
 }
 
@@ -526,16 +533,22 @@ static cudaError_t launch_bwd_tc_t(vrnerf_field *F, const float *o, const float 
     return launch_grid_scatter(F, o, d, r, rec, off, n_used, n, dfeat, st);
 }
 
+#ifndef VRN_SCATTER_LEVELS
+#define VRN_SCATTER_LEVELS 8  // levels per group of the grid-gradient scatter
+#endif
+
 template <int L>
 static cudaError_t launch_grid_scatter_t(vrnerf_field *F, const float *o, const float *d, const float *r,
                                          const int2 *rec, const long long *off, const int *n_used, long long n,
                                          const float4 *dfeat, cudaStream_t st) {
+    constexpr int LG = VRN_SCATTER_LEVELS < L ? VRN_SCATTER_LEVELS : L;
+    auto kern = grid_scatter_kernel<L, LG>;
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, grid_scatter_kernel<L>, 128, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, 0);
     if (e != cudaSuccess) return e;
     const long long blocks = (n + 127) / 128, cap = (long long)num_sms() * (per_sm > 0 ? per_sm : 1);
-    grid_scatter_kernel<L><<<(int)(blocks < cap ? blocks : cap), 128, 0, st>>>(F->view, o, d, r, rec, off, n_used, n,
-                                                                               dfeat, F->grid_grad);
+    const dim3 grid((unsigned)(blocks < cap ? blocks : cap), L / LG);
+    kern<<<grid, 128, 0, st>>>(F->view, o, d, r, rec, off, n_used, n, dfeat, F->grid_grad);
     return cudaGetLastError();
 }
 

@@ -6,10 +6,11 @@
 // 12 800 rays) still fill the GPU:
 // 1. count / emit: every ray is marched (occupancy rule of Sec. 4.3, no
 //    early termination) and its evaluated samples are listed contiguously
-//    as (ray, step) records;
+//    as (ray, step) records, in ray order (offsets by a prefix sum);
 // 2. sample forward: one thread per sample gathers the LOD-weighted features
 //    and runs the fp32 MLPs: sigma and PQ colour per sample;
-// 3. ray composite: one thread per ray composites its samples front to back
+// 3. ray composite: each lane composites one ray at a time (and takes the
+//    next ray when it is done) front to back
 //    (stopping where transmittance drops below T_eps, or after the number of
 //    samples a forward pass reported), forms dL/dC (L1: sign(C - target) /
 //    3B, or a given upstream gradient) and walks its samples backwards: with
@@ -112,59 +113,216 @@ __device__ __forceinline__ void minigemm_cols(const float *sD, const float *sA, 
 }
 
 // ---- 1. count / emit ----------------------------------------------------
-// Evaluated samples of ray b (no early termination) and the start of its
-// records: one atomic per warp reserves the warp's records. With `mask`
-// (mw words per ray, zeroed beforehand), the ray's evaluated step indices
-// are also kept as bits, so that emit needs no second march.
+// Rays differ widely in length (a few evaluated samples for most, hundreds
+// for some), and with one ray per thread a warp runs as long as its longest
+// ray while its other lanes idle. The per-ray kernels below (count, and the
+// ray composite of step 3) keep every lane busy instead: a lane whose ray is
+// done takes the next ray index from its warp's batch of 32, and the warp
+// takes a new batch from a global counter (one atomic per batch) when the
+// batch runs out. Which lane handles which ray does not change any result.
+struct RayQueue {
+    long long base;  // next ray index of the warp's batch
+    int left;        // rays of the batch not handed out yet
+    bool empty;      // every ray has been handed out
+};
+
+// Called by all 32 lanes of the warp together; each lane with want == true
+// receives a ray index, or -1 once all B rays have been handed out.
+__device__ __forceinline__ long long take_ray(RayQueue &q, bool want, unsigned long long *__restrict__ next,
+                                              long long B) {
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    long long mine = -1;
+    unsigned need = __ballot_sync(FULL, want);
+    while (need && !q.empty) {
+        if (q.left == 0) {
+            unsigned long long g = 0;
+            if (lane == 0) g = atomicAdd(next, 32ull);
+            g = __shfl_sync(FULL, g, 0);
+            if ((long long)g >= B) {
+                q.empty = true;
+                break;
+            }
+            q.base = (long long)g;
+            q.left = (int)(B - q.base < 32 ? B - q.base : 32);
+        }
+        const int take = min(__popc(need), q.left);
+        const int rank = __popc(need & ((1u << lane) - 1u));
+        if (((need >> lane) & 1u) && rank < take) mine = q.base + rank;
+        q.base += take;
+        q.left -= take;
+        need = __ballot_sync(FULL, want && mine < 0);
+    }
+    return mine;
+}
+
+constexpr int kCountChunk = 8;  // march iterations of a lane between two refills
+
+// Evaluated samples of every ray (no early termination) -> cnt; with `mask`
+// (mw words per ray, zeroed beforehand) the ray's evaluated step indices are
+// also kept as bits, so that emit needs no second march. The records'
+// offsets come from the scan kernels below. `next` starts at 0.
 __global__ void __launch_bounds__(128)
 count_kernel(const FieldView f, const float *__restrict__ o_in, const float *__restrict__ d_in, int B,
-             int *__restrict__ cnt, long long *__restrict__ off, unsigned long long *__restrict__ total,
-             uint32_t *__restrict__ mask, int mw) {
-    const int lane = threadIdx.x & 31;
-    for (long long b0 = (long long)blockIdx.x * blockDim.x; b0 < B; b0 += (long long)gridDim.x * blockDim.x) {
-        const long long b = b0 + threadIdx.x;
-        int n = 0;
-        if (b < B) {
-            MarchRay m;
+             int *__restrict__ cnt, uint32_t *__restrict__ mask, int mw, unsigned long long *__restrict__ next) {
+    RayQueue q{0, 0, false};
+    bool live = false, retired = false;
+    long long b = -1;
+    MarchRay m;
+    int n = 0, wi = -1;
+    uint32_t word = 0u, *mrow = nullptr;
+    unsigned tested = 0;
+    while (true) {
+        const long long got = take_ray(q, !live && !retired, next, B);
+        if (!live && !retired) {
+            if (got < 0) {
+                retired = true;
+            } else {
+                b = got;
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                m.o[k] = o_in[3 * b + k];
-                m.d[k] = d_in[3 * b + k];
-            }
-            march_init(f, m);
-            unsigned tested = 0;
-            float p[3];
-            uint32_t *mrow = mask ? mask + (size_t)b * mw : nullptr;
-            uint32_t word = 0;
-            int wi = -1;
-            while (march_next(f, f.t_tab, m, p, 1 << 30, tested) == MARCH_SAMPLE) {
-                ++n;
-                if (mrow) {
-                    const int w = m.step >> 5;
-                    if (w != wi) {
-                        if (wi >= 0) mrow[wi] = word;
-                        wi = w;
-                        word = 0u;
-                    }
-                    word |= 1u << (m.step & 31);
+                for (int k = 0; k < 3; ++k) {
+                    m.o[k] = o_in[3 * b + k];
+                    m.d[k] = d_in[3 * b + k];
                 }
-                ++m.step;
+                march_init(f, m);
+                n = 0;
+                wi = -1;
+                word = 0u;
+                mrow = mask ? mask + (size_t)b * mw : nullptr;
+                live = true;
             }
-            if (mrow && wi >= 0) mrow[wi] = word;
         }
-        int incl = n;
+        if (__all_sync(0xffffffffu, retired)) break;
+        if (!live) continue;
+        float p[3];
+        const int r = march_next(f, f.t_tab, m, p, kCountChunk, tested);
+        if (r == MARCH_SAMPLE) {
+            ++n;
+            if (mrow) {
+                const int w = m.step >> 5;
+                if (w != wi) {
+                    if (wi >= 0) mrow[wi] = word;
+                    wi = w;
+                    word = 0u;
+                }
+                word |= 1u << (m.step & 31);
+            }
+            ++m.step;
+        } else if (r == MARCH_END) {
+            if (mrow && wi >= 0) mrow[wi] = word;
+            cnt[b] = n;
+            live = false;
+        }
+    }
+}
+
+// Exclusive prefix sums of cnt[0..B) -> off, and their total, in three
+// launches: per-block sums of kScanPer counts, a scan of those sums by one
+// block, then each block's own scan plus its block's offset.
+constexpr int kScanThreads = 1024, kScanItems = 4, kScanPer = kScanThreads * kScanItems;
+
+// inclusive scan over the block's threads (all threads call it); *total = the block's sum
+__device__ __forceinline__ long long block_scan(long long v, long long *warp_sums, long long *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int s = 1; s < 32; s <<= 1) {
+        const long long u = __shfl_up_sync(0xffffffffu, v, s);
+        if (lane >= s) v += u;
+    }
+    if (lane == 31) warp_sums[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        long long w = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0;
 #pragma unroll
         for (int s = 1; s < 32; s <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, incl, s);
-            if (lane >= s) incl += v;
+            const long long u = __shfl_up_sync(0xffffffffu, w, s);
+            if (lane >= s) w += u;
         }
-        unsigned long long base = 0;
-        if (lane == 31) base = atomicAdd(total, (unsigned long long)incl);
-        base = __shfl_sync(0xffffffffu, base, 31);
-        if (b < B) {
-            cnt[b] = n;
-            off[b] = (long long)base + incl - n;
+        warp_sums[lane] = w;  // inclusive over warps
+    }
+    __syncthreads();
+    const long long r = v + (warp > 0 ? warp_sums[warp - 1] : 0);
+    *total = warp_sums[(blockDim.x >> 5) - 1];
+    __syncthreads();  // warp_sums may be reused after this
+    return r;
+}
+
+// Small batches (up to kScanOneBlock x kScanPer rays): one block walks the
+// counts in chunks of kScanPer with a running carry, in one launch.
+constexpr int kScanOneBlock = 8;
+
+__global__ void __launch_bounds__(kScanThreads)
+scan_one_block_kernel(const int *__restrict__ cnt, int B, long long *__restrict__ off,
+                      unsigned long long *__restrict__ total_out) {
+    __shared__ long long ws[32];
+    long long carry = 0;
+    for (long long c = 0; c < B; c += kScanPer) {  // uniform over the block
+        const long long base = c + (long long)threadIdx.x * kScanItems;
+        int v4[kScanItems];
+        long long v = 0;
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            v4[k] = base + k < B ? cnt[base + k] : 0;
+            v += v4[k];
         }
+        long long tot;
+        long long x = block_scan(v, ws, &tot) - v + carry;
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            if (base + k < B) off[base + k] = x;
+            x += v4[k];
+        }
+        carry += tot;
+    }
+    if (threadIdx.x == 0) *total_out = (unsigned long long)carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+scan_sums_kernel(const int *__restrict__ cnt, int B, long long *__restrict__ bsum) {
+    __shared__ long long ws[32];
+    const long long base = (long long)blockIdx.x * kScanPer + (long long)threadIdx.x * kScanItems;
+    long long v = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+        if (base + k < B) v += cnt[base + k];
+    long long total;
+    block_scan(v, ws, &total);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+scan_blocks_kernel(long long *__restrict__ bsum, int nb, unsigned long long *__restrict__ total_out) {
+    __shared__ long long ws[32];
+    long long carry = 0;
+    for (int c = 0; c < nb; c += kScanThreads) {  // uniform over the block
+        const int i = c + threadIdx.x;
+        const long long v = i < nb ? bsum[i] : 0;
+        long long tot;
+        const long long incl = block_scan(v, ws, &tot);
+        if (i < nb) bsum[i] = carry + incl - v;  // exclusive: offset of block i
+        carry += tot;
+    }
+    if (threadIdx.x == 0) *total_out = (unsigned long long)carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+scan_offsets_kernel(const int *__restrict__ cnt, int B, const long long *__restrict__ boff,
+                    long long *__restrict__ off) {
+    __shared__ long long ws[32];
+    const long long base = (long long)blockIdx.x * kScanPer + (long long)threadIdx.x * kScanItems;
+    int c[kScanItems];
+    long long v = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        c[k] = base + k < B ? cnt[base + k] : 0;
+        v += c[k];
+    }
+    long long total;
+    long long x = block_scan(v, ws, &total) - v + boff[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < B) off[base + k] = x;
+        x += c[k];
     }
 }
 
@@ -250,61 +408,95 @@ sample_fwd_kernel(const FieldView f, const float *__restrict__ o_in, const float
 // count); else stop after the sample where T < T_eps. target (nullable): L1
 // loss against PQ(target / 100), else gC_given is dL/dC. Overwrites sc with
 // (dL/dsigma, dL/dz_0..2) of every composited sample (z: pre-sigmoid colour)
-// and zeros for the rest.
+// and zeros for the rest. C_out (nullable): forward only, the composited PQ
+// colour and sample count per ray.
+// Each lane walks one ray at a time and takes the next ray when it is done
+// (take_ray): per iteration a lane handles one sample of its ray, in the
+// composite (phase 0) or the gradient walk (phase 1), or up to 8 records of
+// the zero tail (phase 2). `next` starts at 0.
 __global__ void __launch_bounds__(128)
 ray_comp_kernel(const FieldView f, const float *__restrict__ o_in, const float *__restrict__ d_in, int B,
                 const int *__restrict__ cnt, const long long *__restrict__ off, const int2 *__restrict__ rec,
                 const int *__restrict__ n_given, const float *__restrict__ target, const float *__restrict__ gC_given,
                 float inv_n, float4 *__restrict__ sc, int *__restrict__ n_used, float *__restrict__ loss_sum,
-                float *__restrict__ hist, float *__restrict__ C_out) {
+                float *__restrict__ hist, float *__restrict__ C_out, unsigned long long *__restrict__ next) {
+    RayQueue q{0, 0, false};
     float loss = 0.0f;
-    for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < B; b += (long long)gridDim.x * blockDim.x) {
-        const long long k0 = off[b];
-        const int m = cnt[b];
-        const int lim = n_given ? min(n_given[b], m) : m;
-        float T = 1.0f, C[3] = {0, 0, 0};
-        int n = 0;
-        while (n < lim) {
-            const float4 v = sc[k0 + n];
-            const int step = rec[k0 + n].y;
-            const float t = f.t_tab[step], sd = v.x * (f.t_tab[step + 1] - t);
-            const float alpha = -expm1f(-sd), w = T * alpha;
-            C[0] += w * v.y;
-            C[1] += w * v.z;
-            C[2] += w * v.w;
-            if (hist) {
-                const float o[3] = {o_in[3 * b], o_in[3 * b + 1], o_in[3 * b + 2]};
-                const float d[3] = {d_in[3 * b], d_in[3 * b + 1], d_in[3 * b + 2]};
-                float p[3];
-                int vox;
-                sample_voxel(f, o, d, t, p, vox);
-                atomicMax(reinterpret_cast<int *>(hist) + vox, __float_as_int(alpha));
-            }
-            T *= expf(-sd);
-            ++n;
-            if (!n_given && T < f.T_eps) break;
-        }
-        if (C_out) {  // forward only: composited PQ colour and sample count
-            C_out[3 * b] = C[0];
-            C_out[3 * b + 1] = C[1];
-            C_out[3 * b + 2] = C[2];
-            n_used[b] = n;
-            continue;
-        }
-        float g[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            if (target) {
-                const float diff = C[c] - linear_to_pq(target[3 * b + c]);
-                g[c] = diff > 0.0f ? inv_n : (diff < 0.0f ? -inv_n : 0.0f);
-                loss += fabsf(diff);
+    bool live = false, retired = false;
+    long long b = -1, k0 = 0;
+    int m = 0, lim = 0, n = 0, k = 0, phase = 0;
+    float T = 1.0f, C[3] = {0, 0, 0}, g[3] = {0, 0, 0}, Cpre[3] = {0, 0, 0}, ro[3] = {0, 0, 0}, rd[3] = {0, 0, 1};
+    while (true) {
+        const long long got = take_ray(q, !live && !retired, next, B);
+        if (!live && !retired) {
+            if (got < 0) {
+                retired = true;
             } else {
-                g[c] = gC_given[3 * b + c];
+                b = got;
+                k0 = off[b];
+                m = cnt[b];
+                lim = n_given ? min(n_given[b], m) : m;
+                n = 0;
+                phase = 0;
+                T = 1.0f;
+                C[0] = C[1] = C[2] = 0.0f;
+                if (hist) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        ro[c] = o_in[3 * b + c];
+                        rd[c] = d_in[3 * b + c];
+                    }
+                }
+                live = true;
             }
         }
-        float Cpre[3] = {0, 0, 0};
-        T = 1.0f;
-        for (int k = 0; k < n; ++k) {
+        if (__all_sync(0xffffffffu, retired)) break;
+        if (!live) continue;
+        if (phase == 0) {  // composite sample n
+            bool done = n >= lim;
+            if (!done) {
+                const float4 v = sc[k0 + n];
+                const int step = rec[k0 + n].y;
+                const float t = f.t_tab[step], sd = v.x * (f.t_tab[step + 1] - t);
+                const float alpha = -expm1f(-sd), w = T * alpha;
+                C[0] += w * v.y;
+                C[1] += w * v.z;
+                C[2] += w * v.w;
+                if (hist) {
+                    float p[3];
+                    int vox;
+                    sample_voxel(f, ro, rd, t, p, vox);
+                    atomicMax(reinterpret_cast<int *>(hist) + vox, __float_as_int(alpha));
+                }
+                T *= expf(-sd);
+                ++n;
+                done = n >= lim || (!n_given && T < f.T_eps);
+            }
+            if (done) {
+                if (C_out) {  // forward only: composited PQ colour and sample count
+                    C_out[3 * b] = C[0];
+                    C_out[3 * b + 1] = C[1];
+                    C_out[3 * b + 2] = C[2];
+                    n_used[b] = n;
+                    live = false;
+                    continue;
+                }
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    if (target) {
+                        const float diff = C[c] - linear_to_pq(target[3 * b + c]);
+                        g[c] = diff > 0.0f ? inv_n : (diff < 0.0f ? -inv_n : 0.0f);
+                        loss += fabsf(diff);
+                    } else {
+                        g[c] = gC_given[3 * b + c];
+                    }
+                    Cpre[c] = 0.0f;
+                }
+                T = 1.0f;
+                k = 0;
+                phase = n > 0 ? 1 : 2;
+            }
+        } else if (phase == 1) {  // gradients of sample k
             const float4 v = sc[k0 + k];
             const int step = rec[k0 + k].y;
             const float delta = f.t_tab[step + 1] - f.t_tab[step], sd = v.x * delta;
@@ -321,13 +513,19 @@ ray_comp_kernel(const FieldView f, const float *__restrict__ o_in, const float *
             // dL/do_0 = dL/dsigma * sigma (sigma = exp(o_0 + bias)), with this pass's sigma
             sc[k0 + k] = make_float4(dsig * v.x, dz[0], dz[1], dz[2]);
             T = Tn;
+            if (++k == n) phase = 2;
+        } else {  // zeros for the samples after the last composited one
+#pragma unroll 1
+            for (int e = 0; e < 8 && k < m; ++e, ++k) sc[k0 + k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (k >= m) {
+                n_used[b] = n;
+                live = false;
+            }
         }
-        for (int k = n; k < m; ++k) sc[k0 + k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        n_used[b] = n;
     }
     if (loss_sum) {
 #pragma unroll
-        for (int k = 16; k > 0; k >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, k);
+        for (int s = 16; s > 0; s >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, s);
         if ((threadIdx.x & 31) == 0 && loss != 0.0f) atomicAdd(loss_sum, loss);
     }
 }
@@ -577,7 +775,8 @@ struct TrainScratch {
     uint4 *feat = nullptr;    // bf16 features per sample (tensor-core backward only)
     float4 *dfeat = nullptr;  // dL/dfeatures per sample, fp32 (backward)
     long long scap = 0, fcap = 0, dcap = 0;
-    unsigned long long *total = nullptr;   // device counter of records
+    unsigned long long *total = nullptr;   // device: [0] records, [1] [2] ray counters of count / ray composite
+    long long *bsum = nullptr;             // per block of kScanPer rays: sum, then offset (count_pass)
     unsigned long long *total_h = nullptr; // pinned host copy
     uint32_t *mask = nullptr;              // per ray: bits of its evaluated steps (count -> emit)
     long long mask_cap = 0;                // words allocated
@@ -601,7 +800,7 @@ static int ensure_train(vrnerf_field *F, int B) {
     if (!F->train_scratch) F->train_scratch = new TrainScratch();
     TrainScratch &S = *static_cast<TrainScratch *>(F->train_scratch);
     if (!S.total) {
-        if ((e = cudaMalloc(&S.total, sizeof(unsigned long long))) != cudaSuccess ||
+        if ((e = cudaMalloc(&S.total, 4 * sizeof(unsigned long long))) != cudaSuccess ||
             (e = cudaMallocHost(&S.total_h, sizeof(unsigned long long))) != cudaSuccess)
             return fail(VRNERF_ENOMEM, "training scratch: %s", cudaGetErrorString(e));
     }
@@ -609,12 +808,14 @@ static int ensure_train(vrnerf_field *F, int B) {
         cudaFree(S.cnt);
         cudaFree(S.n_used);
         cudaFree(S.off);
+        cudaFree(S.bsum);
         S.cnt = S.n_used = nullptr;
-        S.off = nullptr;
+        S.off = S.bsum = nullptr;
         S.cap = 0;
         if ((e = cudaMalloc(&S.cnt, sizeof(int) * (size_t)B)) != cudaSuccess ||
             (e = cudaMalloc(&S.n_used, sizeof(int) * (size_t)B)) != cudaSuccess ||
-            (e = cudaMalloc(&S.off, sizeof(long long) * (size_t)B)) != cudaSuccess)
+            (e = cudaMalloc(&S.off, sizeof(long long) * (size_t)B)) != cudaSuccess ||
+            (e = cudaMalloc(&S.bsum, sizeof(long long) * (size_t)((B + kScanPer - 1) / kScanPer))) != cudaSuccess)
             return fail(VRNERF_ENOMEM, "training scratch: %s", cudaGetErrorString(e));
         S.cap = B;
     }
@@ -647,6 +848,7 @@ void release_train_scratch(vrnerf_field *F) {
     cudaFree(S->cnt);
     cudaFree(S->n_used);
     cudaFree(S->off);
+    cudaFree(S->bsum);
     cudaFree(S->rec);
     cudaFree(S->sc);
     cudaFree(S->feat);
@@ -670,11 +872,12 @@ static cudaError_t grid_for(K kern, int threads, size_t smem, long long work, in
 }
 
 // Marches rays [0, B) of (o, d), counts their evaluated samples and reserves
-// their records (S.cnt, S.off); *n receives the total. One small read-back.
+// their records (S.cnt, S.off: contiguous per ray, in ray order); *n receives
+// the total. One small read-back.
 static int count_pass(vrnerf_field *F, TrainScratch &S, const float *o, const float *d, int B, cudaStream_t st,
                       long long *n) {
     int blocks = 0;
-    cudaError_t e = cudaMemsetAsync(S.total, 0, sizeof(unsigned long long), st);
+    cudaError_t e = cudaMemsetAsync(S.total, 0, 4 * sizeof(unsigned long long), st);
     // step bits for emit, when they fit (else emit marches again)
     const int mw = (F->view.S + 31) / 32;
     const long long words = (long long)B * mw;
@@ -692,7 +895,18 @@ static int count_pass(vrnerf_field *F, TrainScratch &S, const float *o, const fl
     S.mask_valid = mask != nullptr;
     if (e == cudaSuccess) e = grid_for(count_kernel, 128, 0, B, blocks);
     if (e == cudaSuccess) {
-        count_kernel<<<blocks, 128, 0, st>>>(F->view, o, d, B, S.cnt, S.off, S.total, mask, mw);
+        count_kernel<<<blocks, 128, 0, st>>>(F->view, o, d, B, S.cnt, mask, mw, S.total + 1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && B > 0) {  // record offsets: exclusive prefix sums of the counts
+        const int nb = (B + kScanPer - 1) / kScanPer;
+        if (nb <= kScanOneBlock) {
+            scan_one_block_kernel<<<1, kScanThreads, 0, st>>>(S.cnt, B, S.off, S.total);
+        } else {
+            scan_sums_kernel<<<nb, kScanThreads, 0, st>>>(S.cnt, B, S.bsum);
+            scan_blocks_kernel<<<1, kScanThreads, 0, st>>>(S.bsum, nb, S.total);
+            scan_offsets_kernel<<<nb, kScanThreads, 0, st>>>(S.cnt, B, S.bsum, S.off);
+        }
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(S.total_h, S.total, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
@@ -757,10 +971,11 @@ static int samples_pass(vrnerf_field *F, TrainScratch &S, const float *o, const 
         }
     }
     if (e == cudaSuccess) e = grid_for(ray_comp_kernel, 128, 0, Bc, blocks);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S.total + 2, 0, sizeof(unsigned long long), st);
     if (e == cudaSuccess) {
         ray_comp_kernel<<<blocks, 128, 0, st>>>(f, o, d, Bc, S.cnt, S.off, S.rec, n_given, target, gC, inv3B, S.sc,
                                                 C_out ? n_out : S.n_used, target ? F->loss_acc : nullptr,
-                                                C_out ? nullptr : F->hist, C_out);
+                                                C_out ? nullptr : F->hist, C_out, S.total + 2);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && n > 0 && tc_bwd) {

@@ -269,3 +269,34 @@ def test_sample_budget_splits_the_batch_without_changing_it(V, prec):
     for a, b in ((g1, g0), (m1, m0)):
         assert np.all(np.abs(a - b) <= 1e-5 * np.abs(b) + 1e-6 * np.abs(b).max())
     assert (p1 == p0).all() and (n1 == n0).all()
+
+
+def test_large_batch_record_offsets(V):
+    """2^17 rays in one pass take the multi-block prefix sum of the record
+    offsets (more than 8 x 4096 rays); the same rays in batches of 16 384 take
+    the one-block scan. Colours and sample counts agree bit for bit (records
+    land where each ray's composite reads them), and 300 sampled rays match
+    the oracle's render (fp32 MLPs, 1e-4 relative; a ray whose early
+    termination flips at T_eps within T_eps + 1e-4)."""
+    sc = S.make_scene("room")
+    cfg = sc.cfg
+    poses, intr = S.training_views(sc.occ, cfg, n_views=16)
+    B, part = 1 << 17, 1 << 14
+    o, d, r, _ = S.training_batch(poses, intr, B, seed=9, step=1)
+    f = V.Field(cfg, sc.grid, sc.mlp, sc.occ_bits)
+    pq, n = V.vrnerf_forward_rays(f, _cuda(o), _cuda(d), _cuda(r))
+    pq, n = pq.cpu().numpy(), n.cpu().numpy()
+    for s0 in range(0, B, part):
+        sl = slice(s0, s0 + part)
+        p2, n2 = V.vrnerf_forward_rays(f, _cuda(o[sl]), _cuda(d[sl]), _cuda(r[sl]))
+        assert (p2.cpu().numpy() == pq[sl]).all() and (n2.cpu().numpy() == n[sl]).all(), s0
+    V.vrnerf_field_status(f)
+    f.close()
+    pick = np.sort(np.random.default_rng(3).choice(B, 300, replace=False))
+    ref = O.Field(cfg, sc.grid, sc.mlp, sc.occ_bits).render_rays(o[pick], d[pick], r[pick])
+    err = np.abs(pq[pick].astype(np.float64) - ref["pq"])
+    flip = n[pick] != ref["n"]
+    assert flip.mean() <= 0.01
+    assert np.all((err <= 1e-4 * np.abs(ref["pq"]) + 1e-6)[~flip]), err[~flip].max()
+    if flip.any():
+        assert err[flip].max() <= cfg.T_eps + 1e-4

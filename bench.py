@@ -109,9 +109,11 @@ def load_peaks():
 
 
 class Clocks:
-    """nvidia-smi sampler (every 200 ms) started before the warm-up; mark()
+    """nvidia-smi sampler (every 50 ms) started before the warm-up; mark()
     at the start of the timed region, stop() at its end. The summary uses the
-    samples taken between the two (the last earlier one if none was)."""
+    samples taken between the two; when the region was shorter than one
+    interval, the first sample after it (taken within 50 ms of its end, the
+    GPU still at the region's clocks) and the last one before it."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -120,7 +122,7 @@ class Clocks:
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
@@ -144,13 +146,22 @@ class Clocks:
             self.f.close()
             os.unlink(self.f.name)
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        end = len(self._lines())
+        in_region = end - self.skip
+        if in_region <= 0:  # wait (at most 0.5 s) for the first sample after the region
+            t0 = time.perf_counter()
+            while len(self._lines()) <= end and time.perf_counter() - t0 < 0.5:
+                time.sleep(0.005)
         self.p.terminate()
         try:
             self.p.wait(timeout=5)
         except Exception:
             self.p.kill()
         lines = self._lines()
-        lines = lines[self.skip:] or lines[max(self.skip - 1, 0):self.skip]
+        if in_region > 0:
+            lines = lines[self.skip:end]
+        else:
+            lines = lines[max(self.skip - 1, 0):self.skip] + lines[end:end + 1]
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in lines:
@@ -168,7 +179,8 @@ class Clocks:
         os.unlink(self.f.name)
         return {"sm_mhz": float(np.median(sm)) if sm else None,
                 "sm_max_mhz": float(max(mx)) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "in_region": max(in_region, 0),
+                "interval_ms": 50}
 
 
 # Keys printed last, in this order: a reader that keeps only the end of the

@@ -156,7 +156,10 @@ __device__ __forceinline__ long long take_ray(RayQueue &q, bool want, unsigned l
     return mine;
 }
 
-constexpr int kCountChunk = 8;  // march iterations of a lane between two refills
+#ifndef VRN_COUNT_CHUNK
+#define VRN_COUNT_CHUNK 8
+#endif
+constexpr int kCountChunk = VRN_COUNT_CHUNK;  // march iterations of a lane between two refills
 
 // Evaluated samples of every ray (no early termination) -> cnt; with `mask`
 // (mw words per ray, zeroed beforehand) the ray's evaluated step indices are
@@ -411,9 +414,14 @@ sample_fwd_kernel(const FieldView f, const float *__restrict__ o_in, const float
 // and zeros for the rest. C_out (nullable): forward only, the composited PQ
 // colour and sample count per ray.
 // Each lane walks one ray at a time and takes the next ray when it is done
-// (take_ray): per iteration a lane handles one sample of its ray, in the
-// composite (phase 0) or the gradient walk (phase 1), or up to 8 records of
-// the zero tail (phase 2). `next` starts at 0.
+// (take_ray): per iteration a lane handles up to kCompSamples samples of its
+// ray, in the composite (phase 0) or the gradient walk (phase 1), or up to 8
+// records of the zero tail (phase 2). `next` starts at 0.
+#ifndef VRN_COMP_SAMPLES
+#define VRN_COMP_SAMPLES 4
+#endif
+constexpr int kCompSamples = VRN_COMP_SAMPLES;
+
 __global__ void __launch_bounds__(128)
 ray_comp_kernel(const FieldView f, const float *__restrict__ o_in, const float *__restrict__ d_in, int B,
                 const int *__restrict__ cnt, const long long *__restrict__ off, const int2 *__restrict__ rec,
@@ -452,9 +460,10 @@ ray_comp_kernel(const FieldView f, const float *__restrict__ o_in, const float *
         }
         if (__all_sync(0xffffffffu, retired)) break;
         if (!live) continue;
-        if (phase == 0) {  // composite sample n
+        if (phase == 0) {  // composite samples n, n + 1, ...
             bool done = n >= lim;
-            if (!done) {
+#pragma unroll 1
+            for (int e = 0; e < kCompSamples && !done; ++e) {
                 const float4 v = sc[k0 + n];
                 const int step = rec[k0 + n].y;
                 const float t = f.t_tab[step], sd = v.x * (f.t_tab[step + 1] - t);
@@ -496,24 +505,28 @@ ray_comp_kernel(const FieldView f, const float *__restrict__ o_in, const float *
                 k = 0;
                 phase = n > 0 ? 1 : 2;
             }
-        } else if (phase == 1) {  // gradients of sample k
-            const float4 v = sc[k0 + k];
-            const int step = rec[k0 + k].y;
-            const float delta = f.t_tab[step + 1] - f.t_tab[step], sd = v.x * delta;
-            const float alpha = -expm1f(-sd), Tn = T * expf(-sd), w = T * alpha;
-            const float cc[3] = {v.y, v.z, v.w};
-            float dsig = 0.0f, dz[3];
+        } else if (phase == 1) {  // gradients of samples k, k + 1, ...
+#pragma unroll 1
+            for (int e = 0; e < kCompSamples && k < n; ++e) {
+                const float4 v = sc[k0 + k];
+                const int step = rec[k0 + k].y;
+                const float delta = f.t_tab[step + 1] - f.t_tab[step], sd = v.x * delta;
+                const float alpha = -expm1f(-sd), Tn = T * expf(-sd), w = T * alpha;
+                const float cc[3] = {v.y, v.z, v.w};
+                float dsig = 0.0f, dz[3];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float suffix = C[c] - (Cpre[c] + w * cc[c]);
-                dsig += g[c] * delta * (Tn * cc[c] - suffix);
-                dz[c] = w * g[c] * cc[c] * (1.0f - cc[c]);
-                Cpre[c] += w * cc[c];
+                for (int c = 0; c < 3; ++c) {
+                    const float suffix = C[c] - (Cpre[c] + w * cc[c]);
+                    dsig += g[c] * delta * (Tn * cc[c] - suffix);
+                    dz[c] = w * g[c] * cc[c] * (1.0f - cc[c]);
+                    Cpre[c] += w * cc[c];
+                }
+                // dL/do_0 = dL/dsigma * sigma (sigma = exp(o_0 + bias)), with this pass's sigma
+                sc[k0 + k] = make_float4(dsig * v.x, dz[0], dz[1], dz[2]);
+                T = Tn;
+                ++k;
             }
-            // dL/do_0 = dL/dsigma * sigma (sigma = exp(o_0 + bias)), with this pass's sigma
-            sc[k0 + k] = make_float4(dsig * v.x, dz[0], dz[1], dz[2]);
-            T = Tn;
-            if (++k == n) phase = 2;
+            if (k == n) phase = 2;
         } else {  // zeros for the samples after the last composited one
 #pragma unroll 1
             for (int e = 0; e < 8 && k < m; ++e, ++k) sc[k0 + k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);

@@ -40,13 +40,13 @@ WORKLOAD = "room_2048x2048_single_eye"
 STEREO_BUDGET_MS = 1000.0 / 36.0  # one frame at the 36 Hz the paper's demo sustains
 
 
-# DRAM bytes read + written by one 2048x2048 launch of render_tc_kernel<16, 0, 0>
+# DRAM bytes read + written by one 2048x2048 launch of render_tc_kernel<16, 0, 0, 4>
 # (ncu dram__bytes_read.sum + dram__bytes_write.sum, one capture of the benchmark
 # frame). NCU_TRAFFIC_CURRENT says whether the kernel is unchanged since that
 # capture; when it is not, the bench line reports traffic null and the old
 # figure beside it.
-NCU_TRAFFIC_BYTES = 53221632 + 25712384
-NCU_TRAFFIC_CURRENT = True  # captured on the current kernel (per-axis distance field)
+NCU_TRAFFIC_BYTES = 56300544 + 32215808
+NCU_TRAFFIC_CURRENT = True  # captured on the current kernel (four tiles per CTA)
 
 
 def parse():

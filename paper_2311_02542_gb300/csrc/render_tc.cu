@@ -41,18 +41,28 @@ constexpr int kLookahead = VRN_LOOKAHEAD;  // samples a lane may hold found ahea
 
 // Tiles per CTA (NT): each 128-thread warpgroup runs its own 128-row tile
 // (its own activation tile, mbarrier, TMEM columns and named barrier) and
-// the tiles share one weight image. With two, three 8-warp CTAs (the
-// register limit) take 160 KB of shared memory per SM instead of six 4-warp
-// CTAs' 228 KB, and L1 keeps the rest for the hash-grid gather: measured
-// 10 % faster on an unbounded scene's frame, whose far-field samples spread
-// over the whole table, and up to 2.5 % slower on a bounded room, which
-// therefore keeps one tile per CTA.
-template <bool CT>
-constexpr int render_tiles() { return CT ? 2 : 1; }
+// the tiles share one weight image, so more tiles per CTA leave more of the
+// SM's shared memory to L1 for the hash-grid gather. Bounded scenes with
+// fp16 or bf16 operands run four tiles per 16-warp CTA, two CTAs per SM at
+// 64 registers a thread: 32 warps and 168 KB of shared memory per SM,
+// against six 4-warp CTAs at 80 registers (24 warps, 228 KB); measured 6 %
+// faster on the room frame despite the extra register spills. The fp8 path
+// spills far more at 64 registers (7 % slower) and keeps one tile per CTA.
+// Contracted scenes keep two tiles per 8-warp CTA, three CTAs per SM at 80
+// registers, as their look-ahead queue lives in registers (10 % faster than
+// one tile on the unbounded frame; four tiles: 4 % slower).
+#ifndef VRN_TILES_BOUNDED
+#define VRN_TILES_BOUNDED 4
+#endif
+template <bool CT, int FMT>
+constexpr int render_tiles() { return CT ? 2 : (FMT == 2 ? 1 : VRN_TILES_BOUNDED); }
+// resident CTAs per SM that the register budget is cut for
+template <int NT>
+constexpr int render_min_blocks() { return NT == 4 ? 2 : kTcMinBlocks / NT; }
 static_assert((kLookahead & (kLookahead - 1)) == 0, "the look-ahead queue is a power-of-two ring");
 
-template <int L, int FMT, bool CT, int NT = render_tiles<CT>()>
-__global__ void __launch_bounds__(kTcThreads * NT, kTcMinBlocks / NT)
+template <int L, int FMT, bool CT, int NT = render_tiles<CT, FMT>()>
+__global__ void __launch_bounds__(kTcThreads * NT, render_min_blocks<NT>())
 render_tc_kernel(const FieldView f, const RaySource src, const RenderOut out,
                  unsigned long long *__restrict__ counter, const uint4 *__restrict__ wimg,
                  unsigned long long *__restrict__ status) {
@@ -331,7 +341,7 @@ __global__ void build_tc_image_fp8_kernel(const float *__restrict__ mlp, int D, 
 // ---------------------------------------------------------------------------
 template <int L, int FMT, bool CT>
 static cudaError_t render_tc_ct(vrnerf_field *F, const RaySource &src, const RenderOut &out, cudaStream_t st) {
-    constexpr int NT = render_tiles<CT>();
+    constexpr int NT = render_tiles<CT, FMT>();
     const size_t smem = tc_smem_bytes(2 * L, 0, NT);
     auto kern = render_tc_kernel<L, FMT, CT, NT>;
     int bps = 0;

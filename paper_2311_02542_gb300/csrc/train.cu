@@ -161,13 +161,25 @@ __device__ __forceinline__ long long take_ray(RayQueue &q, bool want, unsigned l
 #endif
 constexpr int kCountChunk = VRN_COUNT_CHUNK;  // march iterations of a lane between two refills
 
+// A ray past this many evaluated samples goes to a warp of its own: a few
+// rays hold hundreds of samples (a hundred times the median), and one lane
+// walking them alone sets the time of the whole kernel at small batches.
+constexpr int kLongRay = 32;
+#ifndef VRN_LONG_COUNT
+#define VRN_LONG_COUNT 32
+#endif
+constexpr int kLongCount = VRN_LONG_COUNT;  // samples after which count_kernel hands a ray on
+
 // Evaluated samples of every ray (no early termination) -> cnt; with `mask`
 // (mw words per ray, zeroed beforehand) the ray's evaluated step indices are
 // also kept as bits, so that emit needs no second march. The records'
-// offsets come from the scan kernels below. `next` starts at 0.
+// offsets come from the scan kernels below. `next` and *n_long start at 0.
+// A ray that reaches kLongCount samples stops here: its count so far goes
+// to cnt and (ray, next step) to long_rays, for count_long_kernel.
 __global__ void __launch_bounds__(128)
 count_kernel(const FieldView f, const float *__restrict__ o_in, const float *__restrict__ d_in, int B,
-             int *__restrict__ cnt, uint32_t *__restrict__ mask, int mw, unsigned long long *__restrict__ next) {
+             int *__restrict__ cnt, uint32_t *__restrict__ mask, int mw, unsigned long long *__restrict__ next,
+             int2 *__restrict__ long_rays, unsigned int *__restrict__ n_long) {
     RayQueue q{0, 0, false};
     bool live = false, retired = false;
     long long b = -1;
@@ -211,11 +223,76 @@ count_kernel(const FieldView f, const float *__restrict__ o_in, const float *__r
                 word |= 1u << (m.step & 31);
             }
             ++m.step;
+            if (n >= kLongCount && m.step < f.S) {  // the rest of the ray to a warp of its own
+                if (mrow) mrow[wi] = word;
+                cnt[b] = n;
+                long_rays[atomicAdd(n_long, 1u)] = make_int2((int)b, m.step);
+                live = false;
+            }
         } else if (r == MARCH_END) {
             if (mrow && wi >= 0) mrow[wi] = word;
             cnt[b] = n;
             live = false;
         }
+    }
+}
+
+// The rest of each long ray, from the step where count_kernel left it: the
+// warp's 32 lanes march consecutive segments of the remaining steps. The
+// march finds every step whose sample lies in an occupied voxel (the skip
+// never passes one, and a bounded ray that has left the grid does not come
+// back), so the segments together give the same steps as one march, and
+// their counts add up. Mask words that two segments (or count_kernel) share
+// are merged with atomicOr.
+__global__ void __launch_bounds__(128)
+count_long_kernel(const FieldView f, const float *__restrict__ o_in, const float *__restrict__ d_in,
+                  int *__restrict__ cnt, uint32_t *__restrict__ mask, int mw,
+                  const int2 *__restrict__ long_rays, const unsigned int *__restrict__ n_long) {
+    const int lane = threadIdx.x & 31;
+    const unsigned total = *n_long;
+    const unsigned warps = gridDim.x * (blockDim.x >> 5);
+    for (unsigned e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); e < total; e += warps) {
+        const int2 lr = long_rays[e];
+        const long long b = lr.x;
+        const int len = (f.S - lr.y + 31) / 32;
+        const int s0 = lr.y + lane * len, s1 = min(f.S, s0 + len);
+        int n = 0;
+        if (s0 < s1) {
+            MarchRay m;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                m.o[k] = o_in[3 * b + k];
+                m.d[k] = d_in[3 * b + k];
+            }
+            march_init(f, m);
+            m.step = s0;
+            uint32_t *mrow = mask ? mask + (size_t)b * mw : nullptr;
+            uint32_t word = 0u;
+            int wi = -1;
+            unsigned tested = 0;
+            float p[3];
+            while (true) {
+                const int r = march_next(f, f.t_tab, m, p, kCountChunk, tested);
+                if (r == MARCH_END || m.step >= s1) break;
+                if (r == MARCH_SAMPLE) {
+                    ++n;
+                    if (mrow) {
+                        const int w = m.step >> 5;
+                        if (w != wi) {
+                            if (wi >= 0) atomicOr(mrow + wi, word);
+                            wi = w;
+                            word = 0u;
+                        }
+                        word |= 1u << (m.step & 31);
+                    }
+                    ++m.step;
+                }
+            }
+            if (mrow && wi >= 0) atomicOr(mrow + wi, word);
+        }
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) n += __shfl_xor_sync(0xffffffffu, n, s);
+        if (lane == 0) cnt[b] += n;
     }
 }
 
@@ -427,7 +504,8 @@ ray_comp_kernel(const FieldView f, const float *__restrict__ o_in, const float *
                 const int *__restrict__ cnt, const long long *__restrict__ off, const int2 *__restrict__ rec,
                 const int *__restrict__ n_given, const float *__restrict__ target, const float *__restrict__ gC_given,
                 float inv_n, float4 *__restrict__ sc, int *__restrict__ n_used, float *__restrict__ loss_sum,
-                float *__restrict__ hist, float *__restrict__ C_out, unsigned long long *__restrict__ next) {
+                float *__restrict__ hist, float *__restrict__ C_out, unsigned long long *__restrict__ next,
+                int *__restrict__ long_rays, unsigned int *__restrict__ n_long) {
     RayQueue q{0, 0, false};
     float loss = 0.0f;
     bool live = false, retired = false;
@@ -443,19 +521,23 @@ ray_comp_kernel(const FieldView f, const float *__restrict__ o_in, const float *
                 b = got;
                 k0 = off[b];
                 m = cnt[b];
-                lim = n_given ? min(n_given[b], m) : m;
-                n = 0;
-                phase = 0;
-                T = 1.0f;
-                C[0] = C[1] = C[2] = 0.0f;
-                if (hist) {
+                if (m > kLongRay) {  // composited by ray_comp_long_kernel; this lane takes another ray
+                    long_rays[atomicAdd(n_long, 1u)] = (int)b;
+                } else {
+                    lim = n_given ? min(n_given[b], m) : m;
+                    n = 0;
+                    phase = 0;
+                    T = 1.0f;
+                    C[0] = C[1] = C[2] = 0.0f;
+                    if (hist) {
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        ro[c] = o_in[3 * b + c];
-                        rd[c] = d_in[3 * b + c];
+                        for (int c = 0; c < 3; ++c) {
+                            ro[c] = o_in[3 * b + c];
+                            rd[c] = d_in[3 * b + c];
+                        }
                     }
+                    live = true;
                 }
-                live = true;
             }
         }
         if (__all_sync(0xffffffffu, retired)) break;
@@ -541,6 +623,156 @@ ray_comp_kernel(const FieldView f, const float *__restrict__ o_in, const float *
         for (int s = 16; s > 0; s >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, s);
         if ((threadIdx.x & 31) == 0 && loss != 0.0f) atomicAdd(loss_sum, loss);
     }
+}
+
+// Warp inclusive scans over the 32 lanes.
+__device__ __forceinline__ float warp_prod_scan(float x) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int s = 1; s < 32; s <<= 1) {
+        const float u = __shfl_up_sync(0xffffffffu, x, s);
+        if (lane >= s) x *= u;
+    }
+    return x;
+}
+__device__ __forceinline__ float warp_sum_scan(float x) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int s = 1; s < 32; s <<= 1) {
+        const float u = __shfl_up_sync(0xffffffffu, x, s);
+        if (lane >= s) x += u;
+    }
+    return x;
+}
+
+// The long rays of ray_comp_kernel (more than kLongRay samples), one warp
+// each, 32 samples at a time: the transmittance before sample j is the carry
+// times the product of exp(-sigma_i delta_i) over the chunk's earlier samples
+// (a warp product scan), the composite stops after the first sample whose
+// transmittance drops below T_eps, and the gradient walk takes the prefix of
+// w_i c_i from a warp sum scan. The same quantities as ray_comp_kernel, with
+// the fp32 products and sums in another order.
+__global__ void __launch_bounds__(128)
+ray_comp_long_kernel(const FieldView f, const float *__restrict__ o_in, const float *__restrict__ d_in,
+                     const int *__restrict__ cnt, const long long *__restrict__ off, const int2 *__restrict__ rec,
+                     const int *__restrict__ n_given, const float *__restrict__ target,
+                     const float *__restrict__ gC_given, float inv_n, float4 *__restrict__ sc,
+                     int *__restrict__ n_used, float *__restrict__ loss_sum, float *__restrict__ hist,
+                     float *__restrict__ C_out, const int *__restrict__ long_rays,
+                     const unsigned int *__restrict__ n_long) {
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned total = *n_long;
+    const unsigned warps = gridDim.x * (blockDim.x >> 5);
+    float loss = 0.0f;
+    for (unsigned e = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); e < total; e += warps) {
+        const long long b = long_rays[e];
+        const long long k0 = off[b];
+        const int m = cnt[b];
+        const int lim = n_given ? min(n_given[b], m) : m;
+        float ro[3] = {0, 0, 0}, rd[3] = {0, 0, 1};
+        if (hist) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                ro[c] = o_in[3 * b + c];
+                rd[c] = d_in[3 * b + c];
+            }
+        }
+        // ---- composite ----
+        float T = 1.0f, C[3] = {0, 0, 0};
+        int n = 0;
+        for (int c0 = 0; c0 < lim;) {  // uniform over the warp
+            const int j = c0 + lane;
+            const bool valid = j < lim;
+            float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            float t = 0.0f, sd = 0.0f;
+            if (valid) {
+                v = sc[k0 + j];
+                const int step = rec[k0 + j].y;
+                t = f.t_tab[step];
+                sd = v.x * (f.t_tab[step + 1] - t);
+            }
+            const float incl = warp_prod_scan(valid ? expf(-sd) : 1.0f);
+            float excl = __shfl_up_sync(FULL, incl, 1);
+            if (lane == 0) excl = 1.0f;
+            const float Tj = T * excl, Ta = T * incl;
+            const unsigned term = __ballot_sync(FULL, valid && !n_given && Ta < f.T_eps);
+            const int last = term ? __ffs(term) - 1 : min(31, lim - 1 - c0);  // last composited lane
+            const bool used = lane <= last;
+            const float w = used ? Tj * (-expm1f(-sd)) : 0.0f;
+            // the chunk's sum taken from the same scan the gradient walk uses, so
+            // that its prefix at the last sample is C exactly (suffix 0 there)
+            C[0] += __shfl_sync(FULL, warp_sum_scan(w * v.y), last);
+            C[1] += __shfl_sync(FULL, warp_sum_scan(w * v.z), last);
+            C[2] += __shfl_sync(FULL, warp_sum_scan(w * v.w), last);
+            if (hist && used) {
+                float p[3];
+                int vox;
+                sample_voxel(f, ro, rd, t, p, vox);
+                atomicMax(reinterpret_cast<int *>(hist) + vox, __float_as_int(-expm1f(-sd)));
+            }
+            n += last + 1;
+            T = __shfl_sync(FULL, Ta, last);
+            if (term) break;
+            c0 += 32;
+        }
+        if (C_out) {  // forward only
+            if (lane == 0) {
+                C_out[3 * b] = C[0];
+                C_out[3 * b + 1] = C[1];
+                C_out[3 * b + 2] = C[2];
+                n_used[b] = n;
+            }
+            continue;
+        }
+        float g[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            if (target) {
+                const float diff = C[c] - linear_to_pq(target[3 * b + c]);
+                g[c] = diff > 0.0f ? inv_n : (diff < 0.0f ? -inv_n : 0.0f);
+                if (lane == 0) loss += fabsf(diff);
+            } else {
+                g[c] = gC_given[3 * b + c];
+            }
+        }
+        // ---- gradients of the composited samples ----
+        T = 1.0f;
+        float carry[3] = {0, 0, 0};
+        for (int c0 = 0; c0 < n; c0 += 32) {  // uniform over the warp
+            const int j = c0 + lane;
+            const bool valid = j < n;
+            float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            float delta = 0.0f, sd = 0.0f;
+            if (valid) {
+                v = sc[k0 + j];
+                const int step = rec[k0 + j].y;
+                delta = f.t_tab[step + 1] - f.t_tab[step];
+                sd = v.x * delta;
+            }
+            const float incl = warp_prod_scan(valid ? expf(-sd) : 1.0f);
+            float excl = __shfl_up_sync(FULL, incl, 1);
+            if (lane == 0) excl = 1.0f;
+            const float Tj = T * excl, Tn = T * incl;
+            const float w = valid ? Tj * (-expm1f(-sd)) : 0.0f;
+            const float cc[3] = {v.y, v.z, v.w};
+            float dsig = 0.0f, dz[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float wc = w * cc[c];
+                const float pre = warp_sum_scan(wc);  // inclusive prefix of w c in this chunk
+                const float suffix = C[c] - (carry[c] + pre);
+                dsig += g[c] * delta * (Tn * cc[c] - suffix);
+                dz[c] = w * g[c] * cc[c] * (1.0f - cc[c]);
+                carry[c] += __shfl_sync(FULL, pre, 31);
+            }
+            if (valid) sc[k0 + j] = make_float4(dsig * v.x, dz[0], dz[1], dz[2]);
+            T = __shfl_sync(FULL, Tn, min(31, n - 1 - c0));
+        }
+        for (int j = n + lane; j < m; j += 32) sc[k0 + j] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (lane == 0) n_used[b] = n;
+    }
+    if (loss_sum && lane == 0 && loss != 0.0f) atomicAdd(loss_sum, loss);
 }
 
 // ---- 4. sample backward -------------------------------------------------------
@@ -788,8 +1020,11 @@ struct TrainScratch {
     uint4 *feat = nullptr;    // bf16 features per sample (tensor-core backward only)
     float4 *dfeat = nullptr;  // dL/dfeatures per sample, fp32 (backward)
     long long scap = 0, fcap = 0, dcap = 0;
-    unsigned long long *total = nullptr;   // device: [0] records, [1] [2] ray counters of count / ray composite
+    unsigned long long *total = nullptr;   // device: [0] records, [1] [2] ray counters of count / ray composite,
+                                           // [3] [4] long rays of ray composite / count (unsigned int each)
     long long *bsum = nullptr;             // per block of kScanPer rays: sum, then offset (count_pass)
+    int2 *long_count = nullptr;            // per ray: (ray, step) handed from count_kernel to count_long_kernel
+    int *long_comp = nullptr;              // per ray: rays handed from ray_comp_kernel to ray_comp_long_kernel
     unsigned long long *total_h = nullptr; // pinned host copy
     uint32_t *mask = nullptr;              // per ray: bits of its evaluated steps (count -> emit)
     long long mask_cap = 0;                // words allocated
@@ -813,7 +1048,7 @@ static int ensure_train(vrnerf_field *F, int B) {
     if (!F->train_scratch) F->train_scratch = new TrainScratch();
     TrainScratch &S = *static_cast<TrainScratch *>(F->train_scratch);
     if (!S.total) {
-        if ((e = cudaMalloc(&S.total, 4 * sizeof(unsigned long long))) != cudaSuccess ||
+        if ((e = cudaMalloc(&S.total, 8 * sizeof(unsigned long long))) != cudaSuccess ||
             (e = cudaMallocHost(&S.total_h, sizeof(unsigned long long))) != cudaSuccess)
             return fail(VRNERF_ENOMEM, "training scratch: %s", cudaGetErrorString(e));
     }
@@ -822,13 +1057,19 @@ static int ensure_train(vrnerf_field *F, int B) {
         cudaFree(S.n_used);
         cudaFree(S.off);
         cudaFree(S.bsum);
+        cudaFree(S.long_count);
+        cudaFree(S.long_comp);
         S.cnt = S.n_used = nullptr;
         S.off = S.bsum = nullptr;
+        S.long_count = nullptr;
+        S.long_comp = nullptr;
         S.cap = 0;
         if ((e = cudaMalloc(&S.cnt, sizeof(int) * (size_t)B)) != cudaSuccess ||
             (e = cudaMalloc(&S.n_used, sizeof(int) * (size_t)B)) != cudaSuccess ||
             (e = cudaMalloc(&S.off, sizeof(long long) * (size_t)B)) != cudaSuccess ||
-            (e = cudaMalloc(&S.bsum, sizeof(long long) * (size_t)((B + kScanPer - 1) / kScanPer))) != cudaSuccess)
+            (e = cudaMalloc(&S.bsum, sizeof(long long) * (size_t)((B + kScanPer - 1) / kScanPer))) != cudaSuccess ||
+            (e = cudaMalloc(&S.long_count, sizeof(int2) * (size_t)B)) != cudaSuccess ||
+            (e = cudaMalloc(&S.long_comp, sizeof(int) * (size_t)B)) != cudaSuccess)
             return fail(VRNERF_ENOMEM, "training scratch: %s", cudaGetErrorString(e));
         S.cap = B;
     }
@@ -862,6 +1103,8 @@ void release_train_scratch(vrnerf_field *F) {
     cudaFree(S->n_used);
     cudaFree(S->off);
     cudaFree(S->bsum);
+    cudaFree(S->long_count);
+    cudaFree(S->long_comp);
     cudaFree(S->rec);
     cudaFree(S->sc);
     cudaFree(S->feat);
@@ -884,13 +1127,21 @@ static cudaError_t grid_for(K kern, int threads, size_t smem, long long work, in
     return cudaSuccess;
 }
 
+// CTAs (4 warps each) of the warp-per-ray kernels for the long rays of a
+// pass of B rays: their number is known on the device only, so the grid is
+// sized for the worst case up to 4 CTAs per SM and the warps loop.
+static int long_ray_blocks(long long B) {
+    const long long want = (B + 3) / 4, cap = (long long)num_sms() * 4;
+    return (int)(want < cap ? (want < 1 ? 1 : want) : cap);
+}
+
 // Marches rays [0, B) of (o, d), counts their evaluated samples and reserves
 // their records (S.cnt, S.off: contiguous per ray, in ray order); *n receives
 // the total. One small read-back.
 static int count_pass(vrnerf_field *F, TrainScratch &S, const float *o, const float *d, int B, cudaStream_t st,
                       long long *n) {
     int blocks = 0;
-    cudaError_t e = cudaMemsetAsync(S.total, 0, 4 * sizeof(unsigned long long), st);
+    cudaError_t e = cudaMemsetAsync(S.total, 0, 8 * sizeof(unsigned long long), st);
     // step bits for emit, when they fit (else emit marches again)
     const int mw = (F->view.S + 31) / 32;
     const long long words = (long long)B * mw;
@@ -908,7 +1159,11 @@ static int count_pass(vrnerf_field *F, TrainScratch &S, const float *o, const fl
     S.mask_valid = mask != nullptr;
     if (e == cudaSuccess) e = grid_for(count_kernel, 128, 0, B, blocks);
     if (e == cudaSuccess) {
-        count_kernel<<<blocks, 128, 0, st>>>(F->view, o, d, B, S.cnt, mask, mw, S.total + 1);
+        unsigned int *n_long = reinterpret_cast<unsigned int *>(S.total + 4);
+        count_kernel<<<blocks, 128, 0, st>>>(F->view, o, d, B, S.cnt, mask, mw, S.total + 1, S.long_count, n_long);
+        if ((e = cudaGetLastError()) == cudaSuccess)
+            count_long_kernel<<<long_ray_blocks(B), 128, 0, st>>>(F->view, o, d, S.cnt, mask, mw, S.long_count,
+                                                                  n_long);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && B > 0) {  // record offsets: exclusive prefix sums of the counts
@@ -984,11 +1239,16 @@ static int samples_pass(vrnerf_field *F, TrainScratch &S, const float *o, const 
         }
     }
     if (e == cudaSuccess) e = grid_for(ray_comp_kernel, 128, 0, Bc, blocks);
-    if (e == cudaSuccess) e = cudaMemsetAsync(S.total + 2, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S.total + 2, 0, 2 * sizeof(unsigned long long), st);
     if (e == cudaSuccess) {
+        unsigned int *n_long = reinterpret_cast<unsigned int *>(S.total + 3);
         ray_comp_kernel<<<blocks, 128, 0, st>>>(f, o, d, Bc, S.cnt, S.off, S.rec, n_given, target, gC, inv3B, S.sc,
                                                 C_out ? n_out : S.n_used, target ? F->loss_acc : nullptr,
-                                                C_out ? nullptr : F->hist, C_out, S.total + 2);
+                                                C_out ? nullptr : F->hist, C_out, S.total + 2, S.long_comp, n_long);
+        if ((e = cudaGetLastError()) == cudaSuccess)
+            ray_comp_long_kernel<<<long_ray_blocks(Bc), 128, 0, st>>>(
+                f, o, d, S.cnt, S.off, S.rec, n_given, target, gC, inv3B, S.sc, C_out ? n_out : S.n_used,
+                target ? F->loss_acc : nullptr, C_out ? nullptr : F->hist, C_out, S.long_comp, n_long);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && n > 0 && tc_bwd) {

@@ -300,3 +300,43 @@ def test_large_batch_record_offsets(V):
     assert np.all((err <= 1e-4 * np.abs(ref["pq"]) + 1e-6)[~flip]), err[~flip].max()
     if flip.any():
         assert err[flip].max() <= cfg.T_eps + 1e-4
+
+
+@pytest.mark.parametrize("variant", ["room", "room_surface"])
+def test_long_rays_against_oracle(V, variant):
+    """Rays with more than 32 evaluated samples are counted and composited by
+    one warp each (the rest of the count split into 32 segments, the
+    composite 32 samples at a time with warp scans). Every such ray of a
+    12 800-ray training batch (476 here; the literal room's run to 217
+    samples without terminating, the opaque room's terminate early, three of
+    them after more than 32 samples) plus 300 short rays: loss and gradients
+    against the oracle at the fp32 bar, and the forward's colours and sample
+    counts."""
+    sc = S.make_scene(variant)
+    cfg = sc.cfg
+    poses, intr = S.training_views(sc.occ, cfg, n_views=64)
+    o, d, r, tgt = S.training_batch(poses, intr, 12800, seed=5, step=0)
+    F = O.Field(cfg, sc.grid, sc.mlp, sc.occ_bits)
+    _, _, cnt = F.march(o, d, cfg.max_steps)
+    long = np.nonzero(cnt > 32)[0]
+    assert len(long) > 100 and cnt.max() > 128
+    short = np.random.default_rng(1).choice(np.nonzero(cnt <= 32)[0], 300, replace=False)
+    pick = np.concatenate([long, short])
+    o, d, r, tgt = o[pick], d[pick], r[pick], tgt[pick]
+    f = V.Field(cfg, sc.grid, sc.mlp, sc.occ_bits)
+    loss_ref, rg, rm = F.backward(o, d, r, tgt)
+    loss = V.vrnerf_backward(f, _cuda(o), _cuda(d), _cuda(r), _cuda(tgt))
+    gg, gm = V.vrnerf_field_get_grads(f)
+    assert loss == pytest.approx(loss_ref, rel=1e-5)
+    _check_grads(gg, gm, rg, rm)
+    pq, n = V.vrnerf_forward_rays(f, _cuda(o), _cuda(d), _cuda(r))
+    V.vrnerf_field_status(f)
+    f.close()
+    ref = F.render_rays(o, d, r)
+    pq, n = pq.cpu().numpy(), n.cpu().numpy()
+    flip = n != ref["n"]
+    assert flip.mean() <= 0.01
+    err = np.abs(pq.astype(np.float64) - ref["pq"])
+    assert np.all((err <= 1e-4 * np.abs(ref["pq"]) + 1e-6)[~flip]), err[~flip].max()
+    if flip.any():
+        assert err[flip].max() <= cfg.T_eps + 1e-4

@@ -433,9 +433,13 @@ grid_scatter_kernel(const FieldView f, const float *__restrict__ o_in, const flo
 // Sample forward of the bf16 training precision: one thread per sample of a
 // 128-sample tile gathers its features straight into the bf16 operand tile
 // (kept in global memory for the backward) and the tile runs the MLPs on the
-// tensor cores; sigma and PQ colour per sample.
-template <int L>
-__global__ void __launch_bounds__(kTcThreads, kTcMinBlocks)
+// tensor cores; sigma and PQ colour per sample. Like the render kernel, a
+// CTA runs kFwdTiles tiles (one per 4-warp group, each with its own tiles of
+// the batch) that share one weight image, two CTAs per SM.
+constexpr int kFwdTiles = 4;
+
+template <int L, int NT>
+__global__ void __launch_bounds__(kTcThreads * NT, NT == 4 ? 2 : kTcMinBlocks / NT)
 sample_fwd_tc_kernel(const FieldView f, const float *__restrict__ o_in, const float *__restrict__ d_in,
                      const float *__restrict__ r_in, const int2 *__restrict__ rec, long long n,
                      float4 *__restrict__ sc, uint4 *__restrict__ feat_out, const uint4 *__restrict__ wimg,
@@ -443,13 +447,14 @@ sample_fwd_tc_kernel(const FieldView f, const float *__restrict__ o_in, const fl
     constexpr int D = 2 * L;
     extern __shared__ __align__(1024) unsigned char smem[];
     float *unused;
-    const TcShared S = tc_setup<D, 1>(smem, wimg, unused, nullptr, 0);
-    const int r = threadIdx.x;
+    const TcShared S = tc_setup<D, 1, NT>(smem, wimg, unused, nullptr, 0);
+    const int r = tile_row();
+    const int g = NT == 1 ? 0 : (int)(threadIdx.x >> 7);
     uint32_t phase = 0;
     bool ok = true;
     const long long tiles = (n + kTcThreads - 1) / kTcThreads;
-    for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-        if (__syncthreads_or(*S.abort)) break;
+    for (long long tile = (long long)blockIdx.x * NT + g; tile < tiles; tile += (long long)gridDim.x * NT) {
+        if (tile_sync_or(S.bar, *S.abort != 0)) break;
         const long long i = tile * kTcThreads + r;
         const bool have = i < n;
         float dir[3] = {0.0f, 0.0f, 1.0f};
@@ -565,15 +570,17 @@ static cudaError_t launch_fwd_tc_t(vrnerf_field *F, const float *o, const float 
     constexpr int D = 2 * L;
     cudaError_t e = ensure_bwd_images(F, st);
     if (e != cudaSuccess) return e;
-    const size_t smem = tc_smem_bytes(D, 0);
-    auto kern = sample_fwd_tc_kernel<L>;
+    constexpr int NT = kFwdTiles;
+    const size_t smem = tc_smem_bytes(D, 0, NT);
+    auto kern = sample_fwd_tc_kernel<L, NT>;
     int bps = 0;
-    if ((e = prepare_tc(kern, smem, bps)) != cudaSuccess) return e;
+    if ((e = prepare_tc(kern, smem, bps, NT)) != cudaSuccess) return e;
     const long long tiles = (n + kTcThreads - 1) / kTcThreads, cap = (long long)num_sms() * bps;
-    const int grid = (int)(tiles < cap ? tiles : cap);
+    const long long want = (tiles + NT - 1) / NT;
+    const int grid = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
     unsigned long long *status = reinterpret_cast<unsigned long long *>(F->counter) + 1;
-    kern<<<grid, kTcThreads, smem, st>>>(F->view, o, d, r, rec, n, sc, feat,
-                                         reinterpret_cast<const uint4 *>(F->tcb_w), status);
+    kern<<<grid, kTcThreads * NT, smem, st>>>(F->view, o, d, r, rec, n, sc, feat,
+                                              reinterpret_cast<const uint4 *>(F->tcb_w), status);
     return cudaGetLastError();
 }
 

@@ -623,7 +623,9 @@ def main():
                           "fps_p99": round(1e3 / float(np.percentile(st_ms, 99)), 2),
                           "frames": int(st_ms.size)},
         "e2e": {"value": round(e2e_v, 3), "unit": "Mrays/s", "h2d_bytes_per_step": 64,
-                "d2h_bytes_per_step": rays * 12},
+                "d2h_bytes_per_step": rays * 12,
+                "note": "vrnerf_render_host with pinned host arrays: cameras copied in, the image written "
+                        "by the kernel into the pinned output (zero-copy), timed to the call's return"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": hbm_peak,
                      "unit": "GB/s", "frac": round(achieved / hbm_peak, 5),
                      "traffic": (NCU_TRAFFIC_BYTES if NCU_TRAFFIC_CURRENT and precision_name == "fp16"

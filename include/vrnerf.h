@@ -193,8 +193,11 @@ int vrnerf_render(vrnerf_field *field, const float *cameras, const float *intrin
 
 /* vrnerf_render (Sec. 5) with every array in host memory: copies the cameras in and
  * the image out on `stream` through the field's device staging buffers and
- * returns after the stream has finished (synchronous). The optional outputs
- * of opts are ignored. EINVAL, ENOMEM, ECUDA. */
+ * returns after the stream has finished (synchronous). When out_host is
+ * pinned host memory the GPU can address (cudaHostAlloc / cudaHostRegister,
+ * mapped), the kernel writes the image into it directly and no staging
+ * buffer or copy is used; the values are the same. The optional outputs of
+ * opts are ignored. EINVAL, ENOMEM, ECUDA. */
 int vrnerf_render_host(vrnerf_field *field, const float *cameras_host, const float *intrinsics_host,
                        const int32_t *resolution_host, int32_t n, float *out_host,
                        const vrnerf_render_opts *opts, void *stream);

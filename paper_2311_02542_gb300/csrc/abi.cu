@@ -476,7 +476,16 @@ int vrnerf_render_host(vrnerf_field *F, const float *cameras_host, const float *
     cudaStream_t st = (cudaStream_t)stream;
     const size_t cam_bytes = (size_t)n * 16 * sizeof(float);
     const size_t out_bytes = (size_t)rays * 3 * sizeof(float);
-    if ((rc = F->ensure_staging(cam_bytes, out_bytes))) return rc;
+    // pinned host memory the GPU can address: the kernel writes the image
+    // there itself, overlapping the transfer with the render (no staging
+    // buffer, no copy after the kernel); pageable memory goes through staging
+    float *out_dev = nullptr;
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, out_host) == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer)
+        out_dev = static_cast<float *>(pa.devicePointer);
+    else
+        cudaGetLastError();
+    if ((rc = F->ensure_staging(cam_bytes, out_dev ? 0 : out_bytes))) return rc;
     cudaError_t e = cudaMemcpyAsync(F->stage_cam, cameras_host, (size_t)n * 12 * 4, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(F->stage_cam + (size_t)n * 12, intrinsics_host, (size_t)n * 4 * 4,
@@ -486,8 +495,8 @@ int vrnerf_render_host(vrnerf_field *F, const float *cameras_host, const float *
     make_camera_source(F->stage_cam, F->stage_cam + (size_t)n * 12, resolution_host, n, *src);
     vrnerf_render_opts o2{};
     if (opts) o2.precision = opts->precision;
-    if ((rc = render_common(F, *src, F->stage_out, &o2, st, rays))) return rc;
-    e = cudaMemcpyAsync(out_host, F->stage_out, out_bytes, cudaMemcpyDeviceToHost, st);
+    if ((rc = render_common(F, *src, out_dev ? out_dev : F->stage_out, &o2, st, rays))) return rc;
+    if (!out_dev) e = cudaMemcpyAsync(out_host, F->stage_out, out_bytes, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "render_host: download");
     return VRNERF_OK;

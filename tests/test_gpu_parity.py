@@ -265,8 +265,17 @@ def test_render_host_matches_device(V, cube):
     f = V.Field(cfg, cube.grid, cube.mlp, cube.occ_bits)
     c2w, K, res = S.camera_unit_cube(cube.occ, cfg, 1, 64, 48)
     a = V.vrnerf_render(f, _cuda(c2w), _cuda(K), res).cpu().numpy()
-    b = V.vrnerf_render_host(f, c2w, K, res)
+    b = V.vrnerf_render_host(f, c2w, K, res)  # pageable output: staging buffer and copy
     assert (a == b).all()
+    # pinned output: the kernel writes into host memory itself
+    pinned = torch.full((a.shape[0], 3), -1.0, dtype=torch.float32).pin_memory().numpy()
+    c = V.vrnerf_render_host(f, c2w, K, res, out=pinned)
+    assert c is pinned and (a == c).all()
+    for prec in ("fp16", "bf16"):
+        ref = V.vrnerf_render(f, _cuda(c2w), _cuda(K), res, precision=prec).cpu().numpy()
+        pinned[:] = -1.0
+        V.vrnerf_render_host(f, c2w, K, res, out=pinned, precision=prec)
+        assert (ref == pinned).all()
     f.close()
 
 

@@ -108,7 +108,7 @@ def test_query_tensorcore(V, cube, room, prec):
             bound = dh @ np.abs(W2[0]) + u * (np.abs(W2[0]) * hh).sum(1)
             rel = np.abs(gs - sig) / sig
             pos_b = bound > 0  # a point whose hidden units are all zero has o_0 = bias exactly
-            ratio = np.max(rel[pos_b] / bound[pos_b])
+            ratio = float(np.max(rel[pos_b] / bound[pos_b])) if pos_b.any() else 0.0
             print(f"bf16 sigma: max rel err {rel.max():.3e}, max bound {bound.max():.3e}, "
                   f"worst err / bound {ratio:.3f}")
             assert np.all(rel <= 2 * bound + 1e-6), ratio
